@@ -1,0 +1,223 @@
+"""FP64 CPU oracle for the D3Q19 BGK update (ctypes front end of lbm_oracle.c).
+
+TEST INFRASTRUCTURE ONLY: the test suite, the smoke check and the benchmark's
+CPU-baseline leg may import this package; the product path never does. It
+shares no code with the CUDA library.
+
+Arrays are numpy float64 in canonical layout: populations f[19][nz][ny][nx],
+velocity u[3][nz][ny][nx], x fastest; flags uint8 [nz][ny][nx] with 0 = fluid,
+1 = solid. The state f is the pre-collision populations f^n (push form).
+
+Every function follows Sec. 2 of the paper (moments, equilibrium after Qian et
+al., BGK relaxation of Eq. 1, streaming, bounce-back after Ziegler), with the
+Guo body force and halfway bounce-back as the readings stated in the C source.
+"""
+import ctypes
+
+import numpy as np
+
+from . import build as _build
+
+Q = 19
+FMT = {None: 0, "f64": 0, "f32": 1, "f16": 2, "bf16": 3}
+
+class Oracle:
+    """The oracle's functions bound to one build of lbm_oracle.c (ctypes)."""
+
+    def __init__(self, path):
+        L = ctypes.CDLL(path)
+        dp = ctypes.POINTER(ctypes.c_double)
+        ip = ctypes.POINTER(ctypes.c_int)
+        vp = ctypes.c_void_p
+        ci = ctypes.c_int
+        L.oracle_lattice.argtypes = [ip, dp, ip]
+        L.oracle_equilibrium.argtypes = [ctypes.c_double, dp, dp]
+        L.oracle_moments.argtypes = [dp, dp, dp, dp]
+        L.oracle_collide_cell.argtypes = [dp, ctypes.c_double, dp, dp]
+        L.oracle_round.argtypes = [ctypes.c_double, ci]
+        L.oracle_round.restype = ctypes.c_double
+        L.oracle_init.argtypes = [ci] * 3 + [vp, vp, vp, vp, ci]
+        L.oracle_run.argtypes = [ci] * 3 + [ctypes.c_double, vp, vp, ci, vp, ci, ci, ci]
+        L.oracle_run.restype = ci
+        L.oracle_macros.argtypes = [ci] * 3 + [vp, vp, ci, vp, vp, vp]
+        L.oracle_sums.argtypes = [ci] * 3 + [vp, vp, ci, vp, vp]
+        L.oracle_max_threads.restype = ci
+        self.lib = L
+        self.path = path
+
+    def lattice(self):
+        """Return (e [19,3] int, w [19] float64, opp [19] int) of the oracle's D3Q19 table."""
+        e = np.zeros((Q, 3), dtype=np.int32)
+        w = np.zeros(Q)
+        opp = np.zeros(Q, dtype=np.int32)
+        ip = ctypes.POINTER(ctypes.c_int)
+        self.lib.oracle_lattice(e.ctypes.data_as(ip), _dp(w), opp.ctypes.data_as(ip))
+        return e, w, opp
+
+    def equilibrium(self, rho, u):
+        """f_eq(rho, u) for one cell (Qian et al., cited in Sec. 2)."""
+        u = _f64(u)
+        out = np.zeros(Q)
+        self.lib.oracle_equilibrium(float(rho), _dp(u), _dp(out))
+        return out
+
+    def moments(self, f, F=(0.0, 0.0, 0.0)):
+        """(rho, u) of one cell, u = (j + F/2)/rho (Sec. 2 step 1 with the Guo shift)."""
+        f, F = _f64(f), _f64(F)
+        rho = np.zeros(1)
+        u = np.zeros(3)
+        self.lib.oracle_moments(_dp(f), _dp(F), _dp(rho), _dp(u))
+        return rho[0], u
+
+    def collide_cell(self, f, tau, F=(0.0, 0.0, 0.0)):
+        """Post-collision populations of one cell (Eq. 1 plus the Guo source)."""
+        f, F = _f64(f), _f64(F)
+        out = np.zeros(Q)
+        self.lib.oracle_collide_cell(_dp(f), float(tau), _dp(F), _dp(out))
+        return out
+
+    def round_storage_value(self, v, fmt):
+        """Round one FP64 value to 'f32' | 'f16' | 'bf16' (ties to even)."""
+        return self.lib.oracle_round(float(v), FMT[fmt])
+
+    def init_equilibrium(self, u0, rho0=None, flags=None, fmt=None):
+        """f^0 = f_eq(rho0, u0) per fluid cell; u0 [3][nz][ny][nx]; returns f [19][nz][ny][nx]."""
+        u0 = _f64(u0)
+        shape = u0.shape[1:]
+        nz, ny, nx = shape
+        fl = _flags(flags, shape)
+        r0 = None if rho0 is None else _f64(rho0)
+        f = np.zeros((Q,) + shape)
+        self.lib.oracle_init(nx, ny, nz, _vp(fl), _vp(r0), _vp(u0), _vp(f), FMT[fmt])
+        return f
+
+    def run(self, f, tau, steps, flags=None, F=None, fmt=None, threads=None):
+        """Advance state f by `steps` collide-and-stream steps; returns a new array."""
+        f = np.array(f, dtype=np.float64, order="C", copy=True)
+        shape = f.shape[1:]
+        nz, ny, nx = shape
+        fl = _flags(flags, shape)
+        Fa, per_cell = _force(F, shape)
+        nt = threads if threads else self.lib.oracle_max_threads()
+        rc = self.lib.oracle_run(nx, ny, nz, float(tau), _vp(fl), _vp(Fa), per_cell, _vp(f),
+                                 int(steps), FMT[fmt], int(nt))
+        if rc != 0:
+            raise MemoryError("oracle_run could not allocate its second lattice")
+        return f
+
+    def macros(self, f, flags=None, F=None):
+        """(rho [nz][ny][nx], u [3][nz][ny][nx]) of state f; zeros at solid cells."""
+        f = _f64(f)
+        shape = f.shape[1:]
+        nz, ny, nx = shape
+        fl = _flags(flags, shape)
+        Fa, per_cell = _force(F, shape)
+        rho = np.zeros(shape)
+        u = np.zeros((3,) + shape)
+        self.lib.oracle_macros(nx, ny, nz, _vp(fl), _vp(Fa), per_cell, _vp(f), _vp(rho), _vp(u))
+        return rho, u
+
+    def sums(self, f, flags=None, F=None):
+        """[sum rho, sum rho u_x, sum rho u_y, sum rho u_z] over fluid cells."""
+        f = _f64(f)
+        shape = f.shape[1:]
+        nz, ny, nx = shape
+        fl = _flags(flags, shape)
+        Fa, per_cell = _force(F, shape)
+        out = np.zeros(4)
+        self.lib.oracle_sums(nx, ny, nz, _vp(fl), _vp(Fa), per_cell, _vp(f), _vp(out))
+        return out
+
+    def max_threads(self):
+        return self.lib.oracle_max_threads()
+
+
+_default = None
+
+
+def default():
+    """The oracle built from oracle/lbm_oracle.c (compiled on first use)."""
+    global _default
+    if _default is None:
+        _default = Oracle(_build.build())
+    return _default
+
+
+def load(path):
+    """An Oracle bound to another build of the same C source (used by mutation tests)."""
+    return Oracle(path)
+
+
+def lattice():
+    return default().lattice()
+
+
+def equilibrium(rho, u):
+    return default().equilibrium(rho, u)
+
+
+def moments(f, F=(0.0, 0.0, 0.0)):
+    return default().moments(f, F)
+
+
+def collide_cell(f, tau, F=(0.0, 0.0, 0.0)):
+    return default().collide_cell(f, tau, F)
+
+
+def round_storage_value(v, fmt):
+    return default().round_storage_value(v, fmt)
+
+
+def init_equilibrium(u0, rho0=None, flags=None, fmt=None):
+    return default().init_equilibrium(u0, rho0, flags, fmt)
+
+
+def run(f, tau, steps, flags=None, F=None, fmt=None, threads=None):
+    return default().run(f, tau, steps, flags, F, fmt, threads)
+
+
+def macros(f, flags=None, F=None):
+    return default().macros(f, flags, F)
+
+
+def sums(f, flags=None, F=None):
+    return default().sums(f, flags, F)
+
+
+def max_threads():
+    return default().max_threads()
+
+
+def _dp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _vp(a):
+    return None if a is None else ctypes.c_void_p(a.ctypes.data)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _flags(flags, shape):
+    if flags is None:
+        return None
+    fl = np.ascontiguousarray(flags, dtype=np.uint8)
+    assert fl.shape == shape, (fl.shape, shape)
+    return fl
+
+
+def _force(F, shape):
+    """Return (array or None, per_cell flag) for a uniform [3] or field [3][nz][ny][nx] force."""
+    if F is None:
+        return None, 0
+    F = _f64(F)
+    if F.shape == (3,):
+        return F, 0
+    assert F.shape == (3,) + shape, F.shape
+    return F, 1
+
+
+__all__ = ["Q", "Oracle", "default", "load", "lattice", "equilibrium", "moments", "collide_cell", "round_storage_value",
+           "init_equilibrium", "run", "macros", "sums", "max_threads"]

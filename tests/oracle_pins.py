@@ -1,0 +1,400 @@
+"""Checks that pin the FP64 oracle to what the paper and the mathematics fix.
+
+Each check takes an `Oracle` instance (oracle.default() or a mutated build)
+and raises AssertionError when the oracle disagrees with:
+  - the textbook D3Q19 lattice (Qian et al., cited in Sec. 2) and its exact
+    rational moment identities;
+  - exact moment properties of the Qian equilibrium and of the Guo source;
+  - the BGK relaxation of Eq. 1 (tau = 1 maps to equilibrium);
+  - conservation laws of streaming and of halfway bounce-back (Sec. 2);
+  - symmetries (translation, reflection);
+  - closed-form solutions: shear-wave decay at nu = (tau - 1/2)/3 and plane
+    Poiseuille flow between bounce-back walls.
+None of them re-types the oracle's own formula.
+"""
+import os
+import sys
+from fractions import Fraction
+
+import numpy as np
+
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+import lbm_inputs  # noqa: E402
+
+# Textbook D3Q19 velocity set with weights as exact rationals (Qian et al.).
+GOLDEN_TABLE = "golden/d3q19_lattice.txt"
+
+
+def load_golden_table(path):
+    e, w = [], []
+    for line in open(path):
+        line = line.split("#", 1)[0].strip()
+        if not line:
+            continue
+        a, b, c, wt = line.split()
+        e.append((int(a), int(b), int(c)))
+        w.append(Fraction(wt))
+    return e, w
+
+
+def check_lattice_table(orc, golden_path):
+    e, w, opp = orc.lattice()
+    ge, gw = load_golden_table(golden_path)
+    assert [tuple(int(v) for v in r) for r in e] == ge, "velocity set differs from the textbook table"
+    for i in range(19):
+        assert w[i] == float(gw[i]), ("weight", i, w[i], gw[i])
+        assert tuple(e[opp[i]]) == tuple(-e[i]), ("opposite", i)
+
+
+def check_rational_identities(golden_path):
+    """Exact lattice isotropy identities of the textbook table (independent of the oracle)."""
+    e, w = load_golden_table(golden_path)
+    assert sum(w) == 1
+    for a in range(3):
+        assert sum(wi * ei[a] for wi, ei in zip(w, e)) == 0
+        for b in range(3):
+            m2 = sum(wi * ei[a] * ei[b] for wi, ei in zip(w, e))
+            assert m2 == (Fraction(1, 3) if a == b else 0)
+            for c in range(3):
+                assert sum(wi * ei[a] * ei[b] * ei[c] for wi, ei in zip(w, e)) == 0
+                for d in range(3):
+                    m4 = sum(wi * ei[a] * ei[b] * ei[c] * ei[d] for wi, ei in zip(w, e))
+                    want = Fraction((a == b) * (c == d) + (a == c) * (b == d) + (a == d) * (b == c), 9)
+                    assert m4 == want, (a, b, c, d, m4, want)
+
+
+def _lattice_arrays(orc):
+    e, w, _ = orc.lattice()
+    return e.astype(np.float64), w
+
+
+def check_equilibrium_moments(orc):
+    """Qian equilibrium: sum f_eq = rho, sum f_eq e = rho u, sum f_eq e e = rho/3 I + rho u u."""
+    e, _ = _lattice_arrays(orc)
+    rng = np.random.default_rng(1)
+    for _ in range(20):
+        rho = 1.0 + 0.2 * rng.standard_normal()
+        u = 0.05 * rng.standard_normal(3)
+        feq = orc.equilibrium(rho, u)
+        assert abs(feq.sum() - rho) < 1e-14
+        assert np.abs(feq @ e - rho * u).max() < 1e-15
+        pi = np.einsum("i,ia,ib->ab", feq, e, e)
+        want = rho / 3.0 * np.eye(3) + rho * np.outer(u, u)
+        assert np.abs(pi - want).max() < 1e-14, np.abs(pi - want).max()
+
+
+def check_collision_properties(orc):
+    """Eq. 1: tau = 1 gives f* = f_eq(rho, u) (F = 0); collision keeps mass; the
+    Guo source gives j* = j + F and the second-moment source
+    (1 - 1/(2 tau)) (u F + F u) (Guo, Zheng & Shi 2002)."""
+    e, w = _lattice_arrays(orc)
+    rng = np.random.default_rng(2)
+    for _ in range(20):
+        f = w * (1.0 + 0.05 * rng.standard_normal(19))
+        rho, u = orc.moments(f)
+        assert abs(rho - f.sum()) < 1e-15
+        assert np.abs(u - (f @ e) / rho).max() < 1e-15
+        fs = orc.collide_cell(f, 1.0)
+        assert np.abs(fs - orc.equilibrium(rho, u)).max() < 1e-15
+        tau = 0.5 + rng.random()
+        F = 1e-3 * rng.standard_normal(3)
+        fs = orc.collide_cell(f, tau, F)
+        assert abs(fs.sum() - f.sum()) < 1e-14
+        assert np.abs(fs @ e - (f @ e + F)).max() < 1e-15
+        rho, uF = orc.moments(f, F)
+        assert np.abs(uF - (f @ e + 0.5 * F) / rho).max() < 1e-15
+        # BGK second moment plus the Guo source moment
+        feq = orc.equilibrium(rho, uF)
+        pi_f = np.einsum("i,ia,ib->ab", f, e, e)
+        pi_eq = np.einsum("i,ia,ib->ab", feq, e, e)
+        pi_s = (1.0 - 0.5 / tau) * (np.outer(uF, F) + np.outer(F, uF))
+        want = pi_f - (pi_f - pi_eq) / tau + pi_s
+        got = np.einsum("i,ia,ib->ab", fs, e, e)
+        assert np.abs(got - want).max() < 1e-14, np.abs(got - want).max()
+
+
+def check_uniform_fixed_point(orc):
+    """A uniform (rho, u) field is a fixed point of the periodic update (F = 0)."""
+    u = np.zeros((3, 6, 5, 7))
+    u[0], u[1], u[2] = 0.03, -0.02, 0.01
+    rho0 = np.full((6, 5, 7), 1.02)
+    f0 = orc.init_equilibrium(u, rho0=rho0)
+    f = orc.run(f0, 0.7, 100)
+    assert np.abs(f - f0).max() < 1e-15 * 100, np.abs(f - f0).max()
+
+
+def check_rest_state_with_walls(orc):
+    """A closed box at rest stays at rest (bounce-back on every face)."""
+    flags = np.zeros((6, 7, 8), dtype=np.uint8)
+    flags[0], flags[-1] = 1, 1
+    flags[:, 0], flags[:, -1] = 1, 1
+    flags[:, :, 0], flags[:, :, -1] = 1, 1
+    flags[3, 3, 3] = 1
+    f0 = orc.init_equilibrium(np.zeros((3, 6, 7, 8)), flags=flags)
+    f = orc.run(f0, 0.8, 20, flags=flags)
+    assert np.abs(f - f0).max() < 1e-16
+
+
+def _random_state(orc, shape, seed, amp=0.02, flags=None):
+    rng = np.random.default_rng(seed)
+    u = amp * rng.standard_normal((3,) + shape)
+    rho0 = 1.0 + 0.01 * rng.standard_normal(shape)
+    f = orc.init_equilibrium(u, rho0=rho0, flags=flags)
+    # add non-equilibrium noise to fluid entries
+    fluid = np.ones(shape, bool) if flags is None else flags == 0
+    f = f + 1e-3 * rng.standard_normal(f.shape) * fluid
+    return f
+
+
+def check_periodic_conservation(orc):
+    """Periodic box, F = 0: total mass and momentum constant to round-off;
+    uniform F: total momentum grows by N F per step."""
+    shape = (5, 6, 7)
+    f = _random_state(orc, shape, 3)
+    s0 = orc.sums(f)
+    f2 = orc.run(f, 0.6, 30)
+    s2 = orc.sums(f2)
+    assert abs(s2[0] - s0[0]) <= 1e-13 * abs(s0[0])
+    assert np.abs(s2[1:] - s0[1:]).max() <= 1e-13 * abs(s0[0])
+    F = np.array([1e-4, -2e-4, 3e-4])
+    n_cells = np.prod(shape)
+    a = orc.sums(f, F=F)
+    b = orc.sums(orc.run(f, 0.6, 7, F=F), F=F)
+    assert abs(b[0] - a[0]) <= 1e-13 * abs(a[0])
+    assert np.abs((b[1:] - a[1:]) - 7 * n_cells * F).max() <= 1e-12, (b[1:] - a[1:]) / (7 * n_cells * F)
+
+
+def check_bounce_back_mass(orc):
+    """Halfway bounce-back permutes fluid entries, so total mass is conserved."""
+    shape = (6, 8, 9)
+    flags = lbm_inputs.random_flags(9, 8, 6, 0.2, 4)
+    f = _random_state(orc, shape, 5, flags=flags)
+    m0 = orc.sums(f, flags=flags)[0]
+    f2 = orc.run(f, 0.55, 25, flags=flags, F=np.array([1e-5, 0, 0]))
+    m2 = orc.sums(f2, flags=flags, F=np.array([1e-5, 0, 0]))[0]
+    assert abs(m2 - m0) <= 1e-13 * m0
+    assert np.all(f2[:, flags == 1] == 0.0)
+
+
+def check_translation_equivariance(orc):
+    """Shifting inputs (state, flags, force field) by a lattice vector shifts the output, bitwise."""
+    shape = (5, 6, 7)
+    flags = lbm_inputs.random_flags(7, 6, 5, 0.15, 6)
+    f = _random_state(orc, shape, 7, flags=flags)
+    F = 1e-4 * np.random.default_rng(8).standard_normal((3,) + shape)
+    out = orc.run(f, 0.62, 5, flags=flags, F=F)
+    sh = (1, 2, 3)
+    ax = (1, 2, 3)
+    out2 = orc.run(np.roll(f, sh, ax), 0.62, 5, flags=np.roll(flags, sh, (0, 1, 2)),
+                   F=np.roll(F, sh, ax))
+    assert np.array_equal(np.roll(out, sh, ax), out2)
+
+
+def check_reflection_symmetry(orc):
+    """Mirroring x -> -x (with e_x -> -e_x on populations and force) commutes with the update."""
+    e, _ = _lattice_arrays(orc)
+    perm = [int(np.where((e == e[i] * np.array([-1, 1, 1])).all(1))[0][0]) for i in range(19)]
+    shape = (4, 5, 6)
+    flags = lbm_inputs.random_flags(6, 5, 4, 0.15, 9)
+    f = _random_state(orc, shape, 10, flags=flags)
+    F = 1e-4 * np.random.default_rng(11).standard_normal((3,) + shape)
+
+    def mirror_pop(g):
+        g = g[perm]
+        return np.roll(g[..., ::-1], 1, axis=-1)  # x -> (-x) mod nx
+
+    def mirror_scalar(s):
+        return np.roll(s[..., ::-1], 1, axis=-1)
+
+    Fm = np.stack([-mirror_scalar(F[0]), mirror_scalar(F[1]), mirror_scalar(F[2])])
+    a = mirror_pop(orc.run(f, 0.58, 6, flags=flags, F=F))
+    b = orc.run(mirror_pop(f), 0.58, 6, flags=mirror_scalar(flags), F=Fm)
+    assert np.abs(a - b).max() < 1e-15, np.abs(a - b).max()
+
+
+def shear_wave_rate(orc, n, tau, t1=50, t2=100):
+    """Decay rate of the k = 2 pi/n shear-wave amplitude between t1 and t2."""
+    k = 2.0 * np.pi / n
+    y = np.arange(n)
+    u0 = np.zeros((3, 1, n, 1))
+    u0[0] = 0.01 * np.sin(k * y)[None, :, None]
+    f = orc.init_equilibrium(u0)
+
+    def amp(g):
+        _, u = orc.macros(g)
+        return 2.0 * np.mean(u[0] * np.sin(k * y)[None, :, None])
+
+    f1 = orc.run(f, tau, t1)
+    f2 = orc.run(f1, tau, t2 - t1)
+    return np.log(amp(f1) / amp(f2)) / (t2 - t1)
+
+
+def check_shear_wave(orc):
+    """u_x = A exp(-nu k^2 t) sin(k y), nu = (tau - 1/2)/3: rate within 2% at n = 32,
+    and the error falls by about 4x at n = 64 (second-order accuracy)."""
+    tau = 0.6
+    nu = (tau - 0.5) / 3.0
+    errs = []
+    for n in (32, 64):
+        k = 2.0 * np.pi / n
+        rate = shear_wave_rate(orc, n, tau)
+        errs.append(abs(rate / (nu * k * k) - 1.0))
+    assert errs[0] < 0.02, errs
+    assert 3.0 < errs[0] / errs[1] < 5.0, errs
+
+
+def poiseuille_error(orc, H, tau, Fx=1e-6):
+    """Max relative deviation from u(y) = F/(2 nu)(y - 1/2)(ny - 3/2 - y) at steady state."""
+    ny = H + 2
+    nu = (tau - 0.5) / 3.0
+    flags = np.zeros((1, ny, 1), np.uint8)
+    flags[:, 0, :] = flags[:, ny - 1, :] = 1
+    F = np.array([Fx, 0.0, 0.0])
+    f = orc.init_equilibrium(np.zeros((3, 1, ny, 1)), flags=flags)
+    f = orc.run(f, tau, int(8 * H * H / nu), flags=flags, F=F, threads=1)
+    _, u = orc.macros(f, flags=flags, F=F)
+    y = np.arange(1, ny - 1)
+    exact = Fx / (2.0 * nu) * (y - 0.5) * (ny - 1.5 - y)
+    return np.abs(u[0, 0, 1:ny - 1, 0] - exact).max() / exact.max()
+
+
+def check_poiseuille(orc):
+    """Plane Poiseuille flow between halfway bounce-back walls: exact at
+    tau = 1/2 + sqrt(3/16); second-order wall error at tau = 0.6."""
+    assert poiseuille_error(orc, 16, 0.5 + np.sqrt(3.0 / 16.0)) < 1e-9
+    e8 = poiseuille_error(orc, 8, 0.6)
+    e16 = poiseuille_error(orc, 16, 0.6)
+    assert e16 < 5e-3 and 3.0 < e8 / e16 < 5.0, (e8, e16)
+
+
+def check_storage_rounding(orc):
+    """Ties-to-even rounding to binary16 / binary32 / bfloat16 equals numpy's and torch's casts."""
+    import torch
+    rng = np.random.default_rng(12)
+    vals = np.concatenate([rng.standard_normal(2000) * 10.0 ** rng.integers(-9, 3, 2000),
+                           [0.0, -0.0, 65504.0, 65519.99, 65520.0, 6e-8, 3e-8, 1e-40,
+                            1.0 + 2.0 ** -11, 1.0 + 3 * 2.0 ** -11, 1.0 + 2.0 ** -8,
+                            1.0 + 3 * 2.0 ** -8, 1.0 + 2.0 ** -24]])
+    for v in vals:
+        assert orc.round_storage_value(v, "f16") == float(np.float16(v)), v
+        assert orc.round_storage_value(v, "f32") == float(np.float32(v)), v
+        # torch rounds float64 -> bfloat16 through float32 (double rounding);
+        # compare on values exactly representable in float32.
+        v32 = float(np.float32(v))
+        want = torch.tensor(v32, dtype=torch.float32).to(torch.bfloat16).item()
+        assert orc.round_storage_value(v32, "bf16") == want, v32
+
+
+def check_advected_shear_wave(orc):
+    """Galilean transport: u = (U, A sin kx, 0) on a periodic line along x gives
+    u_y = A exp(-nu k^2 t) sin(k (x - U t)); phase and amplitude within 1%."""
+    n, U, A, tau, t = 32, 0.05, 0.005, 0.6, 100
+    k = 2.0 * np.pi / n
+    x = np.arange(n)
+    u0 = np.zeros((3, 1, 1, n))
+    u0[0] = U
+    u0[1] = A * np.sin(k * x)
+    f = orc.run(orc.init_equilibrium(u0), tau, t)
+    _, u = orc.macros(f)
+    z = 2.0 * np.mean(u[1, 0, 0] * np.exp(-1j * k * x))  # = A' e^{-i phi} / i
+    phase = -np.angle(1j * z)
+    nu = (tau - 0.5) / 3.0
+    assert abs(phase / (k * U * t) - 1.0) < 0.01, (phase, k * U * t)
+    assert abs(abs(z) / A / np.exp(-nu * k * k * t) - 1.0) < 0.01
+
+
+def check_diagonal_shear_wave(orc):
+    """u_x = A sin(k (y + z)) decays at nu (k_y^2 + k_z^2) = 2 nu k^2 (within 1%)."""
+    n, tau, t1, t2 = 32, 0.6, 50, 100
+    k = 2.0 * np.pi / n
+    basis = np.sin(k * (np.arange(n)[None, :] + np.arange(n)[:, None]))[:, :, None]
+    u0 = np.zeros((3, n, n, 1))
+    u0[0] = 0.01 * basis
+
+    def amp(g):
+        _, u = orc.macros(g)
+        return 2.0 * np.mean(u[0] * basis)
+
+    f1 = orc.run(orc.init_equilibrium(u0), tau, t1)
+    f2 = orc.run(f1, tau, t2 - t1)
+    nu = (tau - 0.5) / 3.0
+    rate = np.log(amp(f1) / amp(f2)) / (t2 - t1)
+    assert abs(rate / (2.0 * nu * k * k) - 1.0) < 0.01, rate / (2.0 * nu * k * k)
+
+
+def check_init_moments(orc):
+    """f^0 = f_eq(rho0, u0) has density rho0 and velocity u0 at every fluid cell."""
+    shape = (3, 4, 5)
+    rng = np.random.default_rng(13)
+    u0 = 0.03 * rng.standard_normal((3,) + shape)
+    rho0 = 1.0 + 0.05 * rng.standard_normal(shape)
+    flags = lbm_inputs.random_flags(5, 4, 3, 0.2, 14)
+    fluid = flags == 0
+    rho, u = orc.macros(orc.init_equilibrium(u0, rho0=rho0, flags=flags), flags=flags)
+    assert np.abs((rho - rho0)[fluid]).max() < 1e-14
+    assert np.abs((u - u0)[:, fluid]).max() < 1e-15
+    assert np.all(rho[~fluid] == 0)
+
+
+def check_shifted_storage_emulation(orc):
+    """Storage rounding acts on the deviation f_i - w_i: the rest state starts
+    exactly at w_i in every format and stays there to FP64 round-off (exactly
+    in binary16, whose smallest step is far above that round-off), and every
+    stored deviation is a value of the format after a run."""
+    _, w, _ = orc.lattice()
+    shape = (4, 5, 6)
+    for fmt in ("f32", "f16", "bf16"):
+        f0 = orc.init_equilibrium(np.zeros((3,) + shape), fmt=fmt)
+        assert np.array_equal(f0, np.broadcast_to(w[:, None, None, None], f0.shape))
+        f5 = orc.run(f0, 0.6, 5, fmt=fmt)
+        assert np.abs(f5 - f0).max() <= 2.3e-16
+        if fmt == "f16":
+            assert np.array_equal(f5, f0)
+    rng = np.random.default_rng(15)
+    f = orc.run(orc.init_equilibrium(0.03 * rng.standard_normal((3,) + shape), fmt="f16"),
+                0.6, 3, fmt="f16")
+    dev = f - w[:, None, None, None]
+    assert np.abs(dev - dev.astype(np.float16).astype(np.float64)).max() < 1e-16
+
+
+ALL_ORACLE_CHECKS = [
+    check_equilibrium_moments,
+    check_collision_properties,
+    check_uniform_fixed_point,
+    check_rest_state_with_walls,
+    check_periodic_conservation,
+    check_bounce_back_mass,
+    check_translation_equivariance,
+    check_reflection_symmetry,
+    check_shear_wave,
+    check_advected_shear_wave,
+    check_diagonal_shear_wave,
+    check_init_moments,
+    check_shifted_storage_emulation,
+    check_poiseuille,
+    check_storage_rounding,
+]
+
+
+def run_all(orc, golden_path):
+    """Run every check; return the name of the first failing one, or None."""
+    checks = [lambda o: check_lattice_table(o, golden_path)] + ALL_ORACLE_CHECKS
+    names = ["check_lattice_table"] + [c.__name__ for c in ALL_ORACLE_CHECKS]
+    for name, chk in zip(names, checks):
+        try:
+            chk(orc)
+        except AssertionError:
+            return name
+    return None
+
+
+if __name__ == "__main__":
+    # python oracle_pins.py <liblbm_oracle.so>: exit 1 naming the first failing
+    # check, 0 if all pass (used to run mutated oracle builds in a child process).
+    import os
+    import sys
+    import oracle
+    failed = run_all(oracle.load(sys.argv[1]),
+                     os.path.join(os.path.dirname(os.path.abspath(__file__)), GOLDEN_TABLE))
+    print("FAILED_CHECK", failed)
+    sys.exit(1 if failed else 0)
