@@ -1,0 +1,379 @@
+"""Throughput of the fused D3Q19 BGK stream-collide path on GB300.
+
+One step = one fused stream-collide update of the whole lattice (one kernel
+launch). The workload is the walled channel: 256 x 128 x 128 cells, periodic
+in x, solid walls at y in {0, 127} and z in {0, 127}, seeded spherical
+obstacles (radius 3-6) filling 10% of the interior, halfway bounce-back,
+uniform body force g_x = 1e-6, tau = 0.55, populations stored in FP32.
+Synthetic inputs (lbm_inputs); the lattices (2 x 319 MB) exceed L2, so no
+flush is needed between steps.
+
+Prints one JSON line: value = million fluid-cell updates per second (MFLUPS,
+the paper's metric), the roofline of the step kernel against measured HBM
+bandwidth, the FP64 oracle timed on the host cores, an end-to-end figure
+through host buffers, the other storage formats and the adjoint/forward
+step-time ratio on the same workload.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+With N > 1 (torchrun), every rank runs an independent replica on its own GPU
+(weak scaling; the method needs no exchange between replicas); rank 0 prints
+the aggregate over the max-over-ranks time.
+"""
+import argparse
+import hashlib
+import glob
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import lbm_inputs  # noqa: E402
+
+METRIC = "D3Q19 MLUPS & % of HBM roofline per precision; adjoint/forward step-time ratio"
+NX, NY, NZ, TAU, GX, SOLID = 256, 128, 128, 0.55, 1e-6, 0.10
+WORKLOAD = ("D3Q19 BGK channel 256x128x128 (x periodic), walls y=0/127 z=0/127 + seeded spheres r 3-6 "
+            "(10% solid), halfway bounce-back, g_x=1e-6, tau=0.55")
+PDF_BYTES = {"f64": 304, "f32": 152, "f16s": 76, "bf16s": 76}
+FLAG_BYTES = 1
+STEP_KERNEL = "k_step"
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for p in sorted(glob.glob(os.path.join(ROOT, "paper_1112_0850_gb300", "csrc", "*"))):
+        with open(p, "rb") as f:
+            h.update(os.path.basename(p).encode())
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(storage):
+    """DRAM bytes per step launch from the committed ncu summary, if it was
+    taken on the current kernel sources; else None."""
+    path = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+    except Exception:
+        return None
+    if d.get("src_hash") != kernel_source_hash():
+        return None
+    ent = d.get("kernels", {}).get(storage)
+    return None if ent is None else float(ent["dram_bytes_per_launch"])
+
+
+def workload_flags():
+    return lbm_inputs.channel_flags(NX, NY, NZ, SOLID, lbm_inputs.seed_for(1))
+
+
+class ClockSampler:
+    """nvidia-smi SM clock and throttle reasons sampled every 100 ms."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        except Exception:
+            pass
+        if self.path and os.path.exists(self.path):
+            os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no nvidia-smi samples"], "samples": 0}
+
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return float("nan")
+
+        sm = np.array([num(r[1]) for r in rows])
+        mx = np.array([num(r[2]) for r in rows])
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": float(np.nanmedian(sm)), "sm_max_mhz": float(np.nanmax(mx)), "reasons": reasons,
+                "samples": len(rows), "power_w_max": float(np.nanmax([num(r[3]) for r in rows]))}
+
+
+# ----------------------------------------------------------------------------------------------
+def oracle_baseline(flags, budget_s, threads=None):
+    """Time the FP64 oracle on a z-slab sample of the workload: returns
+    (MFLUPS, cores, sample description, fluid cells, steps)."""
+    import oracle
+    cores = threads or oracle.max_threads()
+    # calibrate on a thin slab, then size the slab to fill the budget with 2 steps
+    def slab(nzs):
+        z0 = (NZ - nzs) // 2
+        fl = np.ascontiguousarray(flags[z0:z0 + nzs])
+        f = oracle.init_equilibrium(np.zeros((3, nzs, NY, NX)), flags=fl)
+        return fl, f
+    fl, f = slab(4)
+    t0 = time.perf_counter()
+    oracle.run(f, TAU, 1, flags=fl, F=np.array([GX, 0.0, 0.0]), threads=cores)
+    t_cell = (time.perf_counter() - t0) / (4 * NY * NX)
+    steps = 2
+    nzs = int(max(1, min(NZ, budget_s / max(t_cell, 1e-12) / (NY * NX) / steps)))
+    fl, f = slab(nzs)
+    nfl = int((fl == 0).sum())
+    t0 = time.perf_counter()
+    oracle.run(f, TAU, steps, flags=fl, F=np.array([GX, 0.0, 0.0]), threads=cores)
+    dt = time.perf_counter() - t0
+    desc = ("oracle (plain C, FP64, OpenMP over z) on the middle %d of 128 z-layers of the channel "
+            "(%dx%dx%d, %d fluid cells), %d steps, %.1f s" % (nzs, NX, NY, nzs, nfl, steps, dt))
+    return nfl * steps / dt / 1e6, cores, desc, nfl, steps
+
+
+def reference_arm(args):
+    """The oracle as the reference implementation: each step one oracle update
+    of a z-slab sample of the workload, sized so the whole run stays short."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    flags = workload_flags()
+    cores = oracle.max_threads()
+    nsteps = args.steps + args.warmup
+    fl4 = np.ascontiguousarray(flags[62:66])
+    f = oracle.init_equilibrium(np.zeros((3, 4, NY, NX)), flags=fl4)
+    t0 = time.perf_counter()
+    oracle.run(f, TAU, 1, flags=fl4, F=np.array([GX, 0.0, 0.0]), threads=cores)
+    t_cell = (time.perf_counter() - t0) / (4 * NY * NX)
+    budget = 120.0
+    nzs = int(max(2, min(NZ, budget / max(t_cell, 1e-12) / (NY * NX) / max(nsteps, 1))))
+    z0 = (NZ - nzs) // 2
+    fl = np.ascontiguousarray(flags[z0:z0 + nzs])
+    nfl = int((fl == 0).sum())
+    f = oracle.init_equilibrium(np.zeros((3, nzs, NY, NX)), flags=fl)
+    F = np.array([GX, 0.0, 0.0])
+    f = oracle.run(f, TAU, args.warmup, flags=fl, F=F, threads=cores)
+    t0 = time.perf_counter()
+    oracle.run(f, TAU, args.steps, flags=fl, F=F, threads=cores)
+    dt = time.perf_counter() - t0
+    value = nfl * args.steps / dt / 1e6
+    sample = ("each step: one oracle update (plain C, FP64, OpenMP over z) of the middle %d of 128 z-layers "
+              "of the channel (%dx%dx%d, %d fluid cells)" % (nzs, NX, NY, nzs, nfl))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "MFLUPS", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / max(args.steps, 1) * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "storage": "f64 (oracle)",
+                                            "parallelism": "host cores"},
+            "cpu_baseline": {"value": value, "unit": "MFLUPS", "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "MFLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------------------------
+def time_steps(torch, lat, steps, warmup):
+    """Warm up, then time `steps` single-step launches with CUDA events on the lattice's stream."""
+    lat.step(warmup)
+    st = lat.stream
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(st)
+    lat.step(steps)
+    e1.record(st)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1e3
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-extras", action="store_true", help="skip other precisions, adjoint ratio, CPU baseline")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    if args.impl == "reference":
+        return reference_arm(args)
+
+    import torch
+    import torch.distributed as dist
+    from paper_1112_0850_gb300 import build
+    from paper_1112_0850_gb300.lattice import Lattice
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    build.build()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(v):
+        if world == 1:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return t.item()
+
+    flags = workload_flags()
+    F = (GX, 0.0, 0.0)
+    lat = Lattice(NX, NY, NZ, TAU, flags=flags, force=F, storage="f32")
+    n_fluid, n_cells = lat.n_fluid, NX * NY * NZ
+    lat.init_equilibrium(lat.zeros(3))
+
+    # ---- headline: FP32 steps, device-resident --------------------------------------------
+    lat.step(args.warmup)
+    torch.cuda.synchronize()
+    barrier()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(lat.stream)
+        lat.step(args.steps)
+        e1.record(lat.stream)
+        torch.cuda.synchronize()
+    barrier()
+    dt_local = e0.elapsed_time(e1) / 1e3
+    dt = max_over_ranks(dt_local)
+    clocks = clk.summary()
+    status = lat.status_word()
+    value = world * n_fluid * args.steps / dt / 1e6
+    per_launch = dt_local / args.steps
+    peak, peak_kind = measured_peaks()
+    alg_bytes = n_fluid * PDF_BYTES["f32"] + n_cells * FLAG_BYTES
+    achieved = alg_bytes / per_launch / 1e9
+    traffic = ncu_traffic("f32")
+
+    extras = {}
+    cpu = None
+    e2e = None
+    if not args.no_extras:
+        # ---- other storage formats on the same workload -------------------------------------
+        per_prec = {"f32": {"mflups": n_fluid / per_launch / 1e6, "gbs": achieved, "frac": achieved / peak}}
+        ks = max(10, args.steps // 5)
+        for s in ("f64", "f16s", "bf16s"):
+            l2 = Lattice(NX, NY, NZ, TAU, flags=flags, force=F, storage=s)
+            l2.init_equilibrium(l2.zeros(3))
+            t = time_steps(torch, l2, ks, args.warmup) / ks
+            gbs = (n_fluid * PDF_BYTES[s] + n_cells * FLAG_BYTES) / t / 1e9
+            per_prec[s] = {"mflups": n_fluid / t / 1e6, "gbs": gbs, "frac": gbs / peak}
+            l2.close()
+        extras["per_precision"] = per_prec
+        # ---- adjoint / forward step-time ratio (FP32, per-cell force gradient) -------------
+        K = 50
+        tape = lat.new_tape(K)
+        gF = lat.zeros(3)
+        lat.adjoint_seed(lat.zeros(3).add_(1e-3), None, gF)
+        st = lat.stream
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        lat.step_record(K, tape)
+        lat.adjoint_step(K, tape, gF)
+        torch.cuda.synchronize()
+        ev[0].record(st)
+        lat.step_record(K, tape)
+        ev[1].record(st)
+        lat.adjoint_step(K, tape, gF)
+        ev[2].record(st)
+        torch.cuda.synchronize()
+        t_rec = ev[0].elapsed_time(ev[1]) / 1e3 / K
+        t_adj = ev[1].elapsed_time(ev[2]) / 1e3 / K
+        extras["adjoint_forward_ratio"] = (t_rec + t_adj) / per_launch
+        extras["adjoint_forward_ratio_no_recompute"] = t_adj / per_launch
+        extras["adjoint_step_gbs"] = (n_fluid * (76 + 76 + 16 + 24) + n_cells) / t_adj / 1e9
+        del tape, gF
+        # ---- end to end through the C-ABI with host buffers --------------------------------
+        u0_host = torch.zeros((3, NZ, NY, NX), dtype=torch.float32).pin_memory()
+        u_host = torch.empty((3, NZ, NY, NX), dtype=torch.float32).pin_memory()
+        rho_host = torch.empty((NZ, NY, NX), dtype=torch.float32).pin_memory()
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        l3 = Lattice(NX, NY, NZ, TAU, flags=flags, force=F, storage="f32")
+        l3.init_equilibrium(u0_host)
+        l3.step(args.steps)
+        l3.macros(rho_host, u_host)
+        sums = l3.reduce()
+        l3.close()
+        t_e2e = max_over_ranks(time.perf_counter() - t0)
+        h2d = flags.nbytes + u0_host.numel() * 4
+        d2h = u_host.numel() * 4 + rho_host.numel() * 4 + 32
+        e2e = {"value": world * n_fluid * args.steps / t_e2e / 1e6, "unit": "MFLUPS",
+               "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+               "what": "whole job per replica: lbm_create from host flags, init from pinned host u0, "
+                       "%d steps, macros and FP64 totals back to host, destroy" % args.steps,
+               "mass": float(sums[0])}
+        # ---- CPU baseline: the oracle on a bounded sample -----------------------------------
+        if rank == 0 and world == 1:
+            v, cores, desc, _, _ = oracle_baseline(flags, 10.0)
+            cpu = {"value": v, "unit": "MFLUPS", "cores": cores, "kind": "oracle", "sample": desc}
+
+    lat.close()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "MFLUPS", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "nx": NX, "ny": NY, "nz": NZ, "n_cells": n_cells,
+                       "n_fluid": n_fluid, "storage": "f32 (shifted f - w)", "tau": TAU,
+                       "l2": "no flush: two lattices of 319 MB each exceed the 129 MB L2",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic, "kernel": STEP_KERNEL + "<f32,flags,uniform force>",
+                         "peak_source": peak_kind + " hbm_gbs (MEASURED_PEAKS.json)",
+                         "alg_bytes_per_launch": alg_bytes},
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps, "clocks": clocks,
+            "status_word": status,
+        }
+        line.update(extras)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

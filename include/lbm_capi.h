@@ -1,0 +1,212 @@
+/*
+ * lbm_capi.h: C interface of the GB300 D3Q19 BGK lattice Boltzmann library.
+ *
+ * The library advances the D3Q19 lattice Boltzmann equation with the BGK
+ * collision operator (Habich et al., "Performance engineering for the lattice
+ * Boltzmann method on GPGPUs", Sec. 2, Eq. 1), fusing the stream and collide
+ * steps into one pass over two lattices (Sec. 2 and Sec. 6, "stream-collide"
+ * with two grids), with bounce-back at cells flagged as obstacles (Sec. 2,
+ * the Ziegler rule, folded into streaming) and a body force. The equilibrium
+ * is the D3Q19 one of Qian et al. cited in Sec. 2; the body force is the
+ * Guo, Zheng & Shi (2002) scheme, u = (j + F/2)/rho; bounce-back is the
+ * halfway rule. The paper gives neither the force nor the bounce-back
+ * variant; these are this library's readings.
+ *
+ * Conventions shared by every call:
+ *   - Lattice of nx * ny * nz cells, all three axes periodic; walls are cells
+ *     flagged solid. Canonical arrays are C-ordered [.. ][nz][ny][nx] (x
+ *     fastest); N = nx * ny * nz.
+ *   - Velocity set (19 directions, fixed order): rest; +x, -x, +y, -y, +z, -z;
+ *     then (+1,+1,0), (+1,-1,0), (-1,+1,0), (-1,-1,0), (+1,0,+1), (+1,0,-1),
+ *     (-1,0,+1), (-1,0,-1), (0,+1,+1), (0,+1,-1), (0,-1,+1), (0,-1,-1).
+ *     Weights 1/3, 1/18 (axis), 1/36 (diagonal). lbm_lattice_table() returns it.
+ *   - "real" is double when the context stores LBM_F64 and float otherwise:
+ *     every canonical input and output array (density, velocity, force
+ *     field, tape, adjoint gradients) has that element type.
+ *   - Population state is exchanged as shifted deviations s_i = f_i - w_i,
+ *     canonical layout [19][nz][ny][nx], in any of the four storage formats.
+ *   - Pointers to canonical arrays may be device pointers or host pointers
+ *     (pageable or pinned); the library tells them apart with
+ *     cudaPointerGetAttributes. A call that reads a host array copies it in
+ *     before returning; a call that writes a host array synchronizes the
+ *     context's stream and the data is valid when it returns. Device arrays
+ *     are read and written asynchronously on the context's stream.
+ *   - The caller owns every array it passes; the context owns the lattices,
+ *     its copies of flags and force field, the adjoint lattices and scratch.
+ *   - Every call returns an lbm_status; no C++ exception crosses this
+ *     interface. On error, lbm_last_error() describes the failure.
+ *   - Kernel-side failures (a non-finite or non-positive density) set bits of
+ *     a device status word which lbm_status_word() reads; they never trap.
+ */
+#ifndef LBM_CAPI_H
+#define LBM_CAPI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBM_Q 19
+
+typedef struct lbm_ctx lbm_ctx;
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_ERR_ARG = 1,         /* invalid argument (size, tau, pointer, format) */
+    LBM_ERR_OOM = 2,         /* device allocation failed or size would not fit */
+    LBM_ERR_CUDA = 3,        /* a CUDA runtime call failed */
+    LBM_ERR_STATE = 4,       /* call out of order (e.g. adjoint step before seed) */
+    LBM_ERR_DIVERGED = 5,    /* a kernel saw a non-finite or non-positive density */
+    LBM_ERR_INDEX = 6,       /* an index check failed (checked builds only) */
+    LBM_ERR_UNSUPPORTED = 7  /* combination not provided by this build */
+} lbm_status;
+
+/* Population storage formats. S = shifted: the stored value is f_i - w_i
+ * (density deviation around rest, rho0 = 1); collision arithmetic is FP64 for
+ * LBM_F64 and FP32 for the three others. Narrow formats round to nearest even. */
+typedef enum {
+    LBM_F64 = 0,   /* double, 304 B per lattice update  */
+    LBM_F32 = 1,   /* float,  152 B per lattice update  */
+    LBM_F16S = 2,  /* IEEE binary16, 76 B per lattice update */
+    LBM_BF16S = 3  /* bfloat16,      76 B per lattice update */
+} lbm_storage;
+
+/* Bits of the device status word. */
+#define LBM_STATUS_DIVERGED 0x1u /* some fluid cell had rho <= 0 or non-finite rho */
+#define LBM_STATUS_INDEX    0x2u /* a checked build caught an out-of-range index */
+
+typedef struct {
+    lbm_storage storage; /* default LBM_F32 */
+    void *cuda_stream;   /* cudaStream_t used for every launch and copy; NULL = default stream */
+} lbm_options;
+
+typedef struct {
+    int nx, ny, nz;
+    int pitch;                  /* padded row length in elements (rows start 128-byte aligned) */
+    lbm_storage storage;
+    int real_size;              /* bytes of "real": 8 (LBM_F64) or 4 */
+    double tau;
+    int64_t n_cells;            /* nx * ny * nz */
+    int64_t n_fluid;            /* cells with flag 0 */
+    size_t lattice_bytes;       /* bytes of one padded population lattice (19 arrays) */
+    size_t tape_bytes_per_step; /* bytes lbm_step_record writes per step */
+    int64_t steps_done;         /* time steps since the last init or set_state */
+} lbm_info;
+
+/* Fill *opt with defaults (LBM_F32, default stream). */
+lbm_status lbm_options_default(lbm_options *opt);
+
+/* Create a context for an nx * ny * nz periodic lattice (Sec. 2: the uniform
+ * grid of lattice nodes, two lattices for the stream-collide update, Sec. 6).
+ *   tau   relaxation time of Eq. 1; must exceed 0.5 (viscosity (tau - 1/2)/3).
+ *   flags nullable (= all fluid); uint8 [nz][ny][nx], 0 = fluid, nonzero =
+ *         solid (obstacle, bounce-back per Sec. 2); host or device; copied.
+ *   force nullable (= zero); host array of 3 doubles: uniform body-force
+ *         density in lattice units.
+ *   opt   nullable (= defaults).
+ * Sizes: 1 <= nx, ny; 1 <= nz <= 65535; padded cells nz * ny * pitch < 2^31.
+ * Returns LBM_ERR_OOM if two lattices do not fit in free device memory. The
+ * lattices are zero (rest state) after creation. */
+lbm_status lbm_create(lbm_ctx **out, int nx, int ny, int nz, double tau, const uint8_t *flags,
+                      const double force[3], const lbm_options *opt);
+
+/* Free everything the context owns. NULL-safe. Synchronizes its stream. */
+void lbm_destroy(lbm_ctx *ctx);
+
+lbm_status lbm_get_info(const lbm_ctx *ctx, lbm_info *info);
+
+/* Replace the uniform body force (host array of 3 doubles; NULL = zero). */
+lbm_status lbm_set_uniform_force(lbm_ctx *ctx, const double force[3]);
+
+/* Install a per-cell force field F: real [3][nz][ny][nx], host or device,
+ * copied into the context. NULL removes the field (back to the uniform force). */
+lbm_status lbm_set_force_field(lbm_ctx *ctx, const void *F);
+
+/* Initialise the populations to the equilibrium f_eq(rho0, u0) at every fluid
+ * cell (Sec. 2; equilibrium of Qian et al.).
+ *   rho nullable (= 1): real [nz][ny][nx];  u: real [3][nz][ny][nx].
+ * Resets steps_done to 0. */
+lbm_status lbm_init_equilibrium(lbm_ctx *ctx, const void *rho, const void *u);
+
+/* Enqueue n >= 0 fused stream-collide time steps (Sec. 2 steps 1-3 with
+ * bounce-back; Sec. 6 pull-style update over two grids). Asynchronous. */
+lbm_status lbm_step(lbm_ctx *ctx, int n);
+
+/* Macroscopic fields of the current state (Sec. 2 step 1): rho = sum f_i,
+ * u = (sum f_i e_i + F/2) / rho. rho nullable: real [nz][ny][nx];
+ * u: real [3][nz][ny][nx]. Solid cells read 0. */
+lbm_status lbm_macros(lbm_ctx *ctx, void *rho, void *u);
+
+/* Totals over fluid cells of the current state, accumulated in FP64 in a
+ * fixed order (deterministic): out = {sum rho, sum rho u_x, sum rho u_y,
+ * sum rho u_z} with rho u = j + F/2. out is a host array; synchronizes. */
+lbm_status lbm_reduce(lbm_ctx *ctx, double out[4]);
+
+/* Copy the current state out as shifted populations s_i = f_i - w_i in format
+ * fmt, canonical [19][nz][ny][nx] (element type double / float / binary16 /
+ * bfloat16). Solid cells read 0. Host or device destination. */
+lbm_status lbm_get_state(lbm_ctx *ctx, void *dst, lbm_storage fmt);
+
+/* Load a state written by lbm_get_state (any format; converted to the
+ * context's storage with round-to-nearest-even). Solid-cell values ignored.
+ * Resets steps_done to 0. Round trip in the context's own format is exact. */
+lbm_status lbm_set_state(lbm_ctx *ctx, const void *src, lbm_storage fmt);
+
+/* As lbm_step, and also record, for each of the n steps k, the moments the
+ * adjoint needs: (rho, u_x, u_y, u_z) of the pre-collision state at step k,
+ * u including the F/2 shift. tape: device array of n * tape_bytes_per_step
+ * bytes (opaque layout). */
+lbm_status lbm_step_record(lbm_ctx *ctx, int n, void *tape);
+
+/* Start a discrete adjoint (not in the paper: the transpose of the update
+ * above) at the current state f^T for a loss L(rho_T, u_T):
+ *   dL_du   real [3][nz][ny][nx] (required), dL_drho nullable real [nz][ny][nx].
+ *   grad_F  nullable real [3][nz][ny][nx], device: receives dL/dF from the
+ *           explicit F/2 in u_T (accumulated: +=).
+ * Sets the adjoint populations lambda^T = dL/df^T. */
+lbm_status lbm_adjoint_seed(lbm_ctx *ctx, const void *dL_du, const void *dL_drho, void *grad_F);
+
+/* n reverse steps of the adjoint: lambda^k = J_k^T G^T lambda^(k+1) for
+ * k = n-1 .. 0, where G is the streaming/bounce-back permutation and J_k the
+ * BGK + Guo collision Jacobian at the moments recorded in tape (written by
+ * lbm_step_record for the same n steps from the matching state).
+ * grad_F nullable, device real [3][nz][ny][nx]: dL/dF(x) is accumulated (+=). */
+lbm_status lbm_adjoint_step(lbm_ctx *ctx, int n, const void *tape, void *grad_F);
+
+/* Gradients with respect to the initial fields of lbm_init_equilibrium:
+ * grad_u0 [3][nz][ny][nx] and grad_rho0 [nz][ny][nx] (nullable), both real,
+ * device or host, overwritten, from lambda^0 and the same rho0 (nullable =
+ * 1) and u0 that were passed to lbm_init_equilibrium. */
+lbm_status lbm_adjoint_init_grad(lbm_ctx *ctx, const void *rho0, const void *u0, void *grad_u0,
+                                 void *grad_rho0);
+
+/* Read (and clear, if clear != 0) the device status word; synchronizes. */
+lbm_status lbm_status_word(lbm_ctx *ctx, uint32_t *out, int clear);
+
+/* Block the host until all work enqueued on the context's stream is done. */
+lbm_status lbm_synchronize(lbm_ctx *ctx);
+
+/* Message of the last failed call on this context (empty if none). */
+const char *lbm_last_error(const lbm_ctx *ctx);
+
+/* Name of a status code. */
+const char *lbm_status_string(lbm_status s);
+
+/* The velocity set the kernels were compiled with: e[19*3] (row i = e_i),
+ * w[19], opp[19] (index of -e_i). Returns 19. Needs no GPU. */
+int lbm_lattice_table(int *e, double *w, int *opp);
+
+/* Host-side check of the index arithmetic of every kernel launch the library
+ * makes for an nx * ny * nz lattice in format fmt: walks every thread of each
+ * launch configuration on the CPU and verifies that every address it forms
+ * lies inside its buffer. Returns the number of violations (0 = all in
+ * bounds), or -1 for invalid sizes. Needs no GPU. */
+int64_t lbm_check_launch_indices(int nx, int ny, int nz, lbm_storage fmt);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_CAPI_H */

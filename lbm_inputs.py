@@ -81,18 +81,23 @@ def random_flags(nx, ny, nz, solid_frac, seed):
     return (rng.random((nz, ny, nx)) < solid_frac).astype(np.uint8)
 
 
-def taylor_green(n, U0=0.02):
+def taylor_green(n, U0=0.02, dtype=np.float64):
     """Taylor-Green vortex on a periodic n^3 box, k = 2 pi / n:
     u = U0 sin kx cos ky cos kz, v = -U0 cos kx sin ky cos kz, w = 0,
-    rho = 1 + 3 p with p = (U0^2/16)(cos 2kx + cos 2ky)(cos 2kz + 2)."""
-    k = 2.0 * np.pi / n
-    c = np.arange(n, dtype=np.float64) * k
-    z, y, x = np.meshgrid(c, c, c, indexing="ij")
-    u = np.zeros((3, n, n, n))
-    u[0] = U0 * np.sin(x) * np.cos(y) * np.cos(z)
-    u[1] = -U0 * np.cos(x) * np.sin(y) * np.cos(z)
-    p = (U0 * U0 / 16.0) * (np.cos(2 * x) + np.cos(2 * y)) * (np.cos(2 * z) + 2.0)
-    return 1.0 + 3.0 * p, u
+    rho = 1 + 3 p with p = (U0^2/16)(cos 2kx + cos 2ky)(cos 2kz + 2).
+    Built by broadcasting 1-D factors (no meshgrid), in `dtype`."""
+    c = np.arange(n, dtype=np.float64) * (2.0 * np.pi / n)
+    sx, cx = np.sin(c)[None, None, :], np.cos(c)[None, None, :]
+    sy, cy = np.sin(c)[None, :, None], np.cos(c)[None, :, None]
+    cz = np.cos(c)[:, None, None]
+    c2x, c2y = np.cos(2 * c)[None, None, :], np.cos(2 * c)[None, :, None]
+    c2z = np.cos(2 * c)[:, None, None]
+    u = np.zeros((3, n, n, n), dtype=dtype)
+    u[0] = (U0 * cz * cy) * sx
+    u[1] = (-U0 * cz * sy) * cx
+    rho = np.empty((n, n, n), dtype=dtype)
+    rho[...] = 1.0 + 3.0 * (U0 * U0 / 16.0) * (c2z + 2.0) * (c2x + c2y)
+    return rho, u
 
 
 def solenoidal_velocity(n, amp, seed, kmax=4):

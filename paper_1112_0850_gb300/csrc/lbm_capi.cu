@@ -1,0 +1,624 @@
+// C-ABI of the D3Q19 BGK library (declared in include/lbm_capi.h): context
+// management, argument checks, host/device pointer handling, and dispatch of
+// each call to the kernels of its storage format.
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "lbm_launch.h"
+
+using namespace lbm;
+
+struct lbm_ctx {
+    Geom g;
+    RowLaunch L;
+    lbm_storage storage;
+    double tau;
+    double F[3];
+    cudaStream_t stream;
+    int device;
+    void *lat[2];       // lat[cur] holds the latest post-collision populations
+    int cur;
+    uint8_t *flags_d;   // padded [qs], 1 = solid (padding included), or null
+    void *Ffield_d;     // padded [3][qs] of the arithmetic type, or null
+    void *lam[2];       // adjoint lattices (allocated on first seed)
+    int lcur;
+    bool lam_valid;
+    double *red_partials;  // RED_BLOCKS * 4 doubles
+    double *red_out;       // 4 doubles
+    unsigned *status_d;
+    void *staging;         // device buffer for host-side arrays
+    size_t staging_bytes;
+    int64_t n_fluid;
+    int64_t steps_done;
+    std::string err;
+};
+
+namespace {
+
+const char *status_names[] = {"LBM_OK",    "LBM_ERR_ARG",      "LBM_ERR_OOM",   "LBM_ERR_CUDA",
+                              "LBM_ERR_STATE", "LBM_ERR_DIVERGED", "LBM_ERR_INDEX", "LBM_ERR_UNSUPPORTED"};
+
+lbm_status fail(lbm_ctx *ctx, lbm_status s, const std::string &msg) {
+    if (ctx) ctx->err = msg;
+    return s;
+}
+
+lbm_status cuda_fail(lbm_ctx *ctx, cudaError_t e, const char *what) {
+    return fail(ctx, LBM_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+size_t real_size(lbm_storage s) { return s == LBM_F64 ? 8 : 4; }
+
+bool valid_storage(int s) { return s >= LBM_F64 && s <= LBM_BF16S; }
+
+// Elements per padded row so that each row starts on a 128-byte boundary.
+int pitch_for(int nx, lbm_storage s) {
+    int per = 128 / (int)storage_bytes(s);
+    return (nx + per - 1) / per * per;
+}
+
+bool is_device_ptr(const void *p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+Dev make_dev(const lbm_ctx *ctx) {
+    Dev d;
+    d.g = ctx->g;
+    d.L = ctx->L;
+    d.flags = ctx->flags_d;
+    d.Ffield = ctx->Ffield_d;
+    d.F[0] = ctx->F[0];
+    d.F[1] = ctx->F[1];
+    d.F[2] = ctx->F[2];
+    d.force_on = ctx->Ffield_d != nullptr || ctx->F[0] != 0.0 || ctx->F[1] != 0.0 || ctx->F[2] != 0.0;
+    d.omega = 1.0 / ctx->tau;
+    d.status = ctx->status_d;
+    d.stream = ctx->stream;
+    d.n_cells = (long long)ctx->g.nx * ctx->g.ny * ctx->g.nz;
+    return d;
+}
+
+// Host-pointer handling: each canonical array is either used in place (device)
+// or staged through ctx->staging. Inputs are copied in (and the stream
+// synchronized, so the caller may reuse its host buffer on return); outputs
+// are copied back and the stream synchronized by finish().
+struct Staged {
+    struct Item {
+        const void *user;
+        void *dev;
+        size_t bytes;
+        bool output;
+        bool host;
+    };
+    lbm_ctx *ctx;
+    std::vector<Item> items;
+    explicit Staged(lbm_ctx *c) : ctx(c) {}
+
+    int add(const void *user, size_t bytes, bool output) {
+        Item it{user, const_cast<void *>(user), bytes, output, user && !is_device_ptr(user)};
+        items.push_back(it);
+        return (int)items.size() - 1;
+    }
+    void *dev(int k) { return items[k].dev; }
+
+    lbm_status prepare() {
+        size_t need = 0;
+        for (auto &it : items)
+            if (it.host) need += (it.bytes + 255) / 256 * 256;
+        if (need > ctx->staging_bytes) {
+            if (ctx->staging) cudaFree(ctx->staging);
+            ctx->staging = nullptr;
+            ctx->staging_bytes = 0;
+            cudaError_t e = cudaMalloc(&ctx->staging, need);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                return fail(ctx, LBM_ERR_OOM, "cannot allocate staging buffer for host arrays");
+            }
+            ctx->staging_bytes = need;
+        }
+        size_t off = 0;
+        bool copied_in = false;
+        for (auto &it : items) {
+            if (!it.host) continue;
+            it.dev = static_cast<char *>(ctx->staging) + off;
+            off += (it.bytes + 255) / 256 * 256;
+            if (!it.output) {
+                cudaError_t e = cudaMemcpyAsync(it.dev, it.user, it.bytes, cudaMemcpyHostToDevice, ctx->stream);
+                if (e != cudaSuccess) return cuda_fail(ctx, e, "copy of a host input");
+                copied_in = true;
+            }
+        }
+        if (copied_in) {
+            cudaError_t e = cudaStreamSynchronize(ctx->stream);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "copy of a host input");
+        }
+        return LBM_OK;
+    }
+
+    lbm_status finish() {
+        bool any = false;
+        for (auto &it : items) {
+            if (!it.host || !it.output) continue;
+            cudaError_t e = cudaMemcpyAsync(const_cast<void *>(it.user), it.dev, it.bytes, cudaMemcpyDeviceToHost,
+                                            ctx->stream);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "copy of a host output");
+            any = true;
+        }
+        if (any) {
+            cudaError_t e = cudaStreamSynchronize(ctx->stream);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "copy of a host output");
+        }
+        return LBM_OK;
+    }
+};
+
+#define LBM_DISPATCH(ctx, call)                                             \
+    ((ctx)->storage == LBM_F64    ? Ops<LBM_F64>::call                      \
+     : (ctx)->storage == LBM_F32  ? Ops<LBM_F32>::call                      \
+     : (ctx)->storage == LBM_F16S ? Ops<LBM_F16S>::call                     \
+                                  : Ops<LBM_BF16S>::call)
+
+lbm_status check_ctx(const lbm_ctx *ctx) {
+    if (!ctx) return LBM_ERR_ARG;
+    cudaSetDevice(ctx->device);
+    return LBM_OK;
+}
+
+void free_ctx(lbm_ctx *ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    void *ptrs[] = {ctx->lat[0], ctx->lat[1], ctx->flags_d,      ctx->Ffield_d, ctx->lam[0],
+                    ctx->lam[1], ctx->red_partials, ctx->red_out, ctx->status_d, ctx->staging};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    delete ctx;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_options_default(lbm_options *opt) {
+    if (!opt) return LBM_ERR_ARG;
+    opt->storage = LBM_F32;
+    opt->cuda_stream = nullptr;
+    return LBM_OK;
+}
+
+lbm_status lbm_create(lbm_ctx **out, int nx, int ny, int nz, double tau, const uint8_t *flags,
+                      const double force[3], const lbm_options *opt) {
+    if (!out) return LBM_ERR_ARG;
+    *out = nullptr;
+    lbm_options o;
+    lbm_options_default(&o);
+    if (opt) o = *opt;
+    if (nx < 1 || ny < 1 || nz < 1 || nz > 65535 || !(tau > 0.5) || !valid_storage(o.storage))
+        return LBM_ERR_ARG;
+    const int pitch = pitch_for(nx, o.storage);
+    const long long qs = (long long)nz * ny * pitch;
+    if (qs >= (1LL << 31)) return LBM_ERR_ARG;
+    const long long N = (long long)nx * ny * nz;
+
+    lbm_ctx *ctx = new lbm_ctx();
+    memset(&ctx->g, 0, sizeof(ctx->g));
+    ctx->g.nx = nx;
+    ctx->g.ny = ny;
+    ctx->g.nz = nz;
+    ctx->g.pitch = pitch;
+    ctx->g.qs = qs;
+    ctx->L = row_launch(ctx->g);
+    ctx->storage = o.storage;
+    ctx->tau = tau;
+    for (int a = 0; a < 3; ++a) ctx->F[a] = force ? force[a] : 0.0;
+    ctx->stream = static_cast<cudaStream_t>(o.cuda_stream);
+    ctx->lat[0] = ctx->lat[1] = nullptr;
+    ctx->cur = 0;
+    ctx->flags_d = nullptr;
+    ctx->Ffield_d = nullptr;
+    ctx->lam[0] = ctx->lam[1] = nullptr;
+    ctx->lcur = 0;
+    ctx->lam_valid = false;
+    ctx->red_partials = ctx->red_out = nullptr;
+    ctx->status_d = nullptr;
+    ctx->staging = nullptr;
+    ctx->staging_bytes = 0;
+    ctx->steps_done = 0;
+    cudaError_t e = cudaGetDevice(&ctx->device);
+    if (e != cudaSuccess) {
+        delete ctx;
+        return LBM_ERR_CUDA;
+    }
+
+    const size_t lat_bytes = (size_t)Q * (size_t)qs * storage_bytes(o.storage);
+    size_t free_b = 0, total_b = 0;
+    e = cudaMemGetInfo(&free_b, &total_b);
+    if (e != cudaSuccess) {
+        delete ctx;
+        return LBM_ERR_CUDA;
+    }
+    const size_t need = 2 * lat_bytes + (size_t)qs + ((size_t)RED_BLOCKS * 4 + 8) * sizeof(double);
+    if (need > free_b) {
+        delete ctx;
+        return LBM_ERR_OOM;
+    }
+
+    // Flags: padded copy (padding marked solid) and the fluid-cell count.
+    std::vector<uint8_t> hflags;
+    int64_t n_fluid = N;
+    if (flags) {
+        std::vector<uint8_t> canon((size_t)N);
+        if (is_device_ptr(flags)) {
+            e = cudaMemcpy(canon.data(), flags, (size_t)N, cudaMemcpyDeviceToHost);
+            if (e != cudaSuccess) {
+                delete ctx;
+                return LBM_ERR_CUDA;
+            }
+        } else {
+            memcpy(canon.data(), flags, (size_t)N);
+        }
+        hflags.assign((size_t)qs, 1);
+        n_fluid = 0;
+        for (long long z = 0; z < nz; ++z)
+            for (long long y = 0; y < ny; ++y)
+                for (long long x = 0; x < nx; ++x) {
+                    uint8_t f = canon[(size_t)(x + nx * (y + ny * z))] ? 1 : 0;
+                    hflags[(size_t)((z * ny + y) * pitch + x)] = f;
+                    n_fluid += f ? 0 : 1;
+                }
+    }
+    ctx->n_fluid = n_fluid;
+
+    bool ok = cudaMalloc(&ctx->lat[0], lat_bytes) == cudaSuccess &&
+              cudaMalloc(&ctx->lat[1], lat_bytes) == cudaSuccess &&
+              cudaMalloc((void **)&ctx->red_partials, (size_t)RED_BLOCKS * 4 * sizeof(double)) == cudaSuccess &&
+              cudaMalloc((void **)&ctx->red_out, 4 * sizeof(double)) == cudaSuccess &&
+              cudaMalloc((void **)&ctx->status_d, sizeof(unsigned)) == cudaSuccess;
+    if (ok && flags) ok = cudaMalloc((void **)&ctx->flags_d, (size_t)qs) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        free_ctx(ctx);
+        return LBM_ERR_OOM;
+    }
+    ok = cudaMemsetAsync(ctx->lat[0], 0, lat_bytes, ctx->stream) == cudaSuccess &&
+         cudaMemsetAsync(ctx->lat[1], 0, lat_bytes, ctx->stream) == cudaSuccess &&
+         cudaMemsetAsync(ctx->status_d, 0, sizeof(unsigned), ctx->stream) == cudaSuccess;
+    if (ok && flags) ok = cudaMemcpy(ctx->flags_d, hflags.data(), (size_t)qs, cudaMemcpyHostToDevice) == cudaSuccess;
+    if (ok) ok = cudaStreamSynchronize(ctx->stream) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        free_ctx(ctx);
+        return LBM_ERR_CUDA;
+    }
+    *out = ctx;
+    return LBM_OK;
+}
+
+void lbm_destroy(lbm_ctx *ctx) { free_ctx(ctx); }
+
+lbm_status lbm_get_info(const lbm_ctx *ctx, lbm_info *info) {
+    if (!ctx || !info) return LBM_ERR_ARG;
+    info->nx = ctx->g.nx;
+    info->ny = ctx->g.ny;
+    info->nz = ctx->g.nz;
+    info->pitch = ctx->g.pitch;
+    info->storage = ctx->storage;
+    info->real_size = (int)real_size(ctx->storage);
+    info->tau = ctx->tau;
+    info->n_cells = (int64_t)ctx->g.nx * ctx->g.ny * ctx->g.nz;
+    info->n_fluid = ctx->n_fluid;
+    info->lattice_bytes = (size_t)Q * (size_t)ctx->g.qs * storage_bytes(ctx->storage);
+    info->tape_bytes_per_step = 4 * (size_t)ctx->g.qs * real_size(ctx->storage);
+    info->steps_done = ctx->steps_done;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_uniform_force(lbm_ctx *ctx, const double force[3]) {
+    if (check_ctx(ctx)) return LBM_ERR_ARG;
+    for (int a = 0; a < 3; ++a) ctx->F[a] = force ? force[a] : 0.0;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_force_field(lbm_ctx *ctx, const void *F) {
+    if (check_ctx(ctx)) return LBM_ERR_ARG;
+    if (!F) {
+        if (ctx->Ffield_d) {
+            cudaStreamSynchronize(ctx->stream);
+            cudaFree(ctx->Ffield_d);
+        }
+        ctx->Ffield_d = nullptr;
+        return LBM_OK;
+    }
+    const size_t rs = real_size(ctx->storage);
+    if (!ctx->Ffield_d) {
+        cudaError_t e = cudaMalloc(&ctx->Ffield_d, 3 * (size_t)ctx->g.qs * rs);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            ctx->Ffield_d = nullptr;
+            return fail(ctx, LBM_ERR_OOM, "cannot allocate the force field");
+        }
+        e = cudaMemsetAsync(ctx->Ffield_d, 0, 3 * (size_t)ctx->g.qs * rs, ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "clear force field");
+    }
+    // canonical rows of nx reals -> padded rows of pitch reals
+    cudaError_t e = cudaMemcpy2DAsync(ctx->Ffield_d, (size_t)ctx->g.pitch * rs, F, (size_t)ctx->g.nx * rs,
+                                      (size_t)ctx->g.nx * rs, (size_t)3 * ctx->g.ny * ctx->g.nz, cudaMemcpyDefault,
+                                      ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "copy of the force field");
+    if (!is_device_ptr(F)) {
+        e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "copy of the force field");
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_init_equilibrium(lbm_ctx *ctx, const void *rho, const void *u) {
+    if (check_ctx(ctx)) return LBM_ERR_ARG;
+    if (!u) return fail(ctx, LBM_ERR_ARG, "u is required");
+    const size_t N = (size_t)ctx->g.nx * ctx->g.ny * ctx->g.nz, rs = real_size(ctx->storage);
+    Staged st(ctx);
+    int ir = rho ? st.add(rho, N * rs, false) : -1;
+    int iu = st.add(u, 3 * N * rs, false);
+    lbm_status s = st.prepare();
+    if (s) return s;
+    Dev d = make_dev(ctx);
+    cudaError_t e = LBM_DISPATCH(ctx, init_eq(d, ctx->lat[ctx->cur], ir >= 0 ? st.dev(ir) : nullptr, st.dev(iu)));
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "init_equilibrium launch");
+    ctx->steps_done = 0;
+    ctx->lam_valid = false;
+    return LBM_OK;
+}
+
+lbm_status lbm_step(lbm_ctx *ctx, int n) {
+    if (check_ctx(ctx)) return LBM_ERR_ARG;
+    if (n < 0) return fail(ctx, LBM_ERR_ARG, "n must be >= 0");
+    Dev d = make_dev(ctx);
+    for (int k = 0; k < n; ++k) {
+        cudaError_t e = LBM_DISPATCH(ctx, step(d, ctx->lat[ctx->cur], ctx->lat[ctx->cur ^ 1], nullptr));
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "stream-collide launch");
+        ctx->cur ^= 1;
+        ctx->steps_done++;
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_step_record(lbm_ctx *ctx, int n, void *tape) {
+    if (check_ctx(ctx)) return LBM_ERR_ARG;
+    if (n < 0) return fail(ctx, LBM_ERR_ARG, "n must be >= 0");
+    if (n > 0 && (!tape || !is_device_ptr(tape))) return fail(ctx, LBM_ERR_ARG, "tape must be a device array");
+    const size_t per = 4 * (size_t)ctx->g.qs * real_size(ctx->storage);
+    Dev d = make_dev(ctx);
+    for (int k = 0; k < n; ++k) {
+        void *tk = static_cast<char *>(tape) + per * (size_t)k;
+        cudaError_t e = LBM_DISPATCH(ctx, step(d, ctx->lat[ctx->cur], ctx->lat[ctx->cur ^ 1], tk));
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "stream-collide (record) launch");
+        ctx->cur ^= 1;
+        ctx->steps_done++;
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_macros(lbm_ctx *ctx, void *rho, void *u) {
+    if (check_ctx(ctx)) return LBM_ERR_ARG;
+    if (!u) return fail(ctx, LBM_ERR_ARG, "u is required");
+    const size_t N = (size_t)ctx->g.nx * ctx->g.ny * ctx->g.nz, rs = real_size(ctx->storage);
+    Staged st(ctx);
+    int ir = rho ? st.add(rho, N * rs, true) : -1;
+    int iu = st.add(u, 3 * N * rs, true);
+    lbm_status s = st.prepare();
+    if (s) return s;
+    Dev d = make_dev(ctx);
+    cudaError_t e = LBM_DISPATCH(ctx, macros(d, ctx->lat[ctx->cur], ir >= 0 ? st.dev(ir) : nullptr, st.dev(iu)));
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "macros launch");
+    return st.finish();
+}
+
+lbm_status lbm_reduce(lbm_ctx *ctx, double out[4]) {
+    if (check_ctx(ctx)) return LBM_ERR_ARG;
+    if (!out) return fail(ctx, LBM_ERR_ARG, "out is required");
+    Dev d = make_dev(ctx);
+    cudaError_t e = LBM_DISPATCH(ctx, reduce(d, ctx->lat[ctx->cur], ctx->red_partials, ctx->red_out));
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "reduce launch");
+    e = cudaMemcpyAsync(out, ctx->red_out, 4 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "reduce result copy");
+    return LBM_OK;
+}
+
+lbm_status lbm_get_state(lbm_ctx *ctx, void *dst, lbm_storage fmt) {
+    if (check_ctx(ctx)) return LBM_ERR_ARG;
+    if (!dst || !valid_storage(fmt)) return fail(ctx, LBM_ERR_ARG, "bad destination or format");
+    const size_t N = (size_t)ctx->g.nx * ctx->g.ny * ctx->g.nz;
+    Staged st(ctx);
+    int k = st.add(dst, (size_t)Q * N * storage_bytes(fmt), true);
+    lbm_status s = st.prepare();
+    if (s) return s;
+    Dev d = make_dev(ctx);
+    cudaError_t e = LBM_DISPATCH(ctx, get_state(d, ctx->lat[ctx->cur], st.dev(k), (int)fmt));
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "get_state launch");
+    return st.finish();
+}
+
+lbm_status lbm_set_state(lbm_ctx *ctx, const void *src, lbm_storage fmt) {
+    if (check_ctx(ctx)) return LBM_ERR_ARG;
+    if (!src || !valid_storage(fmt)) return fail(ctx, LBM_ERR_ARG, "bad source or format");
+    const size_t N = (size_t)ctx->g.nx * ctx->g.ny * ctx->g.nz;
+    Staged st(ctx);
+    int k = st.add(src, (size_t)Q * N * storage_bytes(fmt), false);
+    lbm_status s = st.prepare();
+    if (s) return s;
+    Dev d = make_dev(ctx);
+    cudaError_t e = LBM_DISPATCH(ctx, set_state(d, ctx->lat[ctx->cur], st.dev(k), (int)fmt));
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "set_state launch");
+    ctx->steps_done = 0;
+    return LBM_OK;
+}
+
+static lbm_status ensure_lambda(lbm_ctx *ctx) {
+    const size_t bytes = (size_t)Q * (size_t)ctx->g.qs * real_size(ctx->storage);
+    for (int k = 0; k < 2; ++k) {
+        if (ctx->lam[k]) continue;
+        cudaError_t e = cudaMalloc(&ctx->lam[k], bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            ctx->lam[k] = nullptr;
+            return fail(ctx, LBM_ERR_OOM, "cannot allocate the adjoint lattices");
+        }
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_adjoint_seed(lbm_ctx *ctx, const void *dL_du, const void *dL_drho, void *grad_F) {
+    if (check_ctx(ctx)) return LBM_ERR_ARG;
+    if (!dL_du) return fail(ctx, LBM_ERR_ARG, "dL_du is required");
+    if (grad_F && !is_device_ptr(grad_F)) return fail(ctx, LBM_ERR_ARG, "grad_F must be a device array");
+    lbm_status s = ensure_lambda(ctx);
+    if (s) return s;
+    const size_t N = (size_t)ctx->g.nx * ctx->g.ny * ctx->g.nz, rs = real_size(ctx->storage);
+    Staged st(ctx);
+    int iu = st.add(dL_du, 3 * N * rs, false);
+    int ir = dL_drho ? st.add(dL_drho, N * rs, false) : -1;
+    s = st.prepare();
+    if (s) return s;
+    Dev d = make_dev(ctx);
+    cudaError_t e = LBM_DISPATCH(ctx, adj_seed(d, ctx->lat[ctx->cur], st.dev(iu), ir >= 0 ? st.dev(ir) : nullptr,
+                                               ctx->lam[ctx->lcur], grad_F));
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "adjoint seed launch");
+    ctx->lam_valid = true;
+    return LBM_OK;
+}
+
+lbm_status lbm_adjoint_step(lbm_ctx *ctx, int n, const void *tape, void *grad_F) {
+    if (check_ctx(ctx)) return LBM_ERR_ARG;
+    if (n < 0) return fail(ctx, LBM_ERR_ARG, "n must be >= 0");
+    if (!ctx->lam_valid) return fail(ctx, LBM_ERR_STATE, "lbm_adjoint_seed must come first");
+    if (n > 0 && (!tape || !is_device_ptr(tape))) return fail(ctx, LBM_ERR_ARG, "tape must be a device array");
+    if (grad_F && !is_device_ptr(grad_F)) return fail(ctx, LBM_ERR_ARG, "grad_F must be a device array");
+    const size_t per = 4 * (size_t)ctx->g.qs * real_size(ctx->storage);
+    Dev d = make_dev(ctx);
+    for (int k = n - 1; k >= 0; --k) {
+        const void *tk = static_cast<const char *>(tape) + per * (size_t)k;
+        cudaError_t e = ctx->storage == LBM_F64
+                            ? AdjOps<double>::step(d, ctx->lam[ctx->lcur], ctx->lam[ctx->lcur ^ 1], tk, grad_F)
+                            : AdjOps<float>::step(d, ctx->lam[ctx->lcur], ctx->lam[ctx->lcur ^ 1], tk, grad_F);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "adjoint step launch");
+        ctx->lcur ^= 1;
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_adjoint_init_grad(lbm_ctx *ctx, const void *rho0, const void *u0, void *grad_u0, void *grad_rho0) {
+    if (check_ctx(ctx)) return LBM_ERR_ARG;
+    if (!u0 || !grad_u0) return fail(ctx, LBM_ERR_ARG, "u0 and grad_u0 are required");
+    if (!ctx->lam_valid) return fail(ctx, LBM_ERR_STATE, "lbm_adjoint_seed must come first");
+    const size_t N = (size_t)ctx->g.nx * ctx->g.ny * ctx->g.nz, rs = real_size(ctx->storage);
+    Staged st(ctx);
+    int ir = rho0 ? st.add(rho0, N * rs, false) : -1;
+    int iu = st.add(u0, 3 * N * rs, false);
+    int ig = st.add(grad_u0, 3 * N * rs, true);
+    int igr = grad_rho0 ? st.add(grad_rho0, N * rs, true) : -1;
+    lbm_status s = st.prepare();
+    if (s) return s;
+    Dev d = make_dev(ctx);
+    const void *r = ir >= 0 ? st.dev(ir) : nullptr;
+    void *gr = igr >= 0 ? st.dev(igr) : nullptr;
+    cudaError_t e = ctx->storage == LBM_F64
+                        ? AdjOps<double>::init_grad(d, ctx->lam[ctx->lcur], r, st.dev(iu), st.dev(ig), gr)
+                        : AdjOps<float>::init_grad(d, ctx->lam[ctx->lcur], r, st.dev(iu), st.dev(ig), gr);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "adjoint init-grad launch");
+    return st.finish();
+}
+
+lbm_status lbm_status_word(lbm_ctx *ctx, uint32_t *out, int clear) {
+    if (check_ctx(ctx) || !out) return LBM_ERR_ARG;
+    unsigned v = 0;
+    cudaError_t e = cudaMemcpyAsync(&v, ctx->status_d, sizeof(unsigned), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e == cudaSuccess && clear) e = cudaMemsetAsync(ctx->status_d, 0, sizeof(unsigned), ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "status word");
+    *out = v;
+    return LBM_OK;
+}
+
+lbm_status lbm_synchronize(lbm_ctx *ctx) {
+    if (check_ctx(ctx)) return LBM_ERR_ARG;
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "synchronize");
+    return LBM_OK;
+}
+
+const char *lbm_last_error(const lbm_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+const char *lbm_status_string(lbm_status s) {
+    return (s >= LBM_OK && s <= LBM_ERR_UNSUPPORTED) ? status_names[s] : "unknown status";
+}
+
+int lbm_lattice_table(int *e, double *w, int *o) {
+    for (int i = 0; i < Q; ++i) {
+        if (e) {
+            e[3 * i] = ex(i);
+            e[3 * i + 1] = ey(i);
+            e[3 * i + 2] = ez(i);
+        }
+        if (w) w[i] = weight(i);
+        if (o) o[i] = opp(i);
+    }
+    return Q;
+}
+
+// Walk every thread of the row launch (and the reduction's cell loop) on the
+// host, forming the same addresses as the kernels with the same helpers.
+int64_t lbm_check_launch_indices(int nx, int ny, int nz, lbm_storage fmt) {
+    if (nx < 1 || ny < 1 || nz < 1 || nz > 65535 || !valid_storage(fmt)) return -1;
+    Geom g;
+    g.nx = nx;
+    g.ny = ny;
+    g.nz = nz;
+    g.pitch = pitch_for(nx, fmt);
+    g.qs = (long long)nz * ny * g.pitch;
+    if (g.qs >= (1LL << 31)) return -1;
+    const RowLaunch L = row_launch(g);
+    const long long N = (long long)nx * ny * nz;
+    int64_t bad = 0;
+    auto cell_ok = [&](int c) { return c >= 0 && c < g.qs && (c % g.pitch) < nx; };
+    long long visited = 0;
+    for (int bz = 0; bz < nz; ++bz)
+        for (int bx = 0; bx < L.nxb * L.nyb; ++bx)
+            for (int ty = 0; ty < L.by_threads; ++ty)
+                for (int tx = 0; tx < L.bx_threads; ++tx) {
+                    int x, y, z;
+                    if (!row_cell(g, L.nxb, L.bx_threads, L.by_threads, bx, bz, tx, ty, x, y, z)) continue;
+                    ++visited;
+                    const int c = cell_index(g, x, y, z);
+                    if (!cell_ok(c)) ++bad;
+                    const long long cc = canon_index(g, x, y, z);
+                    if (cc < 0 || cc >= N) ++bad;
+                    for (int i = 0; i < Q; ++i) {
+                        if (!cell_ok(pull_src(g, x, y, z, i))) ++bad;
+                        if (!cell_ok(push_dst(g, x, y, z, i))) ++bad;
+                        const long long cn = canon_index(g, wrap1(x + ex(i), nx), wrap1(y + ey(i), ny),
+                                                         wrap1(z + ez(i), nz));
+                        if (cn < 0 || cn >= N) ++bad;
+                        if ((long long)opp(i) * g.qs + c >= (long long)Q * g.qs) ++bad;
+                    }
+                }
+    if (visited != N) ++bad;  // every cell owned by exactly one thread
+    if (L.bx_threads * L.by_threads != 256 || L.bx_threads % 32) ++bad;
+    // reduction: canonical walk
+    for (long long cc = 0; cc < N; ++cc) {
+        const int x = (int)(cc % nx);
+        const long long r = cc / nx;
+        const int y = (int)(r % ny), z = (int)(r / ny);
+        if (!cell_ok(cell_index(g, x, y, z))) ++bad;
+    }
+    return bad;
+}
+
+}  // extern "C"

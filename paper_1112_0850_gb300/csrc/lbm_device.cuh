@@ -1,0 +1,211 @@
+// Device-side building blocks of the D3Q19 BGK kernels: the lattice table,
+// population storage formats, the padded structure-of-arrays geometry and the
+// per-cell collision (Sec. 2 of Habich et al.; Eq. 1 with the Qian
+// equilibrium and, as this library's reading, the Guo body force).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/lbm_capi.h"
+
+#define LBM_HD __host__ __device__ __forceinline__
+
+namespace lbm {
+
+constexpr int Q = 19;
+
+// Velocity set, in the order documented in lbm_capi.h: component a of e_i is
+// stored as a + 1 in bits 2i..2i+1 of one 64-bit constant per axis, so that
+// host and device code fold ex(i), ey(i), ez(i) to literals once loops unroll.
+LBM_HD constexpr int ex(int i) { return int((0x1542829549ULL >> (2 * i)) & 3ULL) - 1; }
+LBM_HD constexpr int ey(int i) { return int((0x295489495ULL >> (2 * i)) & 3ULL) - 1; }
+LBM_HD constexpr int ez(int i) { return int((0x888954955ULL >> (2 * i)) & 3ULL) - 1; }
+
+// Index of -e_i: axis pairs (1,2), (3,4), (5,6); the diagonals come in groups
+// of four (7-10, 11-14, 15-18) where member k pairs with member 3 - k.
+LBM_HD constexpr int opp(int i) {
+    return i == 0 ? 0
+                  : (i <= 6 ? ((i & 1) ? i + 1 : i - 1)
+                            : (7 + 4 * ((i - 7) / 4)) + 3 - (i - (7 + 4 * ((i - 7) / 4))));
+}
+
+LBM_HD constexpr double weight(int i) { return i == 0 ? 1.0 / 3.0 : (i <= 6 ? 1.0 / 18.0 : 1.0 / 36.0); }
+
+// The nine opposite pairs (i, opp(i)) with i the member listed first.
+constexpr int NPAIR = 9;
+LBM_HD constexpr int pair_first(int p) { return p < 3 ? 1 + 2 * p : (p < 5 ? 4 + p : (p < 7 ? 6 + p : 8 + p)); }
+
+// ---------------------------------------------------------------------------
+// Storage formats. Every format stores the shifted deviation s = f - w.
+// R is the arithmetic type (double for LBM_F64, float otherwise).
+template <int S> struct Stor;
+
+template <> struct Stor<LBM_F64> {
+    typedef double T;
+    typedef double R;
+    static __device__ __forceinline__ R ld(const T *p) { return __ldg(p); }
+    static __device__ __forceinline__ void st(T *p, R v) { __stcs(p, v); }
+    static __device__ __forceinline__ T enc(R v) { return v; }
+};
+
+template <> struct Stor<LBM_F32> {
+    typedef float T;
+    typedef float R;
+    static __device__ __forceinline__ R ld(const T *p) { return __ldg(p); }
+    static __device__ __forceinline__ void st(T *p, R v) { __stcs(p, v); }
+    static __device__ __forceinline__ T enc(R v) { return v; }
+};
+
+template <> struct Stor<LBM_F16S> {
+    typedef __half T;
+    typedef float R;
+    static __device__ __forceinline__ R ld(const T *p) {
+        return __half2float(__ushort_as_half(__ldg(reinterpret_cast<const unsigned short *>(p))));
+    }
+    static __device__ __forceinline__ void st(T *p, R v) {
+        __stcs(reinterpret_cast<unsigned short *>(p), __half_as_ushort(__float2half_rn(v)));
+    }
+    static __device__ __forceinline__ T enc(R v) { return __float2half_rn(v); }
+};
+
+template <> struct Stor<LBM_BF16S> {
+    typedef __nv_bfloat16 T;
+    typedef float R;
+    static __device__ __forceinline__ R ld(const T *p) {
+        return __bfloat162float(
+            __ushort_as_bfloat16(__ldg(reinterpret_cast<const unsigned short *>(p))));
+    }
+    static __device__ __forceinline__ void st(T *p, R v) {
+        __stcs(reinterpret_cast<unsigned short *>(p), __bfloat16_as_ushort(__float2bfloat16_rn(v)));
+    }
+    static __device__ __forceinline__ T enc(R v) { return __float2bfloat16_rn(v); }
+};
+
+inline size_t storage_bytes(lbm_storage s) { return s == LBM_F64 ? 8 : (s == LBM_F32 ? 4 : 2); }
+
+// ---------------------------------------------------------------------------
+// Geometry of the padded structure-of-arrays store: population i of cell
+// (x, y, z) lives at base + i * qs + (z * ny + y) * pitch + x. Rows are padded
+// to `pitch` elements so that each starts on a 128-byte boundary (Sec. 6,
+// padding cells after each stripe); padding cells are never computed.
+struct Geom {
+    int nx, ny, nz, pitch;
+    long long qs;  // nz * ny * pitch: elements per population array (< 2^31)
+};
+
+LBM_HD int wrap1(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
+
+LBM_HD int cell_index(const Geom &g, int x, int y, int z) { return (z * g.ny + y) * g.pitch + x; }
+
+// Row-oriented launch: block (bx, by) = (x_block + nxb * y_group, z), threads
+// (tx, ty); each thread owns one cell. Used by every per-cell kernel.
+struct RowLaunch {
+    int bx_threads, by_threads;  // block shape
+    int nxb, nyb;                // x blocks per row, y groups
+};
+
+inline RowLaunch row_launch(const Geom &g) {
+    RowLaunch L;
+    int w = 32;  // power of two in [32, 256] covering a row, so blocks hold 256 threads
+    while (w < g.nx && w < 256) w *= 2;
+    L.bx_threads = w;
+    L.by_threads = 256 / w;
+    L.nxb = (g.nx + w - 1) / w;
+    L.nyb = (g.ny + L.by_threads - 1) / L.by_threads;
+    return L;
+}
+
+// Cell owned by thread (tx, ty) of block (bx, bz); false for threads past the edge.
+LBM_HD bool row_cell(const Geom &g, int nxb, int bdx, int bdy, int bx, int bz, int tx, int ty,
+                     int &x, int &y, int &z) {
+    int xb = bx % nxb;
+    int yg = bx / nxb;
+    x = xb * bdx + tx;
+    y = yg * bdy + ty;
+    z = bz;
+    return x < g.nx && y < g.ny && z < g.nz;
+}
+
+// Index of the cell (x + dx, y + dy, z + dz), periodic, |d| <= 1.
+LBM_HD int neighbor_index(const Geom &g, int x, int y, int z, int dx, int dy, int dz) {
+    return cell_index(g, wrap1(x + dx, g.nx), wrap1(y + dy, g.ny), wrap1(z + dz, g.nz));
+}
+
+// Cell that population i of cell (x, y, z) is pulled from: x - e_i.
+LBM_HD int pull_src(const Geom &g, int x, int y, int z, int i) {
+    return neighbor_index(g, x, y, z, -ex(i), -ey(i), -ez(i));
+}
+
+// Cell that population i of cell (x, y, z) streams to: x + e_i.
+LBM_HD int push_dst(const Geom &g, int x, int y, int z, int i) {
+    return neighbor_index(g, x, y, z, ex(i), ey(i), ez(i));
+}
+
+// Canonical (unpadded) index of cell (x, y, z).
+LBM_HD long long canon_index(const Geom &g, int x, int y, int z) {
+    return (long long)x + (long long)g.nx * ((long long)y + (long long)g.ny * z);
+}
+
+// ---------------------------------------------------------------------------
+// Collision of one cell in shifted form (Eq. 1, Qian equilibrium, Guo force):
+//   rho - 1 = sum s_i,  j = sum s_i e_i,  u = (j + F/2) / rho
+//   s*_i = s_i + omega (seq_i - s_i) + S_i,
+//   seq_i = f_eq_i - w_i = w_i [(rho - 1) + rho (3 e.u + 9/2 (e.u)^2 - 3/2 u.u)]
+//   S_i = (1 - omega/2) w_i [3 (e_i - u) + 9 (e_i.u) e_i] . F
+// Opposite directions share the even part and flip the odd part.
+template <class R> struct Mom {
+    R rho1, rho, ux, uy, uz;
+};
+
+template <class R>
+__device__ __forceinline__ Mom<R> moments(const R s[Q], R Fx, R Fy, R Fz) {
+    Mom<R> m;
+    R r = s[0];
+#pragma unroll
+    for (int i = 1; i < Q; ++i) r += s[i];
+    R jx = (s[1] - s[2]) + (s[7] - s[10]) + (s[8] - s[9]) + (s[11] - s[14]) + (s[12] - s[13]);
+    R jy = (s[3] - s[4]) + (s[7] - s[10]) + (s[9] - s[8]) + (s[15] - s[18]) + (s[16] - s[17]);
+    R jz = (s[5] - s[6]) + (s[11] - s[14]) + (s[13] - s[12]) + (s[15] - s[18]) + (s[17] - s[16]);
+    m.rho1 = r;
+    m.rho = R(1) + r;
+    R inv = R(1) / m.rho;
+    m.ux = (jx + R(0.5) * Fx) * inv;
+    m.uy = (jy + R(0.5) * Fy) * inv;
+    m.uz = (jz + R(0.5) * Fz) * inv;
+    return m;
+}
+
+template <class R, bool FORCE>
+__device__ __forceinline__ void collide(R s[Q], const Mom<R> &m, R omega, R Fx, R Fy, R Fz) {
+    const R usq15 = R(1.5) * (m.ux * m.ux + m.uy * m.uy + m.uz * m.uz);
+    const R cF = R(1) - R(0.5) * omega;
+    const R uF = FORCE ? (m.ux * Fx + m.uy * Fy + m.uz * Fz) : R(0);
+    {
+        const R w = R(1.0 / 3.0);
+        R seq = w * (m.rho1 - m.rho * usq15);
+        R src = FORCE ? cF * w * (R(-3) * uF) : R(0);
+        s[0] = s[0] + omega * (seq - s[0]) + src;
+    }
+#pragma unroll
+    for (int p = 0; p < NPAIR; ++p) {
+        const int i = pair_first(p), o = opp(i);
+        const R w = i <= 6 ? R(1.0 / 18.0) : R(1.0 / 36.0);
+        const R eu = R(ex(i)) * m.ux + R(ey(i)) * m.uy + R(ez(i)) * m.uz;
+        const R even = w * (m.rho1 + m.rho * (R(4.5) * eu * eu - usq15));
+        const R odd = w * R(3) * m.rho * eu;
+        R fe = R(0), fo = R(0);
+        if (FORCE) {
+            const R eF = R(ex(i)) * Fx + R(ey(i)) * Fy + R(ez(i)) * Fz;
+            fe = cF * w * (R(9) * eu * eF - R(3) * uF);
+            fo = cF * w * R(3) * eF;
+        }
+        const R a = s[i], b = s[o];
+        s[i] = a + omega * (even + odd - a) + (fe + fo);
+        s[o] = b + omega * (even - odd - b) + (fe - fo);
+    }
+}
+
+}  // namespace lbm

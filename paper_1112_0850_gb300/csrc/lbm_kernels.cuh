@@ -1,0 +1,468 @@
+// Kernels of the D3Q19 BGK path, templated on the population storage format.
+// Included by one translation unit per format (lbm_ops_*.cu), which
+// instantiates Ops<S>.
+//
+// Data layout (HBM): two padded structure-of-arrays lattices of 19 arrays
+// each, P[i][z][y][pitch]; the kernels keep the post-collision populations
+// P^n at the cell where they were computed and gather them at the start of
+// the next step (Sec. 6: loads from the neighbours, aligned coalesced stores
+// to the local cell, two grids). With halfway bounce-back folded into the
+// gather (Sec. 2: bounce-back combined with streaming):
+//   f^{n+1}_i(x) = P^n_i(x - e_i)        if x - e_i is fluid
+//                = P^n_{opp(i)}(x)        otherwise.
+#pragma once
+
+#include "lbm_launch.h"
+
+namespace lbm {
+
+// Element access of canonical arrays in a storage format (values are
+// converted through double, rounding to nearest even when narrowing).
+template <int D> struct IOFmt;
+template <> struct IOFmt<LBM_F64> {
+    typedef double T;
+    static __device__ __forceinline__ double get(const T *p) { return *p; }
+    static __device__ __forceinline__ void put(T *p, double v) { *p = v; }
+};
+template <> struct IOFmt<LBM_F32> {
+    typedef float T;
+    static __device__ __forceinline__ double get(const T *p) { return (double)*p; }
+    static __device__ __forceinline__ void put(T *p, double v) { *p = __double2float_rn(v); }
+};
+template <> struct IOFmt<LBM_F16S> {
+    typedef __half T;
+    static __device__ __forceinline__ double get(const T *p) { return (double)__half2float(*p); }
+    static __device__ __forceinline__ void put(T *p, double v) { *p = __double2half(v); }
+};
+template <> struct IOFmt<LBM_BF16S> {
+    typedef __nv_bfloat16 T;
+    static __device__ __forceinline__ double get(const T *p) { return (double)__bfloat162float(*p); }
+    static __device__ __forceinline__ void put(T *p, double v) { *p = __double2bfloat16(v); }
+};
+
+__device__ __forceinline__ bool is_solid(const uint8_t *flags, int c) { return flags && flags[c]; }
+
+template <class R> __device__ __forceinline__ void force_at(const Dev &d, int c, R &Fx, R &Fy, R &Fz) {
+    if (d.Ffield) {
+        const R *F = static_cast<const R *>(d.Ffield);
+        Fx = F[c];
+        Fy = F[d.g.qs + c];
+        Fz = F[2 * d.g.qs + c];
+    } else {
+        Fx = R(d.F[0]);
+        Fy = R(d.F[1]);
+        Fz = R(d.F[2]);
+    }
+}
+
+// Gather the 19 pre-collision populations of fluid cell (x, y, z) from P.
+template <int S, bool FLAGS>
+__device__ __forceinline__ void gather(const Dev &d, const typename Stor<S>::T *P, int x, int y, int z,
+                                       int c, typename Stor<S>::R s[Q]) {
+    const long long qs = d.g.qs;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        int src = pull_src(d.g, x, y, z, i);
+        long long off = (long long)i * qs + src;
+        if (FLAGS && i > 0 && d.flags[src]) off = (long long)opp(i) * qs + c;
+        s[i] = Stor<S>::ld(P + off);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Fused stream-collide (Sec. 2 steps 1-3, Eq. 1; Sec. 6 pull-style update).
+// Resident blocks of 256 threads per SM the step kernels are compiled for:
+// 4 (<= 64 registers) for FP32 arithmetic, 2 (<= 128) for FP64.
+template <class R> struct MinBlocks {
+    static constexpr int value = sizeof(R) == 8 ? 2 : 4;
+};
+
+template <int S, bool FLAGS, int FORCE, bool RECORD>
+__global__ void __launch_bounds__(256, MinBlocks<typename Stor<S>::R>::value)
+    k_step(const Dev d, const typename Stor<S>::T *__restrict__ src, typename Stor<S>::T *__restrict__ dst,
+           typename Stor<S>::R *__restrict__ tape) {
+    typedef typename Stor<S>::R R;
+    int x, y, z;
+    if (!row_cell(d.g, d.L.nxb, blockDim.x, blockDim.y, blockIdx.x, blockIdx.y, threadIdx.x,
+                  threadIdx.y, x, y, z))
+        return;
+    const int c = cell_index(d.g, x, y, z);
+    if (FLAGS && d.flags[c]) return;
+    R s[Q];
+    gather<S, FLAGS>(d, src, x, y, z, c, s);
+    R Fx = R(0), Fy = R(0), Fz = R(0);
+    if (FORCE) force_at<R>(d, c, Fx, Fy, Fz);
+    const Mom<R> m = moments<R>(s, Fx, Fy, Fz);
+    if (!(m.rho > R(0)) || !(m.rho < R(1e30))) atomicOr(d.status, LBM_STATUS_DIVERGED);
+    if (RECORD) {
+        const long long qs = d.g.qs;
+        __stcs(tape + c, m.rho);
+        __stcs(tape + qs + c, m.ux);
+        __stcs(tape + 2 * qs + c, m.uy);
+        __stcs(tape + 3 * qs + c, m.uz);
+    }
+    collide<R, FORCE != 0>(s, m, R(d.omega), Fx, Fy, Fz);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) Stor<S>::st(dst + (long long)i * d.g.qs + c, s[i]);
+}
+
+// ---------------------------------------------------------------------------
+// Initial state: P^{-1}_i(y) = f_eq_i at y + e_i if that cell is fluid, else
+// f_eq_{opp(i)}(y) (so that the gather yields f^0 = f_eq(rho0, u0)), stored
+// shifted by -w_i.
+template <class R>
+__device__ __forceinline__ R feq_shifted(int i, R rho1, R ux, R uy, R uz) {
+    const R eu = R(ex(i)) * ux + R(ey(i)) * uy + R(ez(i)) * uz;
+    const R usq = ux * ux + uy * uy + uz * uz;
+    const R rho = R(1) + rho1;
+    return R(weight(i)) * (rho1 + rho * (R(3) * eu + R(4.5) * eu * eu - R(1.5) * usq));
+}
+
+__device__ __forceinline__ long long canon_neighbor(const Geom &g, int x, int y, int z, int i) {
+    return canon_index(g, wrap1(x + ex(i), g.nx), wrap1(y + ey(i), g.ny), wrap1(z + ez(i), g.nz));
+}
+
+template <int S, bool FLAGS>
+__global__ void __launch_bounds__(256)
+    k_init_eq(const Dev d, typename Stor<S>::T *__restrict__ P, const typename Stor<S>::R *__restrict__ rho0,
+              const typename Stor<S>::R *__restrict__ u0) {
+    typedef typename Stor<S>::R R;
+    int x, y, z;
+    if (!row_cell(d.g, d.L.nxb, blockDim.x, blockDim.y, blockIdx.x, blockIdx.y, threadIdx.x,
+                  threadIdx.y, x, y, z))
+        return;
+    const int c = cell_index(d.g, x, y, z);
+    if (FLAGS && d.flags[c]) return;
+    const long long N = d.n_cells, cc = canon_index(d.g, x, y, z);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const int t = push_dst(d.g, x, y, z, i);
+        int k = i;
+        long long ct = canon_neighbor(d.g, x, y, z, i);
+        if (FLAGS && d.flags[t]) {
+            k = opp(i);
+            ct = cc;
+        }
+        const R r1 = rho0 ? rho0[ct] - R(1) : R(0);
+        const R v = feq_shifted<R>(k, r1, u0[ct], u0[N + ct], u0[2 * N + ct]);
+        P[(long long)i * d.g.qs + c] = Stor<S>::enc(v);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// get_state: canonical shifted f^n = gather(P), format D; solid cells 0.
+template <int S, int D, bool FLAGS>
+__global__ void __launch_bounds__(256)
+    k_get_state(const Dev d, const typename Stor<S>::T *__restrict__ P, typename IOFmt<D>::T *__restrict__ out) {
+    typedef typename Stor<S>::R R;
+    int x, y, z;
+    if (!row_cell(d.g, d.L.nxb, blockDim.x, blockDim.y, blockIdx.x, blockIdx.y, threadIdx.x,
+                  threadIdx.y, x, y, z))
+        return;
+    const int c = cell_index(d.g, x, y, z);
+    const long long N = d.n_cells, cc = canon_index(d.g, x, y, z);
+    if (FLAGS && d.flags[c]) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) IOFmt<D>::put(out + i * N + cc, 0.0);
+        return;
+    }
+    R s[Q];
+    gather<S, FLAGS>(d, P, x, y, z, c, s);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) IOFmt<D>::put(out + i * N + cc, (double)s[i]);
+}
+
+// set_state: P_i(y) = s_i(y + e_i) if fluid there, else s_{opp(i)}(y).
+template <int S, int D, bool FLAGS>
+__global__ void __launch_bounds__(256)
+    k_set_state(const Dev d, typename Stor<S>::T *__restrict__ P, const typename IOFmt<D>::T *__restrict__ in) {
+    int x, y, z;
+    if (!row_cell(d.g, d.L.nxb, blockDim.x, blockDim.y, blockIdx.x, blockIdx.y, threadIdx.x,
+                  threadIdx.y, x, y, z))
+        return;
+    const int c = cell_index(d.g, x, y, z);
+    if (FLAGS && d.flags[c]) return;
+    const long long N = d.n_cells, cc = canon_index(d.g, x, y, z);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const int t = push_dst(d.g, x, y, z, i);
+        long long off = (long long)i * N + canon_neighbor(d.g, x, y, z, i);
+        if (FLAGS && d.flags[t]) off = (long long)opp(i) * N + cc;
+        IOFmt<S>::put(reinterpret_cast<typename IOFmt<S>::T *>(P) + (long long)i * d.g.qs + c,
+                      IOFmt<D>::get(in + off));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Macroscopic fields (Sec. 2 step 1): rho and u = (j + F/2)/rho; solid 0.
+template <int S, bool FLAGS, bool FORCE>
+__global__ void __launch_bounds__(256)
+    k_macros(const Dev d, const typename Stor<S>::T *__restrict__ P, typename Stor<S>::R *__restrict__ rho,
+             typename Stor<S>::R *__restrict__ u) {
+    typedef typename Stor<S>::R R;
+    int x, y, z;
+    if (!row_cell(d.g, d.L.nxb, blockDim.x, blockDim.y, blockIdx.x, blockIdx.y, threadIdx.x,
+                  threadIdx.y, x, y, z))
+        return;
+    const int c = cell_index(d.g, x, y, z);
+    const long long N = d.n_cells, cc = canon_index(d.g, x, y, z);
+    if (FLAGS && d.flags[c]) {
+        if (rho) rho[cc] = R(0);
+        u[cc] = u[N + cc] = u[2 * N + cc] = R(0);
+        return;
+    }
+    R s[Q];
+    gather<S, FLAGS>(d, P, x, y, z, c, s);
+    R Fx = R(0), Fy = R(0), Fz = R(0);
+    if (FORCE) force_at<R>(d, c, Fx, Fy, Fz);
+    const Mom<R> m = moments<R>(s, Fx, Fy, Fz);
+    if (rho) rho[cc] = m.rho;
+    u[cc] = m.ux;
+    u[N + cc] = m.uy;
+    u[2 * N + cc] = m.uz;
+}
+
+// ---------------------------------------------------------------------------
+// Mass and momentum totals in FP64: fixed grid, each thread walks the cells
+// c = tid, tid + stride, ... in order; blocks combine in a fixed tree; a
+// single block adds the per-block partials in index order. Deterministic.
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <int S, bool FLAGS, bool FORCE>
+__global__ void __launch_bounds__(RED_THREADS)
+    k_reduce(const Dev d, const typename Stor<S>::T *__restrict__ P, double *__restrict__ partials) {
+    typedef typename Stor<S>::R R;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    const long long N = d.n_cells;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long cc = (long long)blockIdx.x * blockDim.x + threadIdx.x; cc < N; cc += stride) {
+        const int x = (int)(cc % d.g.nx);
+        const long long r = cc / d.g.nx;
+        const int y = (int)(r % d.g.ny);
+        const int z = (int)(r / d.g.ny);
+        const int c = cell_index(d.g, x, y, z);
+        if (FLAGS && d.flags[c]) continue;
+        R s[Q];
+        gather<S, FLAGS>(d, P, x, y, z, c, s);
+        R Fx = R(0), Fy = R(0), Fz = R(0);
+        if (FORCE) force_at<R>(d, c, Fx, Fy, Fz);
+        const Mom<R> m = moments<R>(s, Fx, Fy, Fz);
+        acc[0] += (double)m.rho;
+        acc[1] += (double)m.rho * (double)m.ux;
+        acc[2] += (double)m.rho * (double)m.uy;
+        acc[3] += (double)m.rho * (double)m.uz;
+    }
+    __shared__ double sm[RED_THREADS / 32][4];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const double v = warp_sum(acc[k]);
+        if (lane == 0) sm[wid][k] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        double t = 0.0;
+        for (int w = 0; w < RED_THREADS / 32; ++w) t += sm[w][threadIdx.x];
+        partials[blockIdx.x * 4 + threadIdx.x] = t;
+    }
+}
+
+__global__ void __launch_bounds__(RED_THREADS) k_reduce_final(const double *__restrict__ partials, int nblocks,
+                                                             double *__restrict__ out);
+
+// ---------------------------------------------------------------------------
+// Adjoint seed (not in the paper): lambda^T_m = dL/drho + g.(e_m - u)/rho,
+// g = dL/du, at the gathered state; grad_F += g / (2 rho) (u contains F/2).
+template <int S, bool FLAGS, bool FORCE>
+__global__ void __launch_bounds__(256)
+    k_adj_seed(const Dev d, const typename Stor<S>::T *__restrict__ P, const typename Stor<S>::R *__restrict__ dL_du,
+               const typename Stor<S>::R *__restrict__ dL_drho, typename Stor<S>::R *__restrict__ lam,
+               typename Stor<S>::R *__restrict__ grad_F) {
+    typedef typename Stor<S>::R R;
+    int x, y, z;
+    if (!row_cell(d.g, d.L.nxb, blockDim.x, blockDim.y, blockIdx.x, blockIdx.y, threadIdx.x,
+                  threadIdx.y, x, y, z))
+        return;
+    const int c = cell_index(d.g, x, y, z);
+    const long long qs = d.g.qs, N = d.n_cells, cc = canon_index(d.g, x, y, z);
+    if (FLAGS && d.flags[c]) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) lam[i * qs + c] = R(0);
+        return;
+    }
+    R s[Q];
+    gather<S, FLAGS>(d, P, x, y, z, c, s);
+    R Fx = R(0), Fy = R(0), Fz = R(0);
+    if (FORCE) force_at<R>(d, c, Fx, Fy, Fz);
+    const Mom<R> m = moments<R>(s, Fx, Fy, Fz);
+    const R gx = dL_du[cc], gy = dL_du[N + cc], gz = dL_du[2 * N + cc];
+    const R dr = dL_drho ? dL_drho[cc] : R(0);
+    const R inv = R(1) / m.rho;
+    const R base = dr - (gx * m.ux + gy * m.uy + gz * m.uz) * inv;
+#pragma unroll
+    for (int i = 0; i < Q; ++i)
+        lam[i * qs + c] = base + (R(ex(i)) * gx + R(ey(i)) * gy + R(ez(i)) * gz) * inv;
+    if (grad_F) {
+        grad_F[cc] += R(0.5) * gx * inv;
+        grad_F[N + cc] += R(0.5) * gy * inv;
+        grad_F[2 * N + cc] += R(0.5) * gz * inv;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host launchers.
+inline dim3 row_grid(const Dev &d) { return dim3(d.L.nxb * d.L.nyb, d.g.nz); }
+inline dim3 row_block(const Dev &d) { return dim3(d.L.bx_threads, d.L.by_threads); }
+
+template <int S, bool FLAGS, int FORCE>
+static cudaError_t launch_step3(const Dev &d, const void *src, void *dst, void *tape) {
+    typedef typename Stor<S>::T T;
+    typedef typename Stor<S>::R R;
+    if (tape)
+        k_step<S, FLAGS, FORCE, true><<<row_grid(d), row_block(d), 0, d.stream>>>(
+            d, static_cast<const T *>(src), static_cast<T *>(dst), static_cast<R *>(tape));
+    else
+        k_step<S, FLAGS, FORCE, false><<<row_grid(d), row_block(d), 0, d.stream>>>(
+            d, static_cast<const T *>(src), static_cast<T *>(dst), nullptr);
+    return cudaGetLastError();
+}
+
+template <int S, bool FLAGS>
+static cudaError_t launch_step2(const Dev &d, const void *src, void *dst, void *tape) {
+    if (d.Ffield) return launch_step3<S, FLAGS, 2>(d, src, dst, tape);
+    if (d.force_on) return launch_step3<S, FLAGS, 1>(d, src, dst, tape);
+    return launch_step3<S, FLAGS, 0>(d, src, dst, tape);
+}
+
+template <int S>
+cudaError_t Ops<S>::step(const Dev &d, const void *src, void *dst, void *tape) {
+    return d.flags ? launch_step2<S, true>(d, src, dst, tape) : launch_step2<S, false>(d, src, dst, tape);
+}
+
+template <int S>
+cudaError_t Ops<S>::init_eq(const Dev &d, void *lat, const void *rho0, const void *u0) {
+    typedef typename Stor<S>::T T;
+    typedef typename Stor<S>::R R;
+    if (d.flags)
+        k_init_eq<S, true><<<row_grid(d), row_block(d), 0, d.stream>>>(
+            d, static_cast<T *>(lat), static_cast<const R *>(rho0), static_cast<const R *>(u0));
+    else
+        k_init_eq<S, false><<<row_grid(d), row_block(d), 0, d.stream>>>(
+            d, static_cast<T *>(lat), static_cast<const R *>(rho0), static_cast<const R *>(u0));
+    return cudaGetLastError();
+}
+
+template <int S, int D>
+static cudaError_t launch_get(const Dev &d, const void *lat, void *dst) {
+    typedef typename Stor<S>::T T;
+    typedef typename IOFmt<D>::T TD;
+    if (d.flags)
+        k_get_state<S, D, true><<<row_grid(d), row_block(d), 0, d.stream>>>(d, static_cast<const T *>(lat),
+                                                                          static_cast<TD *>(dst));
+    else
+        k_get_state<S, D, false><<<row_grid(d), row_block(d), 0, d.stream>>>(d, static_cast<const T *>(lat),
+                                                                           static_cast<TD *>(dst));
+    return cudaGetLastError();
+}
+
+template <int S, int D>
+static cudaError_t launch_set(const Dev &d, void *lat, const void *src) {
+    typedef typename Stor<S>::T T;
+    typedef typename IOFmt<D>::T TD;
+    if (d.flags)
+        k_set_state<S, D, true><<<row_grid(d), row_block(d), 0, d.stream>>>(d, static_cast<T *>(lat),
+                                                                          static_cast<const TD *>(src));
+    else
+        k_set_state<S, D, false><<<row_grid(d), row_block(d), 0, d.stream>>>(d, static_cast<T *>(lat),
+                                                                           static_cast<const TD *>(src));
+    return cudaGetLastError();
+}
+
+template <int S>
+cudaError_t Ops<S>::get_state(const Dev &d, const void *lat, void *dst, int fmt) {
+    switch (fmt) {
+    case LBM_F64: return launch_get<S, LBM_F64>(d, lat, dst);
+    case LBM_F32: return launch_get<S, LBM_F32>(d, lat, dst);
+    case LBM_F16S: return launch_get<S, LBM_F16S>(d, lat, dst);
+    case LBM_BF16S: return launch_get<S, LBM_BF16S>(d, lat, dst);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <int S>
+cudaError_t Ops<S>::set_state(const Dev &d, void *lat, const void *src, int fmt) {
+    switch (fmt) {
+    case LBM_F64: return launch_set<S, LBM_F64>(d, lat, src);
+    case LBM_F32: return launch_set<S, LBM_F32>(d, lat, src);
+    case LBM_F16S: return launch_set<S, LBM_F16S>(d, lat, src);
+    case LBM_BF16S: return launch_set<S, LBM_BF16S>(d, lat, src);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <int S, bool FLAGS>
+static cudaError_t launch_macros(const Dev &d, const void *lat, void *rho, void *u) {
+    typedef typename Stor<S>::T T;
+    typedef typename Stor<S>::R R;
+    if (d.force_on)
+        k_macros<S, FLAGS, true><<<row_grid(d), row_block(d), 0, d.stream>>>(
+            d, static_cast<const T *>(lat), static_cast<R *>(rho), static_cast<R *>(u));
+    else
+        k_macros<S, FLAGS, false><<<row_grid(d), row_block(d), 0, d.stream>>>(
+            d, static_cast<const T *>(lat), static_cast<R *>(rho), static_cast<R *>(u));
+    return cudaGetLastError();
+}
+
+template <int S>
+cudaError_t Ops<S>::macros(const Dev &d, const void *lat, void *rho, void *u) {
+    return d.flags ? launch_macros<S, true>(d, lat, rho, u) : launch_macros<S, false>(d, lat, rho, u);
+}
+
+template <int S, bool FLAGS>
+static cudaError_t launch_reduce(const Dev &d, const void *lat, double *partials) {
+    typedef typename Stor<S>::T T;
+    if (d.force_on)
+        k_reduce<S, FLAGS, true><<<RED_BLOCKS, RED_THREADS, 0, d.stream>>>(d, static_cast<const T *>(lat),
+                                                                          partials);
+    else
+        k_reduce<S, FLAGS, false><<<RED_BLOCKS, RED_THREADS, 0, d.stream>>>(d, static_cast<const T *>(lat),
+                                                                           partials);
+    return cudaGetLastError();
+}
+
+template <int S>
+cudaError_t Ops<S>::reduce(const Dev &d, const void *lat, double *partials, double *out) {
+    cudaError_t e = d.flags ? launch_reduce<S, true>(d, lat, partials) : launch_reduce<S, false>(d, lat, partials);
+    if (e != cudaSuccess) return e;
+    k_reduce_final<<<1, RED_THREADS, 0, d.stream>>>(partials, RED_BLOCKS, out);
+    return cudaGetLastError();
+}
+
+template <int S, bool FLAGS>
+static cudaError_t launch_seed(const Dev &d, const void *lat, const void *dL_du, const void *dL_drho, void *lam,
+                               void *grad_F) {
+    typedef typename Stor<S>::T T;
+    typedef typename Stor<S>::R R;
+    if (d.force_on)
+        k_adj_seed<S, FLAGS, true><<<row_grid(d), row_block(d), 0, d.stream>>>(
+            d, static_cast<const T *>(lat), static_cast<const R *>(dL_du), static_cast<const R *>(dL_drho),
+            static_cast<R *>(lam), static_cast<R *>(grad_F));
+    else
+        k_adj_seed<S, FLAGS, false><<<row_grid(d), row_block(d), 0, d.stream>>>(
+            d, static_cast<const T *>(lat), static_cast<const R *>(dL_du), static_cast<const R *>(dL_drho),
+            static_cast<R *>(lam), static_cast<R *>(grad_F));
+    return cudaGetLastError();
+}
+
+template <int S>
+cudaError_t Ops<S>::adj_seed(const Dev &d, const void *lat, const void *dL_du, const void *dL_drho, void *lam,
+                             void *grad_F) {
+    return d.flags ? launch_seed<S, true>(d, lat, dL_du, dL_drho, lam, grad_F)
+                   : launch_seed<S, false>(d, lat, dL_du, dL_drho, lam, grad_F);
+}
+
+}  // namespace lbm

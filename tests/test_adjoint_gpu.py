@@ -1,0 +1,126 @@
+"""GPU discrete adjoint against the FP64 reference adjoint (autograd over the
+oracle's update) and against central finite differences of the GPU's own FP64
+forward pass; checkpoint layout must not change the gradient."""
+import numpy as np
+import pytest
+import torch
+
+import lbm_inputs
+from gpu_helpers import REAL, ensure_built, fluid_mask, rel_l2
+from oracle import adjoint as oadj
+
+pytestmark = pytest.mark.gpu
+
+
+def _problem(shape=(6, 7, 8), frac=0.15, seed=31, T=12, amp=0.02, famp=1e-4):
+    nz, ny, nx = shape
+    rng = np.random.default_rng(seed)
+    flags = lbm_inputs.random_flags(nx, ny, nz, frac, seed) if frac else None
+    u0 = amp * rng.standard_normal((3,) + shape)
+    F = famp * rng.standard_normal((3,) + shape)
+    ut = amp * rng.standard_normal((3,) + shape)
+    m = fluid_mask(flags, shape)
+    u0 *= m
+    F *= m
+    return flags, u0, F, ut, T
+
+
+def _gpu_grad(storage, flags, u0, F, ut, T, tau, ckpt, ckpt_fmt=None):
+    from paper_1112_0850_gb300.lattice import Lattice
+    from paper_1112_0850_gb300.rollout import LBMRollout, velocity_loss
+    ensure_built()
+    nz, ny, nx = u0.shape[1:]
+    real = REAL[storage]
+    lat = Lattice(nx, ny, nz, tau, flags=flags, storage=storage)
+    u0t = torch.tensor(u0, dtype=real, device="cuda", requires_grad=True)
+    Ft = torch.tensor(F, dtype=real, device="cuda", requires_grad=True)
+    m = torch.tensor(fluid_mask(flags, u0.shape[1:]), device="cuda")
+    u = LBMRollout.apply(u0t, Ft, lat, T, ckpt, ckpt_fmt)
+    L = velocity_loss(u, torch.tensor(ut, dtype=real, device="cuda"), m)
+    gu, gF = torch.autograd.grad(L, (u0t, Ft))
+    out = (L.item(), gu.double().cpu().numpy(), gF.double().cpu().numpy())
+    lat.close()
+    return out
+
+
+@pytest.mark.parametrize("with_flags", [False, True])
+def test_fp64_adjoint_matches_reference(with_flags):
+    flags, u0, F, ut, T = _problem(frac=0.15 if with_flags else 0.0)
+    L, gu, gF = _gpu_grad("f64", flags, u0, F, ut, T, 0.6, 5)
+    Lr, gur, gFr = oadj.gradients(u0, F, 0.6, T, ut, flags)
+    m = fluid_mask(flags, u0.shape[1:])
+    assert abs(L - Lr) <= 1e-12 * Lr
+    assert rel_l2(gu, gur, m) <= 1e-10
+    assert rel_l2(gF, gFr, m) <= 1e-10
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16s"])
+def test_fp32_adjoint_matches_reference(storage):
+    flags, u0, F, ut, T = _problem()
+    _, gu, gF = _gpu_grad(storage, flags, u0, F, ut, T, 0.6, 4)
+    _, gur, gFr = oadj.gradients(u0, F, 0.6, T, ut, flags)
+    m = fluid_mask(flags, u0.shape[1:])
+    tol = 1e-4 if storage == "f32" else 2e-2
+    assert rel_l2(gu, gur, m) <= tol
+    assert rel_l2(gF, gFr, m) <= tol
+
+
+def test_checkpoint_interval_does_not_change_gradient():
+    flags, u0, F, ut, T = _problem(T=9)
+    ref = _gpu_grad("f64", flags, u0, F, ut, T, 0.57, T)
+    for K in (1, 2, 4):
+        g = _gpu_grad("f64", flags, u0, F, ut, T, 0.57, K)
+        assert np.array_equal(g[1], ref[1]) and np.array_equal(g[2], ref[2])
+
+
+def test_fp64_gradient_matches_central_differences():
+    """16^3 periodic box, random solenoidal u0 (max 0.01) and N(0, 1e-6) force
+    field, T = 50 with checkpoints every 10 steps, FP64 forward and adjoint:
+    <grad, v> against central differences of the GPU forward loss."""
+    from paper_1112_0850_gb300.lattice import Lattice
+    ensure_built()
+    n, T, tau = 16, 50, 0.6
+    S = lbm_inputs.seed_for(3)
+    u0 = lbm_inputs.solenoidal_velocity(n, 0.01, S)
+    F = lbm_inputs.force_field((n, n, n), 1e-6, S + 1)
+    F2 = lbm_inputs.force_field((n, n, n), 1e-6, S + 2)
+    lat = Lattice(n, n, n, tau, storage="f64")
+
+    def run(u, Fc):
+        lat.set_force_field(torch.tensor(Fc).cuda())
+        lat.init_equilibrium(torch.tensor(u).cuda())
+        lat.step(T)
+        _, uu = lat.macros(with_rho=False)
+        return uu.cpu().numpy()
+
+    ut = run(u0, F2)
+
+    def loss(u, Fc):
+        r = run(u, Fc) - ut
+        return 0.5 * float((r * r).sum())
+
+    lat.close()
+    _, gu, gF = _gpu_grad("f64", None, u0, F, ut, T, tau, 10)
+    lat = Lattice(n, n, n, tau, storage="f64")
+    rng = np.random.default_rng(S + 5)
+    for _ in range(6):
+        vu = rng.standard_normal(u0.shape)
+        vF = rng.standard_normal(F.shape)
+        eu = 1e-5 * np.linalg.norm(u0) / np.linalg.norm(vu)
+        eF = 1e-5 * np.linalg.norm(F) / np.linalg.norm(vF)
+        fd_u = (loss(u0 + eu * vu, F) - loss(u0 - eu * vu, F)) / (2 * eu)
+        fd_F = (loss(u0, F + eF * vF) - loss(u0, F - eF * vF)) / (2 * eF)
+        assert abs(fd_u - (gu * vu).sum()) <= 1e-6 * abs(fd_u), (fd_u, (gu * vu).sum())
+        assert abs(fd_F - (gF * vF).sum()) <= 1e-6 * abs(fd_F), (fd_F, (gF * vF).sum())
+    lat.close()
+
+
+def test_adjoint_calls_check_order():
+    from paper_1112_0850_gb300.capi import LBMError
+    from paper_1112_0850_gb300.lattice import Lattice
+    ensure_built()
+    lat = Lattice(8, 4, 4, 0.6, storage="f32")
+    tape = lat.new_tape(1)
+    with pytest.raises(LBMError):
+        lat.adjoint_step(1, tape)
+    lat.close()
