@@ -210,6 +210,22 @@ def reference_arm(args):
 
 
 # ----------------------------------------------------------------------------------------------
+def max_over_ranks(v, world, device):
+    """Largest value of v over all ranks (the slowest replica's time)."""
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.item()
+
+
+def aggregate_mflups(units_per_rank, world, seconds):
+    """Whole-job throughput: every rank processed units_per_rank in at most `seconds`."""
+    return world * units_per_rank / seconds / 1e6
+
+
 def time_steps(torch, lat, steps, warmup):
     """Warm up, then time `steps` single-step launches with CUDA events on the lattice's stream."""
     lat.step(warmup)
@@ -253,13 +269,6 @@ def main():
         if world > 1:
             dist.barrier()
 
-    def max_over_ranks(v):
-        if world == 1:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return t.item()
-
     flags = workload_flags()
     F = (GX, 0.0, 0.0)
     lat = Lattice(NX, NY, NZ, TAU, flags=flags, force=F, storage="f32")
@@ -279,10 +288,10 @@ def main():
         torch.cuda.synchronize()
     barrier()
     dt_local = e0.elapsed_time(e1) / 1e3
-    dt = max_over_ranks(dt_local)
+    dt = max_over_ranks(dt_local, world, "cuda")
     clocks = clk.summary()
     status = lat.status_word()
-    value = world * n_fluid * args.steps / dt / 1e6
+    value = aggregate_mflups(n_fluid * args.steps, world, dt)
     per_launch = dt_local / args.steps
     peak, peak_kind = measured_peaks()
     alg_bytes = n_fluid * PDF_BYTES["f32"] + n_cells * FLAG_BYTES
@@ -339,10 +348,10 @@ def main():
         l3.macros(rho_host, u_host)
         sums = l3.reduce()
         l3.close()
-        t_e2e = max_over_ranks(time.perf_counter() - t0)
+        t_e2e = max_over_ranks(time.perf_counter() - t0, world, "cuda")
         h2d = flags.nbytes + u0_host.numel() * 4
         d2h = u_host.numel() * 4 + rho_host.numel() * 4 + 32
-        e2e = {"value": world * n_fluid * args.steps / t_e2e / 1e6, "unit": "MFLUPS",
+        e2e = {"value": aggregate_mflups(n_fluid * args.steps, world, t_e2e), "unit": "MFLUPS",
                "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
                "what": "whole job per replica: lbm_create from host flags, init from pinned host u0, "
                        "%d steps, macros and FP64 totals back to host, destroy" % args.steps,

@@ -39,8 +39,10 @@ def channel_flags(nx, ny, nz, solid_frac, seed, rmin=3.0, rmax=6.0, walls=True):
     random spheres until obstacles cover `solid_frac` of the interior cells.
 
     Sphere centres: x uniform in [0, nx) (periodic minimum image in x), y and z
-    uniform in [1 + r, n - 2 - r]; radius uniform in [rmin, rmax]; a cell is
-    solid when its index lies within r of the centre; overlap allowed.
+    uniform in [1 + r, n - 2 - r]; radius uniform in [rmin, rmax], capped at
+    (min(ny, nz) - 3)/2 so a sphere fits between the walls; a cell is solid
+    when its index lies within r of the centre; overlap allowed. Boxes too
+    small to reach the fraction stop after 1000 spheres that add nothing.
     """
     rng = np.random.default_rng(seed)
     flags = np.zeros((nz, ny, nx), dtype=np.uint8)
@@ -51,8 +53,11 @@ def channel_flags(nx, ny, nz, solid_frac, seed, rmin=3.0, rmax=6.0, walls=True):
     n_interior = int(interior.sum())
     target = solid_frac * n_interior
     solid = 0
-    while solid < target:
-        r = rng.uniform(rmin, rmax)
+    # a sphere must fit between the walls: 1 + r <= n - 2 - r on y and z
+    r_fit = (min(ny, nz) - 3.0) / 2.0
+    idle = 0  # consecutive spheres that added no cell (tiny boxes may never reach the target)
+    while solid < target and r_fit >= 0.5 and idle < 1000:
+        r = min(rng.uniform(rmin, rmax), r_fit)
         cx = rng.uniform(0.0, nx)
         cy = rng.uniform(1.0 + r, ny - 2.0 - r)
         cz = rng.uniform(1.0 + r, nz - 2.0 - r)
@@ -66,7 +71,9 @@ def channel_flags(nx, ny, nz, solid_frac, seed, rmin=3.0, rmax=6.0, walls=True):
         xw = xs % nx
         sub = np.ix_(zs, ys, xw)
         newly = inside & (flags[sub] == 0) & interior[sub]
-        solid += int(newly.sum())
+        added = int(newly.sum())
+        solid += added
+        idle = 0 if added else idle + 1
         block = flags[sub]
         block[inside & interior[sub]] = 1
         flags[sub] = block

@@ -96,12 +96,15 @@ def _check_one_step(storage, lat, shape, flags, tau, F, nsamp=200, seed=5):
     del st1
     want = _expected_next(S, cells, idx, flags, tau, np.zeros(3) if F is None else np.asarray(F, np.float64))
     if storage == "f64":
-        assert np.abs(got - want).max() <= 1e-16
+        # shifted FP64 arithmetic against the oracle's unshifted FP64: a few ulp of |f| < 0.4
+        assert np.abs(got - want).max() <= 1e-15
     elif storage == "f32":
         assert np.abs(got - want).max() <= 1e-7
     else:
         # one rounding of an FP32 result to the 16-bit format: at most one unit
         # in the last place of the exactly rounded value
+        # (half a unit for the rounding, plus the FP32-vs-FP64 arithmetic difference
+        # that can move a value across a rounding boundary)
         assert np.all(np.abs(got - want) <= _ulp(want, storage) * 1.01 + 1e-30)
 
 
