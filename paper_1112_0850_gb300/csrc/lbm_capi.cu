@@ -21,6 +21,7 @@ struct lbm_ctx {
     void *lat[2];       // lat[cur] holds the latest post-collision populations
     int cur;
     uint8_t *flags_d;   // padded [qs], 1 = solid (padding included), or null
+    uint32_t *mask_d;   // padded [qs] pull masks for the step kernels, or null
     void *Ffield_d;     // padded [3][qs] of the arithmetic type, or null
     void *lam[2];       // adjoint lattices (allocated on first seed)
     int lcur;
@@ -72,7 +73,9 @@ Dev make_dev(const lbm_ctx *ctx) {
     Dev d;
     d.g = ctx->g;
     d.L = ctx->L;
+    d.P = pair_launch(ctx->g);
     d.flags = ctx->flags_d;
+    d.mask = ctx->mask_d;
     d.Ffield = ctx->Ffield_d;
     d.F[0] = ctx->F[0];
     d.F[1] = ctx->F[1];
@@ -175,7 +178,7 @@ void free_ctx(lbm_ctx *ctx) {
     if (!ctx) return;
     cudaSetDevice(ctx->device);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
-    void *ptrs[] = {ctx->lat[0], ctx->lat[1], ctx->flags_d,      ctx->Ffield_d, ctx->lam[0],
+    void *ptrs[] = {ctx->lat[0],       ctx->lat[1], ctx->flags_d,  ctx->mask_d,    ctx->Ffield_d, ctx->lam[0],
                     ctx->lam[1], ctx->red_partials, ctx->red_out, ctx->status_d, ctx->staging};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -222,6 +225,7 @@ lbm_status lbm_create(lbm_ctx **out, int nx, int ny, int nz, double tau, const u
     ctx->lat[0] = ctx->lat[1] = nullptr;
     ctx->cur = 0;
     ctx->flags_d = nullptr;
+    ctx->mask_d = nullptr;
     ctx->Ffield_d = nullptr;
     ctx->lam[0] = ctx->lam[1] = nullptr;
     ctx->lcur = 0;
@@ -244,7 +248,7 @@ lbm_status lbm_create(lbm_ctx **out, int nx, int ny, int nz, double tau, const u
         delete ctx;
         return LBM_ERR_CUDA;
     }
-    const size_t need = 2 * lat_bytes + (size_t)qs + ((size_t)RED_BLOCKS * 4 + 8) * sizeof(double);
+    const size_t need = 2 * lat_bytes + (flags ? 5 * (size_t)qs : 0) + ((size_t)RED_BLOCKS * 4 + 8) * sizeof(double);
     if (need > free_b) {
         delete ctx;
         return LBM_ERR_OOM;
@@ -275,6 +279,21 @@ lbm_status lbm_create(lbm_ctx **out, int nx, int ny, int nz, double tau, const u
                 }
     }
     ctx->n_fluid = n_fluid;
+    // Pull masks: bit i when the source x - e_i of population i is solid
+    // (periodic), SOLID_BIT on solid cells and padding.
+    std::vector<uint32_t> hmask;
+    if (flags) {
+        hmask.assign((size_t)qs, SOLID_BIT);
+        for (int z = 0; z < nz; ++z)
+            for (int y = 0; y < ny; ++y)
+                for (int x = 0; x < nx; ++x) {
+                    const int c = cell_index(ctx->g, x, y, z);
+                    uint32_t m = hflags[(size_t)c] ? SOLID_BIT : 0u;
+                    for (int i = 1; i < Q; ++i)
+                        if (hflags[(size_t)pull_src(ctx->g, x, y, z, i)]) m |= 1u << i;
+                    hmask[(size_t)c] = m;
+                }
+    }
 
     bool ok = cudaMalloc(&ctx->lat[0], lat_bytes) == cudaSuccess &&
               cudaMalloc(&ctx->lat[1], lat_bytes) == cudaSuccess &&
@@ -282,6 +301,7 @@ lbm_status lbm_create(lbm_ctx **out, int nx, int ny, int nz, double tau, const u
               cudaMalloc((void **)&ctx->red_out, 4 * sizeof(double)) == cudaSuccess &&
               cudaMalloc((void **)&ctx->status_d, sizeof(unsigned)) == cudaSuccess;
     if (ok && flags) ok = cudaMalloc((void **)&ctx->flags_d, (size_t)qs) == cudaSuccess;
+    if (ok && flags) ok = cudaMalloc((void **)&ctx->mask_d, (size_t)qs * sizeof(uint32_t)) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         free_ctx(ctx);
@@ -291,6 +311,9 @@ lbm_status lbm_create(lbm_ctx **out, int nx, int ny, int nz, double tau, const u
          cudaMemsetAsync(ctx->lat[1], 0, lat_bytes, ctx->stream) == cudaSuccess &&
          cudaMemsetAsync(ctx->status_d, 0, sizeof(unsigned), ctx->stream) == cudaSuccess;
     if (ok && flags) ok = cudaMemcpy(ctx->flags_d, hflags.data(), (size_t)qs, cudaMemcpyHostToDevice) == cudaSuccess;
+    if (ok && flags)
+        ok = cudaMemcpy(ctx->mask_d, hmask.data(), (size_t)qs * sizeof(uint32_t), cudaMemcpyHostToDevice) ==
+             cudaSuccess;
     if (ok) ok = cudaStreamSynchronize(ctx->stream) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
@@ -610,6 +633,33 @@ int64_t lbm_check_launch_indices(int nx, int ny, int nz, lbm_storage fmt) {
                     }
                 }
     if (visited != N) ++bad;  // every cell owned by exactly one thread
+    // paired launch of the step kernels: every address k_step forms
+    const RowLaunch P = pair_launch(g);
+    long long visited2 = 0;
+    auto in_row = [&](int rowbase, int x) { return x >= 0 && x < g.pitch && rowbase + x < g.qs && rowbase >= 0; };
+    for (int bz = 0; bz < nz; ++bz)
+        for (int bx = 0; bx < P.nxb * P.nyb; ++bx)
+            for (int ty = 0; ty < P.by_threads; ++ty)
+                for (int tx = 0; tx < P.bx_threads; ++tx) {
+                    int x0, y, z;
+                    if (!pair_cell(g, P.nxb, P.bx_threads, P.by_threads, bx, bz, tx, ty, x0, y, z)) continue;
+                    const bool has1 = x0 + 1 < nx;
+                    visited2 += has1 ? 2 : 1;
+                    const int c = cell_index(g, x0, y, z);
+                    if (c % 2 || !in_row(c - x0, x0) || !in_row(c - x0, x0 + 1)) ++bad;  // pair at c, c + 1
+                    const int xa = wrap1(x0 - 1, nx), xb = wrap1(x0 + 1, nx), xc = has1 ? wrap1(x0 + 2, nx) : x0;
+                    for (int i = 0; i < Q; ++i) {
+                        const int row = (wrap1(z - ez(i), nz) * ny + wrap1(y - ey(i), ny)) * g.pitch;
+                        if (ex(i) == 0) {
+                            if (!in_row(row, x0) || !in_row(row, x0 + 1) || (row + x0) % 2) ++bad;
+                        } else {
+                            if (!in_row(row, ex(i) > 0 ? xa : xb) || !in_row(row, ex(i) > 0 ? x0 : xc)) ++bad;
+                            if ((ex(i) > 0 ? xa : xb) >= nx || (has1 && (ex(i) > 0 ? x0 : xc) >= nx)) ++bad;
+                        }
+                    }
+                }
+    if (visited2 != N) ++bad;
+    if (P.bx_threads * P.by_threads != 256 || P.bx_threads % 32) ++bad;
     if (L.bx_threads * L.by_threads != 256 || L.bx_threads % 32) ++bad;
     // reduction: canonical walk
     for (long long cc = 0; cc < N; ++cc) {

@@ -43,12 +43,21 @@ LBM_HD constexpr int pair_first(int p) { return p < 3 ? 1 + 2 * p : (p < 5 ? 4 +
 // R is the arithmetic type (double for LBM_F64, float otherwise).
 template <int S> struct Stor;
 
+// ld2/st2 move the values of two x-adjacent cells (p 2-element aligned).
 template <> struct Stor<LBM_F64> {
     typedef double T;
     typedef double R;
     static __device__ __forceinline__ R ld(const T *p) { return __ldg(p); }
     static __device__ __forceinline__ void st(T *p, R v) { __stcs(p, v); }
     static __device__ __forceinline__ T enc(R v) { return v; }
+    static __device__ __forceinline__ void ld2(const T *p, R &a, R &b) {
+        const double2 v = __ldg(reinterpret_cast<const double2 *>(p));
+        a = v.x;
+        b = v.y;
+    }
+    static __device__ __forceinline__ void st2(T *p, R a, R b) {
+        __stcs(reinterpret_cast<double2 *>(p), make_double2(a, b));
+    }
 };
 
 template <> struct Stor<LBM_F32> {
@@ -57,6 +66,14 @@ template <> struct Stor<LBM_F32> {
     static __device__ __forceinline__ R ld(const T *p) { return __ldg(p); }
     static __device__ __forceinline__ void st(T *p, R v) { __stcs(p, v); }
     static __device__ __forceinline__ T enc(R v) { return v; }
+    static __device__ __forceinline__ void ld2(const T *p, R &a, R &b) {
+        const float2 v = __ldg(reinterpret_cast<const float2 *>(p));
+        a = v.x;
+        b = v.y;
+    }
+    static __device__ __forceinline__ void st2(T *p, R a, R b) {
+        __stcs(reinterpret_cast<float2 *>(p), make_float2(a, b));
+    }
 };
 
 template <> struct Stor<LBM_F16S> {
@@ -69,6 +86,16 @@ template <> struct Stor<LBM_F16S> {
         __stcs(reinterpret_cast<unsigned short *>(p), __half_as_ushort(__float2half_rn(v)));
     }
     static __device__ __forceinline__ T enc(R v) { return __float2half_rn(v); }
+    static __device__ __forceinline__ void ld2(const T *p, R &a, R &b) {
+        const unsigned v = __ldg(reinterpret_cast<const unsigned *>(p));
+        a = __half2float(__ushort_as_half((unsigned short)(v & 0xffffu)));
+        b = __half2float(__ushort_as_half((unsigned short)(v >> 16)));
+    }
+    static __device__ __forceinline__ void st2(T *p, R a, R b) {
+        const unsigned v = (unsigned)__half_as_ushort(__float2half_rn(a)) |
+                           ((unsigned)__half_as_ushort(__float2half_rn(b)) << 16);
+        __stcs(reinterpret_cast<unsigned *>(p), v);
+    }
 };
 
 template <> struct Stor<LBM_BF16S> {
@@ -82,7 +109,35 @@ template <> struct Stor<LBM_BF16S> {
         __stcs(reinterpret_cast<unsigned short *>(p), __bfloat16_as_ushort(__float2bfloat16_rn(v)));
     }
     static __device__ __forceinline__ T enc(R v) { return __float2bfloat16_rn(v); }
+    static __device__ __forceinline__ void ld2(const T *p, R &a, R &b) {
+        const unsigned v = __ldg(reinterpret_cast<const unsigned *>(p));
+        a = __bfloat162float(__ushort_as_bfloat16((unsigned short)(v & 0xffffu)));
+        b = __bfloat162float(__ushort_as_bfloat16((unsigned short)(v >> 16)));
+    }
+    static __device__ __forceinline__ void st2(T *p, R a, R b) {
+        const unsigned v = (unsigned)__bfloat16_as_ushort(__float2bfloat16_rn(a)) |
+                           ((unsigned)__bfloat16_as_ushort(__float2bfloat16_rn(b)) << 16);
+        __stcs(reinterpret_cast<unsigned *>(p), v);
+    }
 };
+
+// Pairs of arithmetic-type values (force field, tape) at an even index.
+__device__ __forceinline__ void ld2_real(const float *p, float &a, float &b) {
+    const float2 v = __ldg(reinterpret_cast<const float2 *>(p));
+    a = v.x;
+    b = v.y;
+}
+__device__ __forceinline__ void ld2_real(const double *p, double &a, double &b) {
+    const double2 v = __ldg(reinterpret_cast<const double2 *>(p));
+    a = v.x;
+    b = v.y;
+}
+__device__ __forceinline__ void st2_real(float *p, float a, float b) {
+    __stcs(reinterpret_cast<float2 *>(p), make_float2(a, b));
+}
+__device__ __forceinline__ void st2_real(double *p, double a, double b) {
+    __stcs(reinterpret_cast<double2 *>(p), make_double2(a, b));
+}
 
 inline size_t storage_bytes(lbm_storage s) { return s == LBM_F64 ? 8 : (s == LBM_F32 ? 4 : 2); }
 
@@ -117,6 +172,35 @@ inline RowLaunch row_launch(const Geom &g) {
     L.nyb = (g.ny + L.by_threads - 1) / L.by_threads;
     return L;
 }
+
+// Paired launch of the step kernels: each thread owns the two x-adjacent cells
+// x0 = 2 (xb * bx_threads + tx) and x0 + 1 of row (y, z); blocks hold 256 threads.
+inline RowLaunch pair_launch(const Geom &g) {
+    RowLaunch L;
+    const int half = (g.nx + 1) / 2;
+    int w = 32;
+    while (w < half && w < 256) w *= 2;
+    L.bx_threads = w;
+    L.by_threads = 256 / w;
+    L.nxb = (half + w - 1) / w;
+    L.nyb = (g.ny + L.by_threads - 1) / L.by_threads;
+    return L;
+}
+
+LBM_HD bool pair_cell(const Geom &g, int nxb, int bdx, int bdy, int bx, int bz, int tx, int ty, int &x0, int &y,
+                      int &z) {
+    const int xb = bx % nxb;
+    const int yg = bx / nxb;
+    x0 = 2 * (xb * bdx + tx);
+    y = yg * bdy + ty;
+    z = bz;
+    return x0 < g.nx && y < g.ny && z < g.nz;
+}
+
+// Pull mask of a cell (precomputed on the host from the flags): bit i,
+// 1 <= i <= 18, is set when the source cell x - e_i is solid, so population i
+// bounces back; SOLID_BIT is set on solid cells and on row padding.
+constexpr uint32_t SOLID_BIT = 0x80000000u;
 
 // Cell owned by thread (tx, ty) of block (bx, bz); false for threads past the edge.
 LBM_HD bool row_cell(const Geom &g, int nxb, int bdx, int bdy, int bx, int bz, int tx, int ty,

@@ -71,39 +71,94 @@ __device__ __forceinline__ void gather(const Dev &d, const typename Stor<S>::T *
 
 // ---------------------------------------------------------------------------
 // Fused stream-collide (Sec. 2 steps 1-3, Eq. 1; Sec. 6 pull-style update).
-// Resident blocks of 256 threads per SM the step kernels are compiled for:
-// 4 (<= 64 registers) for FP32 arithmetic, 2 (<= 128) for FP64.
+//
+// Each thread updates the two x-adjacent cells x0, x0 + 1 of one row, so the
+// populations with e_x = 0 (rest, +-y, +-z and the yz diagonals) move as one
+// aligned pair per load and every population is stored as one aligned pair;
+// populations with e_x = +-1 come from sources shifted by one cell and are
+// loaded per cell. Bounce-back is decided from a 32-bit pull mask per cell
+// (one coalesced load) instead of 18 neighbour flags: a bounced population
+// loads the opposite population of the cell itself, so every value costs
+// exactly one load either way. Solid cells and row padding are computed on
+// in-bounds data and their results are never read.
+//
+// Resident blocks of 256 threads per SM the step kernels are compiled for.
 template <class R> struct MinBlocks {
-    static constexpr int value = sizeof(R) == 8 ? 2 : 4;
+    static constexpr int value = sizeof(R) == 8 ? 1 : 2;
 };
 
 template <int S, bool FLAGS, int FORCE, bool RECORD>
 __global__ void __launch_bounds__(256, MinBlocks<typename Stor<S>::R>::value)
     k_step(const Dev d, const typename Stor<S>::T *__restrict__ src, typename Stor<S>::T *__restrict__ dst,
            typename Stor<S>::R *__restrict__ tape) {
+    typedef typename Stor<S>::T T;
     typedef typename Stor<S>::R R;
-    int x, y, z;
-    if (!row_cell(d.g, d.L.nxb, blockDim.x, blockDim.y, blockIdx.x, blockIdx.y, threadIdx.x,
-                  threadIdx.y, x, y, z))
+    int x0, y, z;
+    if (!pair_cell(d.g, d.P.nxb, blockDim.x, blockDim.y, blockIdx.x, blockIdx.y, threadIdx.x, threadIdx.y, x0,
+                   y, z))
         return;
-    const int c = cell_index(d.g, x, y, z);
-    if (FLAGS && d.flags[c]) return;
-    R s[Q];
-    gather<S, FLAGS>(d, src, x, y, z, c, s);
-    R Fx = R(0), Fy = R(0), Fz = R(0);
-    if (FORCE) force_at<R>(d, c, Fx, Fy, Fz);
-    const Mom<R> m = moments<R>(s, Fx, Fy, Fz);
-    if (!(m.rho > R(0)) || !(m.rho < R(1e30))) atomicOr(d.status, LBM_STATUS_DIVERGED);
-    if (RECORD) {
-        const long long qs = d.g.qs;
-        __stcs(tape + c, m.rho);
-        __stcs(tape + qs + c, m.ux);
-        __stcs(tape + 2 * qs + c, m.uy);
-        __stcs(tape + 3 * qs + c, m.uz);
+    const Geom &g = d.g;
+    const bool has1 = x0 + 1 < g.nx;
+    const int c = cell_index(g, x0, y, z);
+    uint32_t m0 = 0u, m1 = has1 ? 0u : SOLID_BIT;
+    if (FLAGS) {
+        const uint2 mm = __ldg(reinterpret_cast<const uint2 *>(d.mask + c));
+        m0 = mm.x;
+        m1 |= mm.y;
     }
-    collide<R, FORCE != 0>(s, m, R(d.omega), Fx, Fy, Fz);
+    const bool live0 = !(m0 & SOLID_BIT), live1 = !(m1 & SOLID_BIT);
+    if (!live0 && !live1) return;
+    // source columns of the e_x = +-1 populations
+    const int xa = wrap1(x0 - 1, g.nx);           // e_x = +1, cell x0
+    const int xb = wrap1(x0 + 1, g.nx);           // e_x = -1, cell x0
+    const int xc = has1 ? wrap1(x0 + 2, g.nx) : x0;  // e_x = -1, cell x0 + 1 (e_x = +1 pulls from x0)
+    R s0[Q], s1[Q];
 #pragma unroll
-    for (int i = 0; i < Q; ++i) Stor<S>::st(dst + (long long)i * d.g.qs + c, s[i]);
+    for (int i = 0; i < Q; ++i) {
+        const int row = (wrap1(z - ez(i), g.nz) * g.ny + wrap1(y - ey(i), g.ny)) * g.pitch;
+        const T *Pi = src + (long long)i * g.qs;
+        const T *Po = src + (long long)opp(i) * g.qs;
+        const bool b0 = FLAGS && i > 0 && ((m0 >> i) & 1u);
+        const bool b1 = FLAGS && i > 0 && ((m1 >> i) & 1u);
+        if (ex(i) == 0) {
+            if (b0 == b1) {
+                Stor<S>::ld2(b0 ? Po + c : Pi + row + x0, s0[i], s1[i]);
+            } else {
+                s0[i] = Stor<S>::ld(b0 ? Po + c : Pi + row + x0);
+                s1[i] = Stor<S>::ld(b1 ? Po + c + 1 : Pi + row + x0 + 1);
+            }
+        } else {
+            s0[i] = Stor<S>::ld(b0 ? Po + c : Pi + row + (ex(i) > 0 ? xa : xb));
+            s1[i] = Stor<S>::ld(b1 ? Po + c + 1 : Pi + row + (ex(i) > 0 ? x0 : xc));
+        }
+    }
+    R F0x = R(0), F0y = R(0), F0z = R(0), F1x = R(0), F1y = R(0), F1z = R(0);
+    if (FORCE == 1) {
+        F0x = F1x = R(d.F[0]);
+        F0y = F1y = R(d.F[1]);
+        F0z = F1z = R(d.F[2]);
+    } else if (FORCE == 2) {
+        const R *F = static_cast<const R *>(d.Ffield);
+        ld2_real(F + c, F0x, F1x);
+        ld2_real(F + g.qs + c, F0y, F1y);
+        ld2_real(F + 2 * g.qs + c, F0z, F1z);
+    }
+    const Mom<R> ma = moments<R>(s0, F0x, F0y, F0z);
+    const Mom<R> mb = moments<R>(s1, F1x, F1y, F1z);
+    const bool bad0 = live0 && !(ma.rho > R(0) && ma.rho < R(1e30));
+    const bool bad1 = live1 && !(mb.rho > R(0) && mb.rho < R(1e30));
+    if (bad0 || bad1) atomicOr(d.status, LBM_STATUS_DIVERGED);
+    if (RECORD) {
+        const long long qs = g.qs;
+        st2_real(tape + c, ma.rho, mb.rho);
+        st2_real(tape + qs + c, ma.ux, mb.ux);
+        st2_real(tape + 2 * qs + c, ma.uy, mb.uy);
+        st2_real(tape + 3 * qs + c, ma.uz, mb.uz);
+    }
+    collide<R, FORCE != 0>(s0, ma, R(d.omega), F0x, F0y, F0z);
+    collide<R, FORCE != 0>(s1, mb, R(d.omega), F1x, F1y, F1z);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) Stor<S>::st2(dst + (long long)i * g.qs + c, s0[i], s1[i]);
 }
 
 // ---------------------------------------------------------------------------
@@ -318,15 +373,19 @@ __global__ void __launch_bounds__(256)
 inline dim3 row_grid(const Dev &d) { return dim3(d.L.nxb * d.L.nyb, d.g.nz); }
 inline dim3 row_block(const Dev &d) { return dim3(d.L.bx_threads, d.L.by_threads); }
 
+// The step kernels run on the paired launch (two cells per thread).
+inline dim3 step_grid(const Dev &d) { return dim3(d.P.nxb * d.P.nyb, d.g.nz); }
+inline dim3 step_block(const Dev &d) { return dim3(d.P.bx_threads, d.P.by_threads); }
+
 template <int S, bool FLAGS, int FORCE>
 static cudaError_t launch_step3(const Dev &d, const void *src, void *dst, void *tape) {
     typedef typename Stor<S>::T T;
     typedef typename Stor<S>::R R;
     if (tape)
-        k_step<S, FLAGS, FORCE, true><<<row_grid(d), row_block(d), 0, d.stream>>>(
+        k_step<S, FLAGS, FORCE, true><<<step_grid(d), step_block(d), 0, d.stream>>>(
             d, static_cast<const T *>(src), static_cast<T *>(dst), static_cast<R *>(tape));
     else
-        k_step<S, FLAGS, FORCE, false><<<row_grid(d), row_block(d), 0, d.stream>>>(
+        k_step<S, FLAGS, FORCE, false><<<step_grid(d), step_block(d), 0, d.stream>>>(
             d, static_cast<const T *>(src), static_cast<T *>(dst), nullptr);
     return cudaGetLastError();
 }

@@ -1,0 +1,148 @@
+"""The workload configurations at their stated sizes, end to end on the GPU.
+
+- Taylor-Green vortex, periodic 512^3, U0 = 0.02, tau = 0.52, 200 steps:
+  velocity and density of FP32 and 16-bit shifted storage against an FP64
+  run of the same kernels (the FP64 path is itself held to 1e-12 against the
+  oracle, here on a 64^3 Taylor-Green box).
+- Adjoint, periodic 128^3, random solenoidal u0 (max 0.01), per-cell force
+  N(0, 1e-6), 500 steps, checkpoints every 50: the FP32 gradient against the
+  FP64 gradient of the same kernels, and a descent step lowers the loss.
+- Porous channel 384 x 256 x 256 with 15% spheres, tau = 0.55, 2000 steps:
+  FP16-shifted forward with BF16 checkpoints every 100 steps and FP32 adjoint,
+  against the all-FP32 adjoint (relative error of dL/dF over fluid cells).
+Each test prints the measured errors.
+"""
+import numpy as np
+import pytest
+import torch
+
+import lbm_inputs
+import oracle
+from gpu_helpers import ensure_built, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+def _lattice(*a, **k):
+    from paper_1112_0850_gb300.lattice import Lattice
+    ensure_built()
+    return Lattice(*a, **k)
+
+
+def test_taylor_green_64_fp64_matches_oracle():
+    n, tau, T = 64, 0.52, 200
+    rho0, u0 = lbm_inputs.taylor_green(n, 0.02)
+    lat = _lattice(n, n, n, tau, storage="f64")
+    lat.init_equilibrium(torch.tensor(u0).cuda(), torch.tensor(rho0).cuda())
+    lat.step(T)
+    rho, u = lat.macros()
+    lat.close()
+    f = oracle.run(oracle.init_equilibrium(u0, rho0=rho0), tau, T)
+    rho_o, u_o = oracle.macros(f)
+    err_u = rel_l2(u.cpu().numpy(), u_o, None)
+    err_r = np.abs(rho.cpu().numpy() - rho_o).max()
+    print("taylor-green 64^3 FP64 vs oracle: rel u %.3e, max |drho| %.3e" % (err_u, err_r))
+    assert err_u <= 1e-12 and err_r <= 1e-13
+
+
+def test_taylor_green_512_storage_accuracy():
+    n, tau, T = 512, 0.52, 200
+    rho0, u0 = lbm_inputs.taylor_green(n, 0.02)
+    ref = _lattice(n, n, n, tau, storage="f64")
+    ref.init_equilibrium(torch.from_numpy(u0), torch.from_numpy(rho0))  # host arrays: staged by the library
+    ref.step(T)
+    rho_ref, u_ref = ref.macros()
+    sums_ref = ref.reduce()
+    ref.close()
+    u0f, rho0f = u0.astype(np.float32), rho0.astype(np.float32)
+    del u0, rho0
+    errs = {}
+    for storage in ("f32", "f16s", "bf16s"):
+        lat = _lattice(n, n, n, tau, storage=storage)
+        lat.init_equilibrium(torch.from_numpy(u0f), torch.from_numpy(rho0f))
+        lat.step(T)
+        rho, u = lat.macros()
+        sums = lat.reduce()
+        lat.close()
+        du = torch.linalg.vector_norm(u.double() - u_ref) / torch.linalg.vector_norm(u_ref)
+        dr = (rho.double() - rho_ref).abs().max()
+        errs[storage] = (du.item(), dr.item(), abs(sums[0] - sums_ref[0]) / sums_ref[0])
+        del rho, u
+    for s, (du, dr, dm) in errs.items():
+        print("taylor-green 512^3, 200 steps, %s vs FP64: rel u %.3e, max |drho| %.3e, mass drift %.3e" %
+              (s, du, dr, dm))
+    assert errs["f32"][0] <= 1e-5
+    assert errs["f16s"][0] <= 1e-3
+    assert errs["bf16s"][0] <= 1e-2
+
+
+def _adjoint_grads(storage, n, T, K, tau, u0, F, ut, flags=None, ckpt_fmt=None):
+    from paper_1112_0850_gb300.rollout import LBMRollout, velocity_loss
+    nz, ny, nx = u0.shape[1:]
+    real = torch.float64 if storage == "f64" else torch.float32
+    lat = _lattice(nx, ny, nz, tau, flags=flags, storage=storage)
+    u0t = torch.tensor(u0, dtype=real, device="cuda", requires_grad=True)
+    Ft = torch.tensor(F, dtype=real, device="cuda", requires_grad=True)
+    m = None if flags is None else torch.tensor(flags == 0, device="cuda")
+    u = LBMRollout.apply(u0t, Ft, lat, T, K, ckpt_fmt)
+    L = velocity_loss(u, torch.as_tensor(ut, dtype=real, device="cuda"), m)
+    gu, gF = torch.autograd.grad(L, (u0t, Ft))
+    lat.close()
+    return L.item(), gu.double(), gF.double()
+
+
+def _forward_u(storage, tau, T, u0, F, flags=None):
+    nz, ny, nx = u0.shape[1:]
+    real = torch.float64 if storage == "f64" else torch.float32
+    lat = _lattice(nx, ny, nz, tau, flags=flags, storage=storage)
+    lat.set_force_field(torch.as_tensor(F, dtype=real).cuda())
+    lat.init_equilibrium(torch.as_tensor(u0, dtype=real).cuda())
+    lat.step(T)
+    _, u = lat.macros(with_rho=False)
+    lat.close()
+    return u
+
+
+def test_adjoint_config_128_fp32_against_fp64():
+    n, T, K, tau = 128, 500, 50, 0.6
+    S = lbm_inputs.seed_for(3)
+    u0 = lbm_inputs.solenoidal_velocity(n, 0.01, S)
+    F = lbm_inputs.force_field((n, n, n), 1e-6, S + 1)
+    F2 = lbm_inputs.force_field((n, n, n), 1e-6, S + 2)
+    ut = _forward_u("f64", tau, T, u0, F2).cpu().numpy()
+    L32, gu32, gF32 = _adjoint_grads("f32", n, T, K, tau, u0, F, ut)
+    L64, gu64, gF64 = _adjoint_grads("f64", n, T, K, tau, u0, F, ut)
+    eu = (torch.linalg.vector_norm(gu32 - gu64) / torch.linalg.vector_norm(gu64)).item()
+    eF = (torch.linalg.vector_norm(gF32 - gF64) / torch.linalg.vector_norm(gF64)).item()
+    print("adjoint 128^3, 500 steps: L %.6e (FP32) %.6e (FP64); rel grad error FP32 vs FP64: u0 %.3e, F %.3e"
+          % (L32, L64, eu, eF))
+    assert abs(L32 - L64) <= 1e-3 * L64
+    assert eu <= 1e-3 and eF <= 1e-3
+    # a small step against the gradient lowers the loss
+    eta = 0.1 * np.linalg.norm(u0) / torch.linalg.vector_norm(gu64).item()
+    u1 = _forward_u("f64", tau, T, u0 - eta * gu64.cpu().numpy(), F).cpu().numpy()
+    L1 = 0.5 * float(((u1 - ut) ** 2).sum())
+    assert L1 < L64
+
+
+def test_porous_channel_fp16_bf16_checkpoints_gradient():
+    nx, ny, nz, T, K, tau = 384, 256, 256, 2000, 100, 0.55
+    S = lbm_inputs.seed_for(4)
+    flags = lbm_inputs.channel_flags(nx, ny, nz, 0.15, S)
+    fluid = flags == 0
+    shape = (nz, ny, nx)
+    F = lbm_inputs.force_field(shape, 1e-7, S + 1)
+    F[0] += 1e-6
+    F2 = lbm_inputs.force_field(shape, 1e-7, S + 2)
+    F2[0] += 1e-6
+    F *= fluid
+    F2 *= fluid
+    u0 = np.zeros((3,) + shape)
+    ut = _forward_u("f32", tau, T, u0, F2, flags).cpu().numpy()
+    _, _, gF16 = _adjoint_grads("f16s", nx, T, K, tau, u0, F, ut, flags, "bf16s")
+    _, _, gF32 = _adjoint_grads("f32", nx, T, K, tau, u0, F, ut, flags, None)
+    m = torch.tensor(fluid, device="cuda")
+    err = (torch.linalg.vector_norm((gF16 - gF32)[:, m]) / torch.linalg.vector_norm(gF32[:, m])).item()
+    print("porous channel 384x256x256, 2000 steps: rel error of dL/dF, FP16 storage + BF16 checkpoints vs "
+          "all-FP32: %.3e" % err)
+    assert np.isfinite(err) and err <= 0.1

@@ -128,14 +128,20 @@ def test_one_step_matches_rounding_emulation(name, storage):
     m = fluid_mask(flags, (nz, ny, nx))
     d = np.abs(got - want)[:, m]
     a = np.abs(want)[:, m]
+    # FP32 collision arithmetic: sums of 19 terms no larger than the largest
+    # deviation in the state, so its error stays below ~19 * 2^-24 of that
+    arith = 2.0 ** -20 * np.abs(s_n).max()
     if storage == "f32":
-        ulp = np.spacing(a.astype(np.float32)).astype(np.float64)
-    elif storage == "f16s":
-        ulp = np.spacing(a.astype(np.float16)).astype(np.float64)
+        assert np.all(d <= arith), d.max() / arith
     else:
-        ulp = 2.0 ** (np.floor(np.log2(np.maximum(a, 1e-38))) - 7)
-    assert np.all(d <= 1.01 * ulp + 1e-30), (d / np.maximum(ulp, 1e-300)).max()
-    assert (d == 0).mean() > 0.9  # nearly every value is rounded identically
+        if storage == "f16s":
+            ulp = np.spacing(a.astype(np.float16)).astype(np.float64)
+        else:
+            ulp = 2.0 ** (np.floor(np.log2(np.maximum(a, 1e-38))) - 7)
+        # one rounding to the format, possibly on the other side of a
+        # rounding boundary because of the FP32 arithmetic before it
+        assert np.all(d <= 1.01 * ulp + arith), (d / (ulp + arith)).max()
+        assert (d == 0).mean() > 0.9  # nearly every value is rounded identically
     lat.close()
 
 
@@ -146,8 +152,9 @@ def test_init_state_is_equilibrium(storage):
     f0 = oracle.init_equilibrium(as_input(u0, storage), rho0=as_input(rho0, storage), flags=flags)
     s0 = shifted(f0, flags)
     m = fluid_mask(flags, u0.shape[1:])
-    # a few units in the last place of the stored format (|s| < 0.02)
-    tol = {"f64": 2e-17, "f32": 4e-9, "f16s": 1e-5, "bf16s": 1e-4}[storage]
+    # a few units in the last place of the stored format (|s| < 0.02); for
+    # FP64 the oracle's own f - w near w_0 = 1/3 is exact only to ~ulp(1/3)
+    tol = {"f64": 1e-16, "f32": 4e-9, "f16s": 1e-5, "bf16s": 1e-4}[storage]
     assert np.abs(st - s0)[:, m].max() <= tol
     lat.close()
 
