@@ -144,6 +144,39 @@ lbm_status lbm_macros(lbm_ctx *ctx, void *rho, void *u);
  * sum rho u_z} with rho u = j + F/2. out is a host array; synchronizes. */
 lbm_status lbm_reduce(lbm_ctx *ctx, double out[4]);
 
+/* Largest lattice, in cells (nx * ny * nz), that lbm_reduce_state_noalloc
+ * accepts: its fixed scratch array holds one partial sum per 16384 cells. */
+#define LBM_NOALLOC_MAX_CELLS 268435456LL
+
+/* The totals of lbm_reduce, computed from a state the caller passes in,
+ * without allocating any device memory. The paper has no counterpart; this
+ * exists for callers that cannot call cudaMalloc where they need the totals:
+ * code embedded in a framework whose caching allocator already holds the free
+ * device memory, and pipelines that cannot afford cudaMalloc's implicit
+ * device-wide synchronization between their launches.
+ *   state   device array, shifted populations s_i = f_i - w_i in format fmt,
+ *           canonical [19][nz][ny][nx] (as lbm_get_state writes it).
+ *   flags   nullable (= all fluid): device uint8 [nz][ny][nx], nonzero = solid.
+ *   force   nullable (= zero): host array of 3 doubles, the uniform body force
+ *           that enters rho u = j + F/2.
+ *   out     device array of 4 doubles: {sum rho, sum rho u_x, sum rho u_y,
+ *           sum rho u_z} over fluid cells, accumulated in FP64 in a fixed order.
+ *   cuda_stream  cudaStream_t to launch on (NULL = default stream).
+ * Scratch: a file-scope device array of 512 KiB, which every GPU that loads
+ * the library keeps until the process exits; each call overwrites the slots it
+ * uses, so nothing has to be cleared. All calls share that one array: calls
+ * whose kernels can overlap on the GPU (different streams, or different host
+ * threads without ordering) race and may return wrong totals. The first call
+ * on each device looks up the array's device address (cudaGetSymbolAddress
+ * with that device current); make that first call before any stream capture.
+ * Asynchronous on cuda_stream. Returns LBM_ERR_ARG for a null state or out, a
+ * bad format or size, and when nx * ny * nz exceeds LBM_NOALLOC_MAX_CELLS;
+ * LBM_ERR_CUDA if the address look-up or a launch fails. It calls no
+ * cudaMalloc, cudaFree or allocating library routine. */
+lbm_status lbm_reduce_state_noalloc(const void *state, lbm_storage fmt, int nx, int ny, int nz,
+                                    const uint8_t *flags, const double force[3], double *out,
+                                    void *cuda_stream);
+
 /* Copy the current state out as shifted populations s_i = f_i - w_i in format
  * fmt, canonical [19][nz][ny][nx] (element type double / float / binary16 /
  * bfloat16). Solid cells read 0. Host or device destination. */

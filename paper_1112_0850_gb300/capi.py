@@ -17,6 +17,7 @@ STORAGE_NAME = {v: k for k, v in STORAGE.items()}
 STORAGE_BYTES = {LBM_F64: 8, LBM_F32: 4, LBM_F16S: 2, LBM_BF16S: 2}
 STATUS_DIVERGED = 0x1
 STATUS_INDEX = 0x2
+NOALLOC_MAX_CELLS = 268435456
 Q = 19
 
 
@@ -47,6 +48,7 @@ PROTOTYPES = {
     "lbm_step": (_st, [_vp, _i]),
     "lbm_macros": (_st, [_vp, _vp, _vp]),
     "lbm_reduce": (_st, [_vp, _vp]),
+    "lbm_reduce_state_noalloc": (_st, [_vp, _i, _i, _i, _i, _vp, _vp, _vp, _vp]),
     "lbm_get_state": (_st, [_vp, _vp, _i]),
     "lbm_set_state": (_st, [_vp, _vp, _i]),
     "lbm_step_record": (_st, [_vp, _i, _vp]),
