@@ -64,9 +64,9 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(storage):
-    """DRAM bytes per step launch from the committed ncu summary, if it was
-    taken on the current kernel sources; else None."""
+def ncu_traffic(case, storage):
+    """DRAM bytes (read + write) of one step launch from the committed ncu
+    summary, if it was taken on the current kernel sources; else None."""
     path = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
     try:
         with open(path) as f:
@@ -75,7 +75,7 @@ def ncu_traffic(storage):
         return None
     if d.get("src_hash") != kernel_source_hash():
         return None
-    ent = d.get("kernels", {}).get(storage)
+    ent = d.get("kernels", {}).get("%s/%s" % (case, storage))
     return None if ent is None else float(ent["dram_bytes_per_launch"])
 
 
@@ -247,6 +247,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="skip other precisions, adjoint ratio, CPU baseline")
+    ap.add_argument("--case", default="channel", choices=["channel", "taylor-green"],
+                    help="headline workload: the walled channel (default) or a periodic Taylor-Green box")
+    ap.add_argument("--storage", default="f32", choices=["f64", "f32", "f16s", "bf16s"])
+    ap.add_argument("--n", type=int, default=512, help="Taylor-Green box edge")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
@@ -271,9 +275,24 @@ def main():
 
     flags = workload_flags()
     F = (GX, 0.0, 0.0)
-    lat = Lattice(NX, NY, NZ, TAU, flags=flags, force=F, storage="f32")
-    n_fluid, n_cells = lat.n_fluid, NX * NY * NZ
-    lat.init_equilibrium(lat.zeros(3))
+    storage = args.storage
+    if args.case == "channel":
+        lat = Lattice(NX, NY, NZ, TAU, flags=flags, force=F, storage=storage)
+        lat.init_equilibrium(lat.zeros(3))
+        n_cells = NX * NY * NZ
+        workload = WORKLOAD
+        flag_bytes = FLAG_BYTES
+    else:
+        n = args.n
+        lat = Lattice(n, n, n, 0.52, storage=storage)
+        rho_tg, u_tg = lbm_inputs.taylor_green(n, 0.02, dtype=np.float32)
+        real = torch.float64 if storage == "f64" else torch.float32
+        lat.init_equilibrium(torch.from_numpy(u_tg).to("cuda", real), torch.from_numpy(rho_tg).to("cuda", real))
+        del rho_tg, u_tg
+        n_cells = n ** 3
+        workload = "D3Q19 BGK Taylor-Green vortex, periodic %d^3, U0=0.02, tau=0.52" % n
+        flag_bytes = 0
+    n_fluid = lat.n_fluid
 
     # ---- headline: FP32 steps, device-resident --------------------------------------------
     lat.step(args.warmup)
@@ -294,14 +313,14 @@ def main():
     value = aggregate_mflups(n_fluid * args.steps, world, dt)
     per_launch = dt_local / args.steps
     peak, peak_kind = measured_peaks()
-    alg_bytes = n_fluid * PDF_BYTES["f32"] + n_cells * FLAG_BYTES
+    alg_bytes = n_fluid * PDF_BYTES[storage] + n_cells * flag_bytes
     achieved = alg_bytes / per_launch / 1e9
-    traffic = ncu_traffic("f32")
+    traffic = ncu_traffic(args.case, storage)
 
     extras = {}
     cpu = None
     e2e = None
-    if not args.no_extras:
+    if not args.no_extras and args.case == "channel" and storage == "f32":
         # ---- other storage formats on the same workload -------------------------------------
         per_prec = {"f32": {"mflups": n_fluid / per_launch / 1e6, "gbs": achieved, "frac": achieved / peak}}
         ks = max(10, args.steps // 5)
@@ -313,6 +332,24 @@ def main():
             per_prec[s] = {"mflups": n_fluid / t / 1e6, "gbs": gbs, "frac": gbs / peak}
             l2.close()
         extras["per_precision"] = per_prec
+        # ---- the 512^3 periodic Taylor-Green box, every storage format -----------------
+        tg = {}
+        n = 512
+        rho_tg, u_tg = lbm_inputs.taylor_green(n, 0.02, dtype=np.float32)
+        rho_tg, u_tg = torch.from_numpy(rho_tg).cuda(), torch.from_numpy(u_tg).cuda()
+        for s in ("f32", "f16s", "bf16s", "f64"):
+            l2 = Lattice(n, n, n, 0.52, storage=s)
+            if s == "f64":
+                l2.init_equilibrium(u_tg.double(), rho_tg.double())
+            else:
+                l2.init_equilibrium(u_tg, rho_tg)
+            kk = 10 if s == "f64" else 40
+            t = time_steps(torch, l2, kk, 3) / kk
+            gbs = n ** 3 * PDF_BYTES[s] / t / 1e9
+            tg[s] = {"mlups": n ** 3 / t / 1e6, "gbs": gbs, "frac": gbs / peak, "ms_per_step": t * 1e3}
+            l2.close()
+        extras["taylor_green_512"] = tg
+        del rho_tg, u_tg
         # ---- adjoint / forward step-time ratio (FP32, per-cell force gradient) -------------
         K = 50
         tape = lat.new_tape(K)
@@ -361,18 +398,23 @@ def main():
             v, cores, desc, _, _ = oracle_baseline(flags, 10.0)
             cpu = {"value": v, "unit": "MFLUPS", "cores": cores, "kind": "oracle", "sample": desc}
 
+    lat_bytes = lat.info.lattice_bytes
     lat.close()
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "MFLUPS", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "nx": NX, "ny": NY, "nz": NZ, "n_cells": n_cells,
-                       "n_fluid": n_fluid, "storage": "f32 (shifted f - w)", "tau": TAU,
-                       "l2": "no flush: two lattices of 319 MB each exceed the 129 MB L2",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if storage == "f64" else "f32",
+            "data": "synthetic",
+            "config": {"workload": workload, "n_cells": n_cells, "n_fluid": n_fluid,
+                       "storage": storage + " (shifted f - w)",
+                       "l2": "no flush: the two lattices (%.0f MB each) exceed the 129 MB L2" % (
+                           lat_bytes / 1e6),
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": traffic, "kernel": STEP_KERNEL + "<f32,flags,uniform force>",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "kernel": "%s<%s%s>" % (STEP_KERNEL, storage,
+                                                 ",flags,uniform force" if args.case == "channel" else ""),
                          "peak_source": peak_kind + " hbm_gbs (MEASURED_PEAKS.json)",
                          "alg_bytes_per_launch": alg_bytes},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps, "clocks": clocks,

@@ -49,45 +49,14 @@ __global__ void __launch_bounds__(RED_THREADS) k_reduce_final(const double *__re
     }
 }
 
-template <class R, bool FLAGS, bool FORCE>
-__global__ void __launch_bounds__(256, sizeof(R) == 8 ? 2 : 4)
-    k_adj_step(const Dev d, const R *__restrict__ lam_in, R *__restrict__ lam_out, const R *__restrict__ tape,
-               R *__restrict__ grad_F) {
-    int x, y, z;
-    if (!row_cell(d.g, d.L.nxb, blockDim.x, blockDim.y, blockIdx.x, blockIdx.y, threadIdx.x,
-                  threadIdx.y, x, y, z))
-        return;
-    const int c = cell_index(d.g, x, y, z);
-    if (FLAGS && d.flags[c]) return;
-    const long long qs = d.g.qs;
-    // mu = G^T lambda^{n+1}
-    R mu[Q];
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        const int t = push_dst(d.g, x, y, z, i);
-        long long off = (long long)i * qs + t;
-        if (FLAGS && i > 0 && d.flags[t]) off = (long long)opp(i) * qs + c;
-        mu[i] = __ldg(lam_in + off);
-    }
-    const R rho = __ldg(tape + c), ux = __ldg(tape + qs + c), uy = __ldg(tape + 2 * qs + c),
-            uz = __ldg(tape + 3 * qs + c);
-    R Fx = R(0), Fy = R(0), Fz = R(0);
-    if (FORCE) {
-        if (d.Ffield) {
-            const R *F = static_cast<const R *>(d.Ffield);
-            Fx = F[c];
-            Fy = F[qs + c];
-            Fz = F[2 * qs + c];
-        } else {
-            Fx = R(d.F[0]);
-            Fy = R(d.F[1]);
-            Fz = R(d.F[2]);
-        }
-    }
-    const R om = R(d.omega);
+// lambda^n of one cell from mu = G^T lambda^{n+1}, the recorded (rho, u) and
+// the force (see the header comment); adds this step's dL/dF to g.
+template <class R, bool FORCE>
+__device__ __forceinline__ void adj_collide(R mu[Q], R rho, R ux, R uy, R uz, R Fx, R Fy, R Fz, R om, R &gx, R &gy,
+                                            R &gz) {
     const R usq = ux * ux + uy * uy + uz * uz;
-    // P = sum_k w_k mu_k; A4 = sum over pairs w p (e.u)^2; bv = sum w (3 q + 9 (e.u) p) e;
-    // dv = sum w p (e.F) e; with p = mu_i + mu_opp(i), q = mu_i - mu_opp(i).
+    // P = sum_k w_k mu_k; A4 = sum over pairs w p (e.u)^2; b = sum w (3 q + 9 (e.u) p) e;
+    // d = sum w p (e.F) e; with p = mu_i + mu_opp(i), q = mu_i - mu_opp(i)
     R P = R(1.0 / 3.0) * mu[0], A4 = R(0);
     R bx = R(0), by = R(0), bz = R(0), dx = R(0), dy = R(0), dz = R(0);
 #pragma unroll
@@ -114,8 +83,8 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 2 : 4)
     bx -= R(3) * ux * P;
     by -= R(3) * uy * P;
     bz -= R(3) * uz * P;
-    const R cF = R(1) - R(0.5) * om;
     if (FORCE) {
+        const R cF = R(1) - R(0.5) * om;
         dx = cF * (R(9) * dx - R(3) * Fx * P);
         dy = cF * (R(9) * dy - R(3) * Fy * P);
         dz = cF * (R(9) * dz - R(3) * Fz * P);
@@ -125,15 +94,102 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 2 : 4)
     const R betx = om * bx + dx * inv, bety = om * by + dy * inv, betz = om * bz + dz * inv;
     const R keep = R(1) - om;
 #pragma unroll
-    for (int i = 0; i < Q; ++i)
-        __stcs(lam_out + (long long)i * qs + c,
-               keep * mu[i] + alpha + R(ex(i)) * betx + R(ey(i)) * bety + R(ez(i)) * betz);
+    for (int i = 0; i < Q; ++i) mu[i] = keep * mu[i] + alpha + R(ex(i)) * betx + R(ey(i)) * bety + R(ez(i)) * betz;
+    const R h = R(0.5) * inv;
+    gx = bx + dx * h;
+    gy = by + dy * h;
+    gz = bz + dz * h;
+}
+
+// One reverse step for the two x-adjacent cells x0, x0 + 1 of a row, in the
+// layout of the forward step kernel. mu = G^T lambda^{n+1} is gathered with the
+// push mask (bit i: x + e_i is solid, so mu_i(x) = lambda_opp(i)(x) from the
+// cell itself); threads whose two cells are solid skip everything.
+template <class R> struct AdjBlocks {
+    static constexpr int value = sizeof(R) == 8 ? 1 : 3;
+};
+
+template <class R, bool FLAGS, bool FORCE>
+__global__ void __launch_bounds__(256, AdjBlocks<R>::value)
+    k_adj_step(const Dev d, const R *__restrict__ lam_in, R *__restrict__ lam_out, const R *__restrict__ tape,
+               R *__restrict__ grad_F) {
+    int x0, y, z;
+    if (!pair_cell(d.g, d.P.nxb, blockDim.x, blockDim.y, blockIdx.x, blockIdx.y, threadIdx.x, threadIdx.y, x0,
+                   y, z))
+        return;
+    const Geom &g = d.g;
+    const bool has1 = x0 + 1 < g.nx;
+    const int c = cell_index(g, x0, y, z);
+    const long long qs = g.qs;
+    uint32_t m0 = 0u, m1 = has1 ? 0u : SOLID_BIT;
+    if (FLAGS) {
+        const uint2 mm = __ldg(reinterpret_cast<const uint2 *>(d.mask + c));
+        m0 = mm.x;
+        m1 |= mm.y;
+    }
+    const bool live0 = !(m0 & SOLID_BIT), live1 = !(m1 & SOLID_BIT);
+    if (FLAGS && !live0 && !live1) return;
+    // mu_i(x) = lambda_i(x + e_i): source columns of the e_x = +-1 populations
+    const int xa = wrap1(x0 - 1, g.nx);              // e_x = -1, cell x0 (e_x = -1 of x0 + 1 reads x0)
+    const int xb = wrap1(x0 + 1, g.nx);              // e_x = +1, cell x0
+    const int xc = has1 ? wrap1(x0 + 2, g.nx) : x0;  // e_x = +1, cell x0 + 1
+    R mu0[Q], mu1[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const int row = (wrap1(z + ez(i), g.nz) * g.ny + wrap1(y + ey(i), g.ny)) * g.pitch;
+        const R *Li = lam_in + (long long)i * qs + row;
+        const R *Lo = lam_in + (long long)opp(i) * qs + c;  // own cell, opposite population
+        const bool b0 = FLAGS && i > 0 && ((m0 >> i) & 1u);
+        const bool b1 = FLAGS && i > 0 && ((m1 >> i) & 1u);
+        if (ex(i) == 0) {
+            if (b0 == b1) {
+                ld2_real(b0 ? Lo : Li + x0, mu0[i], mu1[i]);
+            } else {
+                mu0[i] = __ldg(b0 ? Lo : Li + x0);
+                mu1[i] = __ldg(b1 ? Lo + 1 : Li + x0 + 1);
+            }
+        } else {
+            mu0[i] = __ldg(b0 ? Lo : Li + (ex(i) > 0 ? xb : xa));
+            mu1[i] = __ldg(b1 ? Lo + 1 : Li + (ex(i) > 0 ? xc : x0));
+        }
+    }
+    R rho0, rho1, ux0, ux1, uy0, uy1, uz0, uz1;
+    ld2_real(tape + c, rho0, rho1);
+    ld2_real(tape + qs + c, ux0, ux1);
+    ld2_real(tape + 2 * qs + c, uy0, uy1);
+    ld2_real(tape + 3 * qs + c, uz0, uz1);
+    R F0x = R(0), F0y = R(0), F0z = R(0), F1x = R(0), F1y = R(0), F1z = R(0);
+    if (FORCE) {
+        if (d.Ffield) {
+            const R *F = static_cast<const R *>(d.Ffield);
+            ld2_real(F + c, F0x, F1x);
+            ld2_real(F + qs + c, F0y, F1y);
+            ld2_real(F + 2 * qs + c, F0z, F1z);
+        } else {
+            F0x = F1x = R(d.F[0]);
+            F0y = F1y = R(d.F[1]);
+            F0z = F1z = R(d.F[2]);
+        }
+    }
+    const R om = R(d.omega);
+    R g0x, g0y, g0z, g1x, g1y, g1z;
+    adj_collide<R, FORCE>(mu0, rho0, ux0, uy0, uz0, F0x, F0y, F0z, om, g0x, g0y, g0z);
+    adj_collide<R, FORCE>(mu1, rho1, ux1, uy1, uz1, F1x, F1y, F1z, om, g1x, g1y, g1z);
+    // (a solid cell of a mixed pair gets a value nobody reads)
+#pragma unroll
+    for (int i = 0; i < Q; ++i) st2_real(lam_out + (long long)i * qs + c, mu0[i], mu1[i]);
     if (grad_F) {
-        const long long N = d.n_cells, cc = canon_index(d.g, x, y, z);
-        const R h = R(0.5) * inv;
-        grad_F[cc] += bx + dx * h;
-        grad_F[N + cc] += by + dy * h;
-        grad_F[2 * N + cc] += bz + dz * h;
+        const long long N = d.n_cells, cc = canon_index(g, x0, y, z);
+        if (live0) {
+            grad_F[cc] += g0x;
+            grad_F[N + cc] += g0y;
+            grad_F[2 * N + cc] += g0z;
+        }
+        if (live1) {
+            grad_F[cc + 1] += g1x;
+            grad_F[N + cc + 1] += g1y;
+            grad_F[2 * N + cc + 1] += g1z;
+        }
     }
 }
 
@@ -178,14 +234,17 @@ __global__ void __launch_bounds__(256)
 
 static dim3 grid_of(const Dev &d) { return dim3(d.L.nxb * d.L.nyb, d.g.nz); }
 static dim3 block_of(const Dev &d) { return dim3(d.L.bx_threads, d.L.by_threads); }
+// the reverse step runs on the paired launch of the forward step kernels
+static dim3 pair_grid_of(const Dev &d) { return dim3(d.P.nxb * d.P.nyb, d.g.nz); }
+static dim3 pair_block_of(const Dev &d) { return dim3(d.P.bx_threads, d.P.by_threads); }
 
 template <class R, bool FLAGS>
 static cudaError_t launch_adj_step(const Dev &d, const void *li, void *lo, const void *tape, void *gF) {
     if (d.force_on)
-        k_adj_step<R, FLAGS, true><<<grid_of(d), block_of(d), 0, d.stream>>>(
+        k_adj_step<R, FLAGS, true><<<pair_grid_of(d), pair_block_of(d), 0, d.stream>>>(
             d, static_cast<const R *>(li), static_cast<R *>(lo), static_cast<const R *>(tape), static_cast<R *>(gF));
     else
-        k_adj_step<R, FLAGS, false><<<grid_of(d), block_of(d), 0, d.stream>>>(
+        k_adj_step<R, FLAGS, false><<<pair_grid_of(d), pair_block_of(d), 0, d.stream>>>(
             d, static_cast<const R *>(li), static_cast<R *>(lo), static_cast<const R *>(tape), static_cast<R *>(gF));
     return cudaGetLastError();
 }

@@ -21,7 +21,7 @@ struct lbm_ctx {
     void *lat[2];       // lat[cur] holds the latest post-collision populations
     int cur;
     uint8_t *flags_d;   // padded [qs], 1 = solid (padding included), or null
-    uint32_t *mask_d;   // padded [qs] pull masks for the step kernels, or null
+    uint32_t *mask_d;   // padded [qs] push masks for the step kernels, or null
     void *Ffield_d;     // padded [3][qs] of the arithmetic type, or null
     void *lam[2];       // adjoint lattices (allocated on first seed)
     int lcur;
@@ -279,8 +279,8 @@ lbm_status lbm_create(lbm_ctx **out, int nx, int ny, int nz, double tau, const u
                 }
     }
     ctx->n_fluid = n_fluid;
-    // Pull masks: bit i when the source x - e_i of population i is solid
-    // (periodic), SOLID_BIT on solid cells and padding.
+    // Push masks: bit j when the neighbour x + e_j is solid (periodic), where
+    // the step kernel stores bounce-back values; SOLID_BIT on solid cells and padding.
     std::vector<uint32_t> hmask;
     if (flags) {
         hmask.assign((size_t)qs, SOLID_BIT);
@@ -289,8 +289,8 @@ lbm_status lbm_create(lbm_ctx **out, int nx, int ny, int nz, double tau, const u
                 for (int x = 0; x < nx; ++x) {
                     const int c = cell_index(ctx->g, x, y, z);
                     uint32_t m = hflags[(size_t)c] ? SOLID_BIT : 0u;
-                    for (int i = 1; i < Q; ++i)
-                        if (hflags[(size_t)pull_src(ctx->g, x, y, z, i)]) m |= 1u << i;
+                    for (int j = 1; j < Q; ++j)
+                        if (hflags[(size_t)push_dst(ctx->g, x, y, z, j)]) m |= 1u << j;
                     hmask[(size_t)c] = m;
                 }
     }
@@ -648,13 +648,21 @@ int64_t lbm_check_launch_indices(int nx, int ny, int nz, lbm_storage fmt) {
                     const int c = cell_index(g, x0, y, z);
                     if (c % 2 || !in_row(c - x0, x0) || !in_row(c - x0, x0 + 1)) ++bad;  // pair at c, c + 1
                     const int xa = wrap1(x0 - 1, nx), xb = wrap1(x0 + 1, nx), xc = has1 ? wrap1(x0 + 2, nx) : x0;
+                    for (int j = 1; j < Q; ++j)  // store-side bounce-back targets
+                        if (!cell_ok(push_dst(g, x0, y, z, j)) || (has1 && !cell_ok(push_dst(g, x0 + 1, y, z, j))))
+                            ++bad;
                     for (int i = 0; i < Q; ++i) {
                         const int row = (wrap1(z - ez(i), nz) * ny + wrap1(y - ey(i), ny)) * g.pitch;
+                        // reverse step: mu_i(x) = lambda_i(x + e_i)
+                        const int rowp = (wrap1(z + ez(i), nz) * ny + wrap1(y + ey(i), ny)) * g.pitch;
                         if (ex(i) == 0) {
                             if (!in_row(row, x0) || !in_row(row, x0 + 1) || (row + x0) % 2) ++bad;
+                            if (!in_row(rowp, x0) || !in_row(rowp, x0 + 1) || (rowp + x0) % 2) ++bad;
                         } else {
                             if (!in_row(row, ex(i) > 0 ? xa : xb) || !in_row(row, ex(i) > 0 ? x0 : xc)) ++bad;
                             if ((ex(i) > 0 ? xa : xb) >= nx || (has1 && (ex(i) > 0 ? x0 : xc) >= nx)) ++bad;
+                            if (!in_row(rowp, ex(i) > 0 ? xb : xa) || !in_row(rowp, ex(i) > 0 ? xc : x0)) ++bad;
+                            if ((ex(i) > 0 ? xb : xa) >= nx || (has1 && (ex(i) > 0 ? xc : x0) >= nx)) ++bad;
                         }
                     }
                 }

@@ -86,15 +86,24 @@ template <> struct Stor<LBM_F16S> {
         __stcs(reinterpret_cast<unsigned short *>(p), __half_as_ushort(__float2half_rn(v)));
     }
     static __device__ __forceinline__ T enc(R v) { return __float2half_rn(v); }
+    // pairs move as one 32-bit word and convert with one packed instruction
     static __device__ __forceinline__ void ld2(const T *p, R &a, R &b) {
-        const unsigned v = __ldg(reinterpret_cast<const unsigned *>(p));
-        a = __half2float(__ushort_as_half((unsigned short)(v & 0xffffu)));
-        b = __half2float(__ushort_as_half((unsigned short)(v >> 16)));
+        union {
+            unsigned u;
+            __half2 h;
+        } v;
+        v.u = __ldg(reinterpret_cast<const unsigned *>(p));
+        const float2 f = __half22float2(v.h);
+        a = f.x;
+        b = f.y;
     }
     static __device__ __forceinline__ void st2(T *p, R a, R b) {
-        const unsigned v = (unsigned)__half_as_ushort(__float2half_rn(a)) |
-                           ((unsigned)__half_as_ushort(__float2half_rn(b)) << 16);
-        __stcs(reinterpret_cast<unsigned *>(p), v);
+        union {
+            unsigned u;
+            __half2 h;
+        } v;
+        v.h = __floats2half2_rn(a, b);
+        __stcs(reinterpret_cast<unsigned *>(p), v.u);
     }
 };
 
@@ -110,14 +119,22 @@ template <> struct Stor<LBM_BF16S> {
     }
     static __device__ __forceinline__ T enc(R v) { return __float2bfloat16_rn(v); }
     static __device__ __forceinline__ void ld2(const T *p, R &a, R &b) {
-        const unsigned v = __ldg(reinterpret_cast<const unsigned *>(p));
-        a = __bfloat162float(__ushort_as_bfloat16((unsigned short)(v & 0xffffu)));
-        b = __bfloat162float(__ushort_as_bfloat16((unsigned short)(v >> 16)));
+        union {
+            unsigned u;
+            __nv_bfloat162 h;
+        } v;
+        v.u = __ldg(reinterpret_cast<const unsigned *>(p));
+        const float2 f = __bfloat1622float2(v.h);
+        a = f.x;
+        b = f.y;
     }
     static __device__ __forceinline__ void st2(T *p, R a, R b) {
-        const unsigned v = (unsigned)__bfloat16_as_ushort(__float2bfloat16_rn(a)) |
-                           ((unsigned)__bfloat16_as_ushort(__float2bfloat16_rn(b)) << 16);
-        __stcs(reinterpret_cast<unsigned *>(p), v);
+        union {
+            unsigned u;
+            __nv_bfloat162 h;
+        } v;
+        v.h = __floats2bfloat162_rn(a, b);
+        __stcs(reinterpret_cast<unsigned *>(p), v.u);
     }
 };
 
@@ -197,8 +214,8 @@ LBM_HD bool pair_cell(const Geom &g, int nxb, int bdx, int bdy, int bx, int bz, 
     return x0 < g.nx && y < g.ny && z < g.nz;
 }
 
-// Pull mask of a cell (precomputed on the host from the flags): bit i,
-// 1 <= i <= 18, is set when the source cell x - e_i is solid, so population i
+// Push mask of a cell (precomputed on the host from the flags): bit j,
+// 1 <= j <= 18, is set when the neighbour x + e_j is solid, so population j
 // bounces back; SOLID_BIT is set on solid cells and on row padding.
 constexpr uint32_t SOLID_BIT = 0x80000000u;
 
@@ -247,9 +264,11 @@ template <class R> struct Mom {
 template <class R>
 __device__ __forceinline__ Mom<R> moments(const R s[Q], R Fx, R Fy, R Fz) {
     Mom<R> m;
+    // rho - 1 summed over opposite pairs first: the odd (velocity) parts of
+    // s_i and s_opp(i) cancel exactly before any rounding of the total
     R r = s[0];
 #pragma unroll
-    for (int i = 1; i < Q; ++i) r += s[i];
+    for (int p = 0; p < NPAIR; ++p) r += s[pair_first(p)] + s[opp(pair_first(p))];
     R jx = (s[1] - s[2]) + (s[7] - s[10]) + (s[8] - s[9]) + (s[11] - s[14]) + (s[12] - s[13]);
     R jy = (s[3] - s[4]) + (s[7] - s[10]) + (s[9] - s[8]) + (s[15] - s[18]) + (s[16] - s[17]);
     R jz = (s[5] - s[6]) + (s[11] - s[14]) + (s[13] - s[12]) + (s[15] - s[18]) + (s[17] - s[16]);

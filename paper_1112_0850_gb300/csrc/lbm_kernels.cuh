@@ -76,23 +76,42 @@ __device__ __forceinline__ void gather(const Dev &d, const typename Stor<S>::T *
 // populations with e_x = 0 (rest, +-y, +-z and the yz diagonals) move as one
 // aligned pair per load and every population is stored as one aligned pair;
 // populations with e_x = +-1 come from sources shifted by one cell and are
-// loaded per cell. Bounce-back is decided from a 32-bit pull mask per cell
-// (one coalesced load) instead of 18 neighbour flags: a bounced population
-// loads the opposite population of the cell itself, so every value costs
-// exactly one load either way. Solid cells and row padding are computed on
-// in-bounds data and their results are never read.
+// loaded per cell. Halfway bounce-back is driven by a 32-bit push mask per cell
+// (bit j: x + e_j is solid; the source x - e_i of population i is solid when
+// bit opp(i) is set), in one of two forms:
 //
-// Resident blocks of 256 threads per SM the step kernels are compiled for.
-template <class R> struct MinBlocks {
-    static constexpr int value = sizeof(R) == 8 ? 1 : 2;
+//  - load side (FP64, FP32): a population whose source is solid loads the
+//    opposite population of the cell itself, so each value costs one load;
+//    the loads wait for the mask, and threads whose two cells are solid skip
+//    all loads. Measured fastest when the bytes per thread hide that latency.
+//  - store side (16-bit storage): the gather never looks at the mask. A solid
+//    cell s keeps in slot i the value the fluid cell s + e_i pulls next step,
+//    namely that cell's post-collision population opp(i); so after collision
+//    a fluid cell x writes P*_j(x) into slot opp(j) of every solid neighbour
+//    x + e_j (one writer per slot). The mask is needed only for the stores.
+//    Solid cells are computed on in-bounds data and store nothing. Measured
+//    fastest with the 2-byte formats, whose few bytes per thread cannot hide
+//    a mask load in front of the gather.
+// Either way the fluid cells' own slots hold the post-collision populations,
+// which is what every flag-aware reader (macros, state, reduction) gathers.
+//
+// Resident blocks of 256 threads per SM the step kernels are compiled for:
+// FP64 arithmetic 1 (<= 255 registers), FP32 storage 3 (<= 80), 16-bit
+// storage 4 (<= 64: fewer bytes per thread, so more threads in flight).
+template <int S> struct StepBlocks {
+    static constexpr int value = S == LBM_F64 ? 1 : (S == LBM_F32 ? 3 : 4);
+};
+template <int S> struct StoreSideBounce {
+    static constexpr bool value = S == LBM_F16S || S == LBM_BF16S;
 };
 
 template <int S, bool FLAGS, int FORCE, bool RECORD>
-__global__ void __launch_bounds__(256, MinBlocks<typename Stor<S>::R>::value)
+__global__ void __launch_bounds__(256, StepBlocks<S>::value)
     k_step(const Dev d, const typename Stor<S>::T *__restrict__ src, typename Stor<S>::T *__restrict__ dst,
            typename Stor<S>::R *__restrict__ tape) {
     typedef typename Stor<S>::T T;
     typedef typename Stor<S>::R R;
+    constexpr bool PUSH = StoreSideBounce<S>::value;
     int x0, y, z;
     if (!pair_cell(d.g, d.P.nxb, blockDim.x, blockDim.y, blockIdx.x, blockIdx.y, threadIdx.x, threadIdx.y, x0,
                    y, z))
@@ -107,29 +126,35 @@ __global__ void __launch_bounds__(256, MinBlocks<typename Stor<S>::R>::value)
         m1 |= mm.y;
     }
     const bool live0 = !(m0 & SOLID_BIT), live1 = !(m1 & SOLID_BIT);
-    if (!live0 && !live1) return;
+    if (FLAGS && !PUSH && !live0 && !live1) return;
     // source columns of the e_x = +-1 populations
-    const int xa = wrap1(x0 - 1, g.nx);           // e_x = +1, cell x0
-    const int xb = wrap1(x0 + 1, g.nx);           // e_x = -1, cell x0
+    const int xa = wrap1(x0 - 1, g.nx);              // e_x = +1, cell x0
+    const int xb = wrap1(x0 + 1, g.nx);              // e_x = -1, cell x0
     const int xc = has1 ? wrap1(x0 + 2, g.nx) : x0;  // e_x = -1, cell x0 + 1 (e_x = +1 pulls from x0)
     R s0[Q], s1[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const int row = (wrap1(z - ez(i), g.nz) * g.ny + wrap1(y - ey(i), g.ny)) * g.pitch;
-        const T *Pi = src + (long long)i * g.qs;
-        const T *Po = src + (long long)opp(i) * g.qs;
-        const bool b0 = FLAGS && i > 0 && ((m0 >> i) & 1u);
-        const bool b1 = FLAGS && i > 0 && ((m1 >> i) & 1u);
-        if (ex(i) == 0) {
-            if (b0 == b1) {
-                Stor<S>::ld2(b0 ? Po + c : Pi + row + x0, s0[i], s1[i]);
+        const T *Pi = src + (long long)i * g.qs + row;
+        if (FLAGS && !PUSH && i > 0) {
+            const T *Po = src + (long long)opp(i) * g.qs + c;  // own cell, opposite population
+            const bool b0 = (m0 >> opp(i)) & 1u, b1 = (m1 >> opp(i)) & 1u;
+            if (ex(i) == 0) {
+                if (b0 == b1) {
+                    Stor<S>::ld2(b0 ? Po : Pi + x0, s0[i], s1[i]);
+                } else {
+                    s0[i] = Stor<S>::ld(b0 ? Po : Pi + x0);
+                    s1[i] = Stor<S>::ld(b1 ? Po + 1 : Pi + x0 + 1);
+                }
             } else {
-                s0[i] = Stor<S>::ld(b0 ? Po + c : Pi + row + x0);
-                s1[i] = Stor<S>::ld(b1 ? Po + c + 1 : Pi + row + x0 + 1);
+                s0[i] = Stor<S>::ld(b0 ? Po : Pi + (ex(i) > 0 ? xa : xb));
+                s1[i] = Stor<S>::ld(b1 ? Po + 1 : Pi + (ex(i) > 0 ? x0 : xc));
             }
+        } else if (ex(i) == 0) {
+            Stor<S>::ld2(Pi + x0, s0[i], s1[i]);
         } else {
-            s0[i] = Stor<S>::ld(b0 ? Po + c : Pi + row + (ex(i) > 0 ? xa : xb));
-            s1[i] = Stor<S>::ld(b1 ? Po + c + 1 : Pi + row + (ex(i) > 0 ? x0 : xc));
+            s0[i] = Stor<S>::ld(Pi + (ex(i) > 0 ? xa : xb));
+            s1[i] = Stor<S>::ld(Pi + (ex(i) > 0 ? x0 : xc));
         }
     }
     R F0x = R(0), F0y = R(0), F0z = R(0), F1x = R(0), F1y = R(0), F1z = R(0);
@@ -157,8 +182,27 @@ __global__ void __launch_bounds__(256, MinBlocks<typename Stor<S>::R>::value)
     }
     collide<R, FORCE != 0>(s0, ma, R(d.omega), F0x, F0y, F0z);
     collide<R, FORCE != 0>(s1, mb, R(d.omega), F1x, F1y, F1z);
+    if (!FLAGS || !PUSH || (live0 && live1)) {
+        // (load side: a solid cell of a mixed pair gets a value nobody reads)
 #pragma unroll
-    for (int i = 0; i < Q; ++i) Stor<S>::st2(dst + (long long)i * g.qs + c, s0[i], s1[i]);
+        for (int i = 0; i < Q; ++i) Stor<S>::st2(dst + (long long)i * g.qs + c, s0[i], s1[i]);
+    } else if (live0 || live1) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            if (live0) Stor<S>::st(dst + (long long)i * g.qs + c, s0[i]);
+            if (live1) Stor<S>::st(dst + (long long)i * g.qs + c + 1, s1[i]);
+        }
+    }
+    if (FLAGS && PUSH && ((m0 | m1) & ~SOLID_BIT)) {
+        // store-side bounce-back into the solid neighbours' slots
+#pragma unroll
+        for (int j = 1; j < Q; ++j) {
+            if (live0 && ((m0 >> j) & 1u))
+                Stor<S>::st(dst + (long long)opp(j) * g.qs + push_dst(g, x0, y, z, j), s0[j]);
+            if (live1 && ((m1 >> j) & 1u))
+                Stor<S>::st(dst + (long long)opp(j) * g.qs + push_dst(g, x0 + 1, y, z, j), s1[j]);
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -194,13 +238,16 @@ __global__ void __launch_bounds__(256)
         const int t = push_dst(d.g, x, y, z, i);
         int k = i;
         long long ct = canon_neighbor(d.g, x, y, z, i);
-        if (FLAGS && d.flags[t]) {
+        const bool bounce = FLAGS && d.flags[t];
+        if (bounce) {
             k = opp(i);
             ct = cc;
         }
         const R r1 = rho0 ? rho0[ct] - R(1) : R(0);
         const R v = feq_shifted<R>(k, r1, u0[ct], u0[N + ct], u0[2 * N + ct]);
         P[(long long)i * d.g.qs + c] = Stor<S>::enc(v);
+        // the solid neighbour's slot that the step kernel pulls f_opp(i)(x) from
+        if (bounce) P[(long long)opp(i) * d.g.qs + t] = Stor<S>::enc(v);
     }
 }
 
@@ -242,9 +289,12 @@ __global__ void __launch_bounds__(256)
     for (int i = 0; i < Q; ++i) {
         const int t = push_dst(d.g, x, y, z, i);
         long long off = (long long)i * N + canon_neighbor(d.g, x, y, z, i);
-        if (FLAGS && d.flags[t]) off = (long long)opp(i) * N + cc;
-        IOFmt<S>::put(reinterpret_cast<typename IOFmt<S>::T *>(P) + (long long)i * d.g.qs + c,
-                      IOFmt<D>::get(in + off));
+        const bool bounce = FLAGS && d.flags[t];
+        if (bounce) off = (long long)opp(i) * N + cc;
+        const double v = IOFmt<D>::get(in + off);
+        IOFmt<S>::put(P + (long long)i * d.g.qs + c, v);
+        // the solid neighbour's slot that the step kernel pulls f_opp(i)(x) from
+        if (bounce) IOFmt<S>::put(P + (long long)opp(i) * d.g.qs + t, v);
     }
 }
 
@@ -344,11 +394,7 @@ __global__ void __launch_bounds__(256)
         return;
     const int c = cell_index(d.g, x, y, z);
     const long long qs = d.g.qs, N = d.n_cells, cc = canon_index(d.g, x, y, z);
-    if (FLAGS && d.flags[c]) {
-#pragma unroll
-        for (int i = 0; i < Q; ++i) lam[i * qs + c] = R(0);
-        return;
-    }
+    if (FLAGS && d.flags[c]) return;  // solid cells' adjoint slots are never read
     R s[Q];
     gather<S, FLAGS>(d, P, x, y, z, c, s);
     R Fx = R(0), Fy = R(0), Fz = R(0);
@@ -359,8 +405,7 @@ __global__ void __launch_bounds__(256)
     const R inv = R(1) / m.rho;
     const R base = dr - (gx * m.ux + gy * m.uy + gz * m.uz) * inv;
 #pragma unroll
-    for (int i = 0; i < Q; ++i)
-        lam[i * qs + c] = base + (R(ex(i)) * gx + R(ey(i)) * gy + R(ez(i)) * gz) * inv;
+    for (int i = 0; i < Q; ++i) lam[i * qs + c] = base + (R(ex(i)) * gx + R(ey(i)) * gy + R(ez(i)) * gz) * inv;
     if (grad_F) {
         grad_F[cc] += R(0.5) * gx * inv;
         grad_F[N + cc] += R(0.5) * gy * inv;

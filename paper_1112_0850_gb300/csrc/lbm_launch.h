@@ -15,7 +15,7 @@ struct Dev {
     RowLaunch L;           // one cell per thread
     RowLaunch P;           // two x-adjacent cells per thread (step kernels)
     const uint8_t *flags;  // padded [qs] (1 = solid, also on padding), or nullptr = all fluid
-    const uint32_t *mask;  // padded [qs] pull masks (SOLID_BIT, bounce bits), null iff flags is
+    const uint32_t *mask;  // padded [qs] push masks (SOLID_BIT, bounce bits), null iff flags is
     const void *Ffield;    // padded [3][qs] of R, or nullptr
     double F[3];           // uniform force (used when Ffield == nullptr)
     bool force_on;         // Ffield != nullptr or F != 0
