@@ -315,7 +315,7 @@ def main():
     peak, peak_kind = measured_peaks()
     alg_bytes = n_fluid * PDF_BYTES[storage] + n_cells * flag_bytes
     achieved = alg_bytes / per_launch / 1e9
-    traffic = ncu_traffic(args.case, storage)
+    traffic = ncu_traffic(args.case if args.case == "channel" else "taylor-green-%d" % args.n, storage)
 
     extras = {}
     cpu = None
