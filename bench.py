@@ -240,6 +240,39 @@ def time_steps(torch, lat, steps, warmup):
     return e0.elapsed_time(e1) / 1e3
 
 
+def sweep():
+    """Throughput against domain size (periodic n^3 boxes, the paper's domain
+    sweeps, Sec. 7) and the effect of padding rows to 128 bytes (Sec. 6): MLUPS
+    and fraction of the measured copy bandwidth per case."""
+    import torch
+    from paper_1112_0850_gb300 import build
+    from paper_1112_0850_gb300.lattice import Lattice
+    build.build()
+    peak, _ = measured_peaks()
+
+    def run(n, storage, row_align=0):
+        lat = Lattice(n, n, n, 0.6, storage=storage, row_align=row_align)
+        rng = np.random.default_rng(1)
+        u = torch.tensor(0.01 * rng.standard_normal((3, n, n, n)), dtype=lat.real).cuda()
+        lat.init_equilibrium(u)
+        k = int(min(2000, max(10, 4e9 / n ** 3)))
+        t = time_steps(torch, lat, k, 5) / k
+        pitch = lat.info.pitch
+        lat.close()
+        gbs = n ** 3 * PDF_BYTES[storage] / t / 1e9
+        return {"n": n, "storage": storage, "pitch": pitch, "steps": k, "mlups": n ** 3 / t / 1e6, "gbs": gbs,
+                "frac": gbs / peak}
+
+    sizes = [16, 24, 32, 48, 64, 96, 128, 160, 200, 256, 320, 384, 448, 512]
+    out = {"sweep": [run(n, s) for s in ("f32", "f16s") for n in sizes],
+           "padding": [run(n, s, ra) for s in ("f32", "f16s") for n in (200, 250)
+                       for ra in (0, 2 * {"f32": 4, "f16s": 2}[s])],
+           "note": "periodic boxes, random velocities (0.01), tau 0.6; small boxes fit in the 129 MB L2, so "
+                   "their fraction of HBM copy bandwidth can exceed 1; padding: row_align 0 = 128-byte rows, "
+                   "otherwise rows padded only to a pair of cells"}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -251,10 +284,14 @@ def main():
                     help="headline workload: the walled channel (default) or a periodic Taylor-Green box")
     ap.add_argument("--storage", default="f32", choices=["f64", "f32", "f16s", "bf16s"])
     ap.add_argument("--n", type=int, default=512, help="Taylor-Green box edge")
+    ap.add_argument("--sweep", action="store_true",
+                    help="domain-size sweep of periodic boxes and the row-padding ablation (one JSON line)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
         return reference_arm(args)
+    if args.sweep:
+        return sweep()
 
     import torch
     import torch.distributed as dist

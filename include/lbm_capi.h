@@ -80,6 +80,9 @@ typedef enum {
 typedef struct {
     lbm_storage storage; /* default LBM_F32 */
     void *cuda_stream;   /* cudaStream_t used for every launch and copy; NULL = default stream */
+    int row_align;       /* bytes each padded row starts on (Sec. 6 padding): 0 = 128 (default);
+                            otherwise a power of two >= 2 elements of the storage format (the
+                            kernels move pairs of cells); 2 elements = no padding beyond pairs */
 } lbm_options;
 
 typedef struct {
@@ -95,7 +98,7 @@ typedef struct {
     int64_t steps_done;         /* time steps since the last init or set_state */
 } lbm_info;
 
-/* Fill *opt with defaults (LBM_F32, default stream). */
+/* Fill *opt with defaults (LBM_F32, default stream, 128-byte rows). */
 lbm_status lbm_options_default(lbm_options *opt);
 
 /* Create a context for an nx * ny * nz periodic lattice (Sec. 2: the uniform
@@ -131,7 +134,11 @@ lbm_status lbm_set_force_field(lbm_ctx *ctx, const void *F);
 lbm_status lbm_init_equilibrium(lbm_ctx *ctx, const void *rho, const void *u);
 
 /* Enqueue n >= 0 fused stream-collide time steps (Sec. 2 steps 1-3 with
- * bounce-back; Sec. 6 pull-style update over two grids). Asynchronous. */
+ * bounce-back; Sec. 6 pull-style update over two grids). Asynchronous. Whole
+ * blocks of 32 steps replay a CUDA graph captured on first use (one launch per
+ * block; rebuilt after the force changes), so small lattices are not bound by
+ * launch overhead; the first call that uses a graph should not be made while
+ * the context's stream is being captured. */
 lbm_status lbm_step(lbm_ctx *ctx, int n);
 
 /* Macroscopic fields of the current state (Sec. 2 step 1): rho = sum f_i,
@@ -232,11 +239,12 @@ const char *lbm_status_string(lbm_status s);
 int lbm_lattice_table(int *e, double *w, int *opp);
 
 /* Host-side check of the index arithmetic of every kernel launch the library
- * makes for an nx * ny * nz lattice in format fmt: walks every thread of each
+ * makes for an nx * ny * nz lattice in format fmt with rows aligned to
+ * row_align bytes (as in lbm_options; 0 = 128): walks every thread of each
  * launch configuration on the CPU and verifies that every address it forms
  * lies inside its buffer. Returns the number of violations (0 = all in
- * bounds), or -1 for invalid sizes. Needs no GPU. */
-int64_t lbm_check_launch_indices(int nx, int ny, int nz, lbm_storage fmt);
+ * bounds), or -1 for invalid sizes or alignment. Needs no GPU. */
+int64_t lbm_check_launch_indices(int nx, int ny, int nz, lbm_storage fmt, int row_align);
 
 #ifdef __cplusplus
 }

@@ -22,7 +22,7 @@ Q = 19
 
 
 class lbm_options(ctypes.Structure):
-    _fields_ = [("storage", ctypes.c_int), ("cuda_stream", ctypes.c_void_p)]
+    _fields_ = [("storage", ctypes.c_int), ("cuda_stream", ctypes.c_void_p), ("row_align", ctypes.c_int)]
 
 
 class lbm_info(ctypes.Structure):
@@ -60,7 +60,7 @@ PROTOTYPES = {
     "lbm_last_error": (ctypes.c_char_p, [_vp]),
     "lbm_status_string": (ctypes.c_char_p, [_i]),
     "lbm_lattice_table": (_i, [_vp, _vp, _vp]),
-    "lbm_check_launch_indices": (ctypes.c_int64, [_i, _i, _i, _i]),
+    "lbm_check_launch_indices": (ctypes.c_int64, [_i, _i, _i, _i, _i]),
 }
 
 _lib = None

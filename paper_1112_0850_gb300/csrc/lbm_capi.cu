@@ -22,6 +22,9 @@ struct lbm_ctx {
     int cur;
     uint8_t *flags_d;   // padded [qs], 1 = solid (padding included), or null
     uint32_t *mask_d;   // padded [qs] push masks for the step kernels, or null
+    uint32_t *links_d;  // bounce-back links (fluid cell, solid cell), grouped by direction
+    int link_off[20];
+    int link_max;
     void *Ffield_d;     // padded [3][qs] of the arithmetic type, or null
     void *lam[2];       // adjoint lattices (allocated on first seed)
     int lcur;
@@ -33,6 +36,10 @@ struct lbm_ctx {
     size_t staging_bytes;
     int64_t n_fluid;
     int64_t steps_done;
+    // CUDA graphs of GRAPH_STEPS consecutive steps, one per starting lattice
+    // (lat[0] or lat[1] as source); rebuilt when the step parameters change
+    cudaGraphExec_t graph[2];
+    bool graph_failed;
     std::string err;
 };
 
@@ -54,9 +61,13 @@ size_t real_size(lbm_storage s) { return s == LBM_F64 ? 8 : 4; }
 
 bool valid_storage(int s) { return s >= LBM_F64 && s <= LBM_BF16S; }
 
-// Elements per padded row so that each row starts on a 128-byte boundary.
-int pitch_for(int nx, lbm_storage s) {
-    int per = 128 / (int)storage_bytes(s);
+// Elements per padded row so that each row starts on a row_align-byte
+// boundary (0 = 128 bytes); -1 if row_align is not allowed.
+int pitch_for(int nx, lbm_storage s, int row_align = 0) {
+    const int eb = (int)storage_bytes(s);
+    const int align = row_align ? row_align : 128;
+    if (align < 2 * eb || (align & (align - 1)) || align > 4096) return -1;
+    const int per = align / eb;
     return (nx + per - 1) / per * per;
 }
 
@@ -82,6 +93,18 @@ Dev make_dev(const lbm_ctx *ctx) {
     d.F[2] = ctx->F[2];
     d.force_on = ctx->Ffield_d != nullptr || ctx->F[0] != 0.0 || ctx->F[1] != 0.0 || ctx->F[2] != 0.0;
     d.omega = 1.0 / ctx->tau;
+    const double cF = 1.0 - 0.5 * d.omega;
+    for (int p = 0; p < NPAIR; ++p) {
+        const int i = pair_first(p);
+        const double eF = ex(i) * ctx->F[0] + ey(i) * ctx->F[1] + ez(i) * ctx->F[2];
+        d.gA[p] = 9.0 * cF * weight(i) * eF;
+        d.gC[p] = 3.0 * cF * weight(i) * eF;
+        d.gAf[p] = (float)d.gA[p];
+        d.gCf[p] = (float)d.gC[p];
+    }
+    d.links = ctx->links_d;
+    for (int j = 0; j < 20; ++j) d.link_off[j] = ctx->link_off[j];
+    d.link_max = ctx->link_max;
     d.status = ctx->status_d;
     d.stream = ctx->stream;
     d.n_cells = (long long)ctx->g.nx * ctx->g.ny * ctx->g.nz;
@@ -174,12 +197,23 @@ lbm_status check_ctx(const lbm_ctx *ctx) {
     return LBM_OK;
 }
 
+// Steps per captured graph (even, so a replay ends on the lattice it began on).
+constexpr int GRAPH_STEPS = 32;
+
+void drop_graphs(lbm_ctx *ctx) {
+    for (int k = 0; k < 2; ++k) {
+        if (ctx->graph[k]) cudaGraphExecDestroy(ctx->graph[k]);
+        ctx->graph[k] = nullptr;
+    }
+}
+
 void free_ctx(lbm_ctx *ctx) {
     if (!ctx) return;
     cudaSetDevice(ctx->device);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
-    void *ptrs[] = {ctx->lat[0],       ctx->lat[1], ctx->flags_d,  ctx->mask_d,    ctx->Ffield_d, ctx->lam[0],
-                    ctx->lam[1], ctx->red_partials, ctx->red_out, ctx->status_d, ctx->staging};
+    drop_graphs(ctx);
+    void *ptrs[] = {ctx->lat[0], ctx->lat[1],  ctx->flags_d,     ctx->mask_d,   ctx->links_d, ctx->Ffield_d,
+                    ctx->lam[0], ctx->lam[1], ctx->red_partials, ctx->red_out, ctx->status_d, ctx->staging};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete ctx;
@@ -193,6 +227,7 @@ lbm_status lbm_options_default(lbm_options *opt) {
     if (!opt) return LBM_ERR_ARG;
     opt->storage = LBM_F32;
     opt->cuda_stream = nullptr;
+    opt->row_align = 0;
     return LBM_OK;
 }
 
@@ -205,7 +240,8 @@ lbm_status lbm_create(lbm_ctx **out, int nx, int ny, int nz, double tau, const u
     if (opt) o = *opt;
     if (nx < 1 || ny < 1 || nz < 1 || nz > 65535 || !(tau > 0.5) || !valid_storage(o.storage))
         return LBM_ERR_ARG;
-    const int pitch = pitch_for(nx, o.storage);
+    const int pitch = pitch_for(nx, o.storage, o.row_align);
+    if (pitch < 0) return LBM_ERR_ARG;
     const long long qs = (long long)nz * ny * pitch;
     if (qs >= (1LL << 31)) return LBM_ERR_ARG;
     const long long N = (long long)nx * ny * nz;
@@ -226,6 +262,9 @@ lbm_status lbm_create(lbm_ctx **out, int nx, int ny, int nz, double tau, const u
     ctx->cur = 0;
     ctx->flags_d = nullptr;
     ctx->mask_d = nullptr;
+    ctx->links_d = nullptr;
+    for (int j = 0; j < 20; ++j) ctx->link_off[j] = 0;
+    ctx->link_max = 0;
     ctx->Ffield_d = nullptr;
     ctx->lam[0] = ctx->lam[1] = nullptr;
     ctx->lcur = 0;
@@ -235,6 +274,8 @@ lbm_status lbm_create(lbm_ctx **out, int nx, int ny, int nz, double tau, const u
     ctx->staging = nullptr;
     ctx->staging_bytes = 0;
     ctx->steps_done = 0;
+    ctx->graph[0] = ctx->graph[1] = nullptr;
+    ctx->graph_failed = false;
     cudaError_t e = cudaGetDevice(&ctx->device);
     if (e != cudaSuccess) {
         delete ctx;
@@ -281,6 +322,32 @@ lbm_status lbm_create(lbm_ctx **out, int nx, int ny, int nz, double tau, const u
     ctx->n_fluid = n_fluid;
     // Push masks: bit j when the neighbour x + e_j is solid (periodic), where
     // the step kernel stores bounce-back values; SOLID_BIT on solid cells and padding.
+    // Bounce-back links for the separate-kernel form: (fluid cell, solid
+    // neighbour x + e_j) grouped by direction j, cells in increasing order.
+    std::vector<uint32_t> hlinks;
+    if (flags) {
+        std::vector<std::vector<uint32_t>> per(Q);
+        for (int z = 0; z < nz; ++z)
+            for (int y = 0; y < ny; ++y)
+                for (int x = 0; x < nx; ++x) {
+                    const int c = cell_index(ctx->g, x, y, z);
+                    if (hflags[(size_t)c]) continue;
+                    for (int j = 1; j < Q; ++j) {
+                        const int t = push_dst(ctx->g, x, y, z, j);
+                        if (hflags[(size_t)t]) {
+                            per[j].push_back((uint32_t)c);
+                            per[j].push_back((uint32_t)t);
+                        }
+                    }
+                }
+        ctx->link_off[0] = ctx->link_off[1] = 0;
+        for (int j = 1; j < Q; ++j) {
+            const int cnt = (int)(per[j].size() / 2);
+            ctx->link_off[j + 1] = ctx->link_off[j] + cnt;
+            if (cnt > ctx->link_max) ctx->link_max = cnt;
+            hlinks.insert(hlinks.end(), per[j].begin(), per[j].end());
+        }
+    }
     std::vector<uint32_t> hmask;
     if (flags) {
         hmask.assign((size_t)qs, SOLID_BIT);
@@ -302,6 +369,8 @@ lbm_status lbm_create(lbm_ctx **out, int nx, int ny, int nz, double tau, const u
               cudaMalloc((void **)&ctx->status_d, sizeof(unsigned)) == cudaSuccess;
     if (ok && flags) ok = cudaMalloc((void **)&ctx->flags_d, (size_t)qs) == cudaSuccess;
     if (ok && flags) ok = cudaMalloc((void **)&ctx->mask_d, (size_t)qs * sizeof(uint32_t)) == cudaSuccess;
+    if (ok && !hlinks.empty())
+        ok = cudaMalloc((void **)&ctx->links_d, hlinks.size() * sizeof(uint32_t)) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         free_ctx(ctx);
@@ -313,6 +382,9 @@ lbm_status lbm_create(lbm_ctx **out, int nx, int ny, int nz, double tau, const u
     if (ok && flags) ok = cudaMemcpy(ctx->flags_d, hflags.data(), (size_t)qs, cudaMemcpyHostToDevice) == cudaSuccess;
     if (ok && flags)
         ok = cudaMemcpy(ctx->mask_d, hmask.data(), (size_t)qs * sizeof(uint32_t), cudaMemcpyHostToDevice) ==
+             cudaSuccess;
+    if (ok && !hlinks.empty())
+        ok = cudaMemcpy(ctx->links_d, hlinks.data(), hlinks.size() * sizeof(uint32_t), cudaMemcpyHostToDevice) ==
              cudaSuccess;
     if (ok) ok = cudaStreamSynchronize(ctx->stream) == cudaSuccess;
     if (!ok) {
@@ -345,12 +417,18 @@ lbm_status lbm_get_info(const lbm_ctx *ctx, lbm_info *info) {
 
 lbm_status lbm_set_uniform_force(lbm_ctx *ctx, const double force[3]) {
     if (check_ctx(ctx)) return LBM_ERR_ARG;
+    cudaStreamSynchronize(ctx->stream);
+    drop_graphs(ctx);  // the force is a kernel argument baked into the graphs
     for (int a = 0; a < 3; ++a) ctx->F[a] = force ? force[a] : 0.0;
     return LBM_OK;
 }
 
 lbm_status lbm_set_force_field(lbm_ctx *ctx, const void *F) {
     if (check_ctx(ctx)) return LBM_ERR_ARG;
+    if ((F != nullptr) != (ctx->Ffield_d != nullptr)) {  // the force mode is baked into the graphs
+        cudaStreamSynchronize(ctx->stream);
+        drop_graphs(ctx);
+    }
     if (!F) {
         if (ctx->Ffield_d) {
             cudaStreamSynchronize(ctx->stream);
@@ -399,9 +477,49 @@ lbm_status lbm_init_equilibrium(lbm_ctx *ctx, const void *rho, const void *u) {
     return LBM_OK;
 }
 
+// Capture GRAPH_STEPS steps starting from lattice `from` into ctx->graph[from]
+// (on a private stream; the graph is then launched on the context's stream).
+// Returns false, leaving no graph, if capture or instantiation fails.
+static bool build_graph(lbm_ctx *ctx, int from) {
+    cudaStream_t cs = nullptr;
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    Dev d = make_dev(ctx);
+    d.stream = cs;
+    cudaGraph_t graph = nullptr;
+    bool ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    for (int k = 0; ok && k < GRAPH_STEPS; ++k) {
+        const int c = from ^ (k & 1);
+        ok = LBM_DISPATCH(ctx, step(d, ctx->lat[c], ctx->lat[c ^ 1], nullptr)) == cudaSuccess;
+    }
+    const bool ended = cudaStreamEndCapture(cs, &graph) == cudaSuccess;
+    ok = ok && ended && graph && cudaGraphInstantiate(&ctx->graph[from], graph, 0) == cudaSuccess;
+    if (graph) cudaGraphDestroy(graph);
+    cudaStreamDestroy(cs);
+    if (!ok) {
+        cudaGetLastError();
+        ctx->graph[from] = nullptr;
+    }
+    return ok;
+}
+
 lbm_status lbm_step(lbm_ctx *ctx, int n) {
     if (check_ctx(ctx)) return LBM_ERR_ARG;
     if (n < 0) return fail(ctx, LBM_ERR_ARG, "n must be >= 0");
+    // whole blocks of GRAPH_STEPS steps replay a captured graph (one launch
+    // instead of GRAPH_STEPS); the remainder is launched step by step
+    while (n >= GRAPH_STEPS && !ctx->graph_failed) {
+        if (!ctx->graph[ctx->cur] && !build_graph(ctx, ctx->cur)) {
+            ctx->graph_failed = true;
+            break;
+        }
+        cudaError_t e = cudaGraphLaunch(ctx->graph[ctx->cur], ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "stream-collide graph launch");
+        n -= GRAPH_STEPS;
+        ctx->steps_done += GRAPH_STEPS;
+    }
     Dev d = make_dev(ctx);
     for (int k = 0; k < n; ++k) {
         cudaError_t e = LBM_DISPATCH(ctx, step(d, ctx->lat[ctx->cur], ctx->lat[ctx->cur ^ 1], nullptr));
@@ -598,13 +716,14 @@ int lbm_lattice_table(int *e, double *w, int *o) {
 
 // Walk every thread of the row launch (and the reduction's cell loop) on the
 // host, forming the same addresses as the kernels with the same helpers.
-int64_t lbm_check_launch_indices(int nx, int ny, int nz, lbm_storage fmt) {
+int64_t lbm_check_launch_indices(int nx, int ny, int nz, lbm_storage fmt, int row_align) {
     if (nx < 1 || ny < 1 || nz < 1 || nz > 65535 || !valid_storage(fmt)) return -1;
     Geom g;
     g.nx = nx;
     g.ny = ny;
     g.nz = nz;
-    g.pitch = pitch_for(nx, fmt);
+    g.pitch = pitch_for(nx, fmt, row_align);
+    if (g.pitch < 0) return -1;
     g.qs = (long long)nz * ny * g.pitch;
     if (g.qs >= (1LL << 31)) return -1;
     const RowLaunch L = row_launch(g);
@@ -667,7 +786,7 @@ int64_t lbm_check_launch_indices(int nx, int ny, int nz, lbm_storage fmt) {
                     }
                 }
     if (visited2 != N) ++bad;
-    if (P.bx_threads * P.by_threads != 256 || P.bx_threads % 32) ++bad;
+    if (P.bx_threads * P.by_threads > 256 || P.bx_threads % 32 || P.by_threads < 1) ++bad;
     if (L.bx_threads * L.by_threads != 256 || L.bx_threads % 32) ++bad;
     // reduction: canonical walk
     for (long long cc = 0; cc < N; ++cc) {

@@ -191,15 +191,17 @@ inline RowLaunch row_launch(const Geom &g) {
 }
 
 // Paired launch of the step kernels: each thread owns the two x-adjacent cells
-// x0 = 2 (xb * bx_threads + tx) and x0 + 1 of row (y, z); blocks hold 256 threads.
+// x0 = 2 (xb * bx_threads + tx) and x0 + 1 of row (y, z). A row's pairs are
+// split into the fewest blocks of at most 256 threads, each a multiple of 32
+// wide, so few lanes idle when nx is not a power of two; rows stack in y up to
+// 256 threads per block.
 inline RowLaunch pair_launch(const Geom &g) {
     RowLaunch L;
     const int half = (g.nx + 1) / 2;
-    int w = 32;
-    while (w < half && w < 256) w *= 2;
-    L.bx_threads = w;
-    L.by_threads = 256 / w;
-    L.nxb = (half + w - 1) / w;
+    L.nxb = (half + 255) / 256;
+    const int per = (half + L.nxb - 1) / L.nxb;
+    L.bx_threads = (per + 31) / 32 * 32;
+    L.by_threads = 256 / L.bx_threads;
     L.nyb = (g.ny + L.by_threads - 1) / L.by_threads;
     return L;
 }
@@ -281,15 +283,39 @@ __device__ __forceinline__ Mom<R> moments(const R s[Q], R Fx, R Fy, R Fz) {
     return m;
 }
 
+// Guo source of one cell with c = 1 - omega/2: rest S_0 = -c uF (3 w_0 = 1),
+// and per opposite pair p (direction i = pair_first(p)):
+//   even part  (e_i.u) A_p - 3 c w_p (u.F),   odd part  C_p,
+//   A_p = 9 c w_p (e_i.F),  C_p = 3 c w_p (e_i.F).
+// A and C depend only on F and tau: a uniform force passes them in precomputed.
+template <class R> struct Guo {
+    R A[NPAIR], C[NPAIR];
+};
+
+template <class R>
+__device__ __forceinline__ Guo<R> guo_terms(R omega, R Fx, R Fy, R Fz) {
+    Guo<R> t;
+    const R cF = R(1) - R(0.5) * omega;
+#pragma unroll
+    for (int p = 0; p < NPAIR; ++p) {
+        const int i = pair_first(p);
+        const R w = i <= 6 ? R(1.0 / 18.0) : R(1.0 / 36.0);
+        const R eF = R(ex(i)) * Fx + R(ey(i)) * Fy + R(ez(i)) * Fz;
+        t.A[p] = R(9) * cF * w * eF;
+        t.C[p] = R(3) * cF * w * eF;
+    }
+    return t;
+}
+
 template <class R, bool FORCE>
-__device__ __forceinline__ void collide(R s[Q], const Mom<R> &m, R omega, R Fx, R Fy, R Fz) {
+__device__ __forceinline__ void collide(R s[Q], const Mom<R> &m, R omega, R Fx, R Fy, R Fz, const Guo<R> &G) {
     const R usq15 = R(1.5) * (m.ux * m.ux + m.uy * m.uy + m.uz * m.uz);
     const R cF = R(1) - R(0.5) * omega;
     const R uF = FORCE ? (m.ux * Fx + m.uy * Fy + m.uz * Fz) : R(0);
     {
         const R w = R(1.0 / 3.0);
         R seq = w * (m.rho1 - m.rho * usq15);
-        R src = FORCE ? cF * w * (R(-3) * uF) : R(0);
+        R src = FORCE ? -cF * uF : R(0);
         s[0] = s[0] + omega * (seq - s[0]) + src;
     }
 #pragma unroll
@@ -301,9 +327,8 @@ __device__ __forceinline__ void collide(R s[Q], const Mom<R> &m, R omega, R Fx, 
         const R odd = w * R(3) * m.rho * eu;
         R fe = R(0), fo = R(0);
         if (FORCE) {
-            const R eF = R(ex(i)) * Fx + R(ey(i)) * Fy + R(ez(i)) * Fz;
-            fe = cF * w * (R(9) * eu * eF - R(3) * uF);
-            fo = cF * w * R(3) * eF;
+            fe = eu * G.A[p] - (R(3) * w) * cF * uF;
+            fo = G.C[p];
         }
         const R a = s[i], b = s[o];
         s[i] = a + omega * (even + odd - a) + (fe + fo);

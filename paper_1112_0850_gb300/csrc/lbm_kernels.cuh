@@ -76,22 +76,21 @@ __device__ __forceinline__ void gather(const Dev &d, const typename Stor<S>::T *
 // populations with e_x = 0 (rest, +-y, +-z and the yz diagonals) move as one
 // aligned pair per load and every population is stored as one aligned pair;
 // populations with e_x = +-1 come from sources shifted by one cell and are
-// loaded per cell. Halfway bounce-back is driven by a 32-bit push mask per cell
-// (bit j: x + e_j is solid; the source x - e_i of population i is solid when
-// bit opp(i) is set), in one of two forms:
+// loaded per cell. Halfway bounce-back takes one of two forms, chosen per
+// storage format by measurement:
 //
-//  - load side (FP64, FP32): a population whose source is solid loads the
-//    opposite population of the cell itself, so each value costs one load;
-//    the loads wait for the mask, and threads whose two cells are solid skip
-//    all loads. Measured fastest when the bytes per thread hide that latency.
-//  - store side (16-bit storage): the gather never looks at the mask. A solid
-//    cell s keeps in slot i the value the fluid cell s + e_i pulls next step,
-//    namely that cell's post-collision population opp(i); so after collision
-//    a fluid cell x writes P*_j(x) into slot opp(j) of every solid neighbour
-//    x + e_j (one writer per slot). The mask is needed only for the stores.
-//    Solid cells are computed on in-bounds data and store nothing. Measured
-//    fastest with the 2-byte formats, whose few bytes per thread cannot hide
-//    a mask load in front of the gather.
+//  - load side (FP64, FP32): a 32-bit push mask per cell (bit j: x + e_j is
+//    solid) is loaded first; a population whose source x - e_i is solid (bit
+//    opp(i)) loads the opposite population of the cell itself, so each value
+//    costs one load; threads whose two cells are solid skip everything.
+//  - separate kernel (16-bit storage), the paper's arrangement (Sec. 7: the
+//    non-fluid cells are treated in a separate kernel): the gather never looks
+//    at flags, because a solid cell s keeps in slot i the value that its fluid
+//    neighbour s + e_i pulls next step (that neighbour's post-collision
+//    population opp(i)). After the step, k_bounce copies those values along a
+//    precomputed list of boundary links. This keeps a dependent load out of
+//    the gather, which the 2-byte formats, with few bytes per thread, cannot
+//    hide.
 // Either way the fluid cells' own slots hold the post-collision populations,
 // which is what every flag-aware reader (macros, state, reduction) gathers.
 //
@@ -101,9 +100,29 @@ __device__ __forceinline__ void gather(const Dev &d, const typename Stor<S>::T *
 template <int S> struct StepBlocks {
     static constexpr int value = S == LBM_F64 ? 1 : (S == LBM_F32 ? 3 : 4);
 };
-template <int S> struct StoreSideBounce {
+template <int S> struct LinkBounce {
     static constexpr bool value = S == LBM_F16S || S == LBM_BF16S;
 };
+
+template <class R> __device__ __forceinline__ Guo<R> uniform_guo(const Dev &d);
+template <> __device__ __forceinline__ Guo<float> uniform_guo<float>(const Dev &d) {
+    Guo<float> t;
+#pragma unroll
+    for (int p = 0; p < NPAIR; ++p) {
+        t.A[p] = d.gAf[p];
+        t.C[p] = d.gCf[p];
+    }
+    return t;
+}
+template <> __device__ __forceinline__ Guo<double> uniform_guo<double>(const Dev &d) {
+    Guo<double> t;
+#pragma unroll
+    for (int p = 0; p < NPAIR; ++p) {
+        t.A[p] = d.gA[p];
+        t.C[p] = d.gC[p];
+    }
+    return t;
+}
 
 template <int S, bool FLAGS, int FORCE, bool RECORD>
 __global__ void __launch_bounds__(256, StepBlocks<S>::value)
@@ -111,7 +130,7 @@ __global__ void __launch_bounds__(256, StepBlocks<S>::value)
            typename Stor<S>::R *__restrict__ tape) {
     typedef typename Stor<S>::T T;
     typedef typename Stor<S>::R R;
-    constexpr bool PUSH = StoreSideBounce<S>::value;
+    constexpr bool LINKS = LinkBounce<S>::value;
     int x0, y, z;
     if (!pair_cell(d.g, d.P.nxb, blockDim.x, blockDim.y, blockIdx.x, blockIdx.y, threadIdx.x, threadIdx.y, x0,
                    y, z))
@@ -119,14 +138,20 @@ __global__ void __launch_bounds__(256, StepBlocks<S>::value)
     const Geom &g = d.g;
     const bool has1 = x0 + 1 < g.nx;
     const int c = cell_index(g, x0, y, z);
-    uint32_t m0 = 0u, m1 = has1 ? 0u : SOLID_BIT;
-    if (FLAGS) {
+    uint32_t m0 = 0u, m1 = 0u;
+    bool live0 = true, live1 = has1;
+    if (FLAGS && !LINKS) {
         const uint2 mm = __ldg(reinterpret_cast<const uint2 *>(d.mask + c));
         m0 = mm.x;
-        m1 |= mm.y;
+        m1 = mm.y;
+        live0 = !(m0 & SOLID_BIT);
+        live1 = has1 && !(m1 & SOLID_BIT);
+        if (!live0 && !live1) return;
+    } else if (FLAGS) {
+        const uchar2 fl = __ldg(reinterpret_cast<const uchar2 *>(d.flags + c));
+        live0 = !fl.x;
+        live1 = has1 && !fl.y;
     }
-    const bool live0 = !(m0 & SOLID_BIT), live1 = !(m1 & SOLID_BIT);
-    if (FLAGS && !PUSH && !live0 && !live1) return;
     // source columns of the e_x = +-1 populations
     const int xa = wrap1(x0 - 1, g.nx);              // e_x = +1, cell x0
     const int xb = wrap1(x0 + 1, g.nx);              // e_x = -1, cell x0
@@ -136,7 +161,7 @@ __global__ void __launch_bounds__(256, StepBlocks<S>::value)
     for (int i = 0; i < Q; ++i) {
         const int row = (wrap1(z - ez(i), g.nz) * g.ny + wrap1(y - ey(i), g.ny)) * g.pitch;
         const T *Pi = src + (long long)i * g.qs + row;
-        if (FLAGS && !PUSH && i > 0) {
+        if (FLAGS && !LINKS && i > 0) {
             const T *Po = src + (long long)opp(i) * g.qs + c;  // own cell, opposite population
             const bool b0 = (m0 >> opp(i)) & 1u, b1 = (m1 >> opp(i)) & 1u;
             if (ex(i) == 0) {
@@ -158,15 +183,20 @@ __global__ void __launch_bounds__(256, StepBlocks<S>::value)
         }
     }
     R F0x = R(0), F0y = R(0), F0z = R(0), F1x = R(0), F1y = R(0), F1z = R(0);
+    Guo<R> G0, G1;
     if (FORCE == 1) {
         F0x = F1x = R(d.F[0]);
         F0y = F1y = R(d.F[1]);
         F0z = F1z = R(d.F[2]);
+        G0 = uniform_guo<R>(d);
+        G1 = G0;
     } else if (FORCE == 2) {
         const R *F = static_cast<const R *>(d.Ffield);
         ld2_real(F + c, F0x, F1x);
         ld2_real(F + g.qs + c, F0y, F1y);
         ld2_real(F + 2 * g.qs + c, F0z, F1z);
+        G0 = guo_terms<R>(R(d.omega), F0x, F0y, F0z);
+        G1 = guo_terms<R>(R(d.omega), F1x, F1y, F1z);
     }
     const Mom<R> ma = moments<R>(s0, F0x, F0y, F0z);
     const Mom<R> mb = moments<R>(s1, F1x, F1y, F1z);
@@ -180,29 +210,46 @@ __global__ void __launch_bounds__(256, StepBlocks<S>::value)
         st2_real(tape + 2 * qs + c, ma.uy, mb.uy);
         st2_real(tape + 3 * qs + c, ma.uz, mb.uz);
     }
-    collide<R, FORCE != 0>(s0, ma, R(d.omega), F0x, F0y, F0z);
-    collide<R, FORCE != 0>(s1, mb, R(d.omega), F1x, F1y, F1z);
-    if (!FLAGS || !PUSH || (live0 && live1)) {
-        // (load side: a solid cell of a mixed pair gets a value nobody reads)
+    collide<R, FORCE != 0>(s0, ma, R(d.omega), F0x, F0y, F0z, G0);
+    collide<R, FORCE != 0>(s1, mb, R(d.omega), F1x, F1y, F1z, G1);
+    // Every pair is stored whole, solid cells included, so 32-byte sectors are
+    // written complete; a solid cell's values are never read (load side), or
+    // its bounce-back slots are overwritten by k_bounce right after (links).
 #pragma unroll
-        for (int i = 0; i < Q; ++i) Stor<S>::st2(dst + (long long)i * g.qs + c, s0[i], s1[i]);
-    } else if (live0 || live1) {
+    for (int i = 0; i < Q; ++i) Stor<S>::st2(dst + (long long)i * g.qs + c, s0[i], s1[i]);
+}
+
+// Bounce-back links (separate-kernel form): for each fluid cell x and
+// direction j with x + e_j solid, slot opp(j) of the solid cell receives the
+// post-collision population j of x, copied bit for bit. Links are grouped by
+// direction (blockIdx.y + 1) and ordered by cell within a direction.
+// Each thread copies LINKS_PER_THREAD links (256 apart, so index loads stay
+// coalesced); all index loads are issued before the value loads, and all value
+// loads before the stores, so the two dependent round trips are shared.
+constexpr int LINKS_PER_THREAD = 4;
+
+template <int S>
+__global__ void __launch_bounds__(256) k_bounce(const Dev d, typename Stor<S>::T *__restrict__ P) {
+    typedef typename Stor<S>::T T;
+    const int j = blockIdx.y + 1;
+    const int base = d.link_off[j], n = d.link_off[j + 1] - base;
+    const int k0 = blockIdx.x * (blockDim.x * LINKS_PER_THREAD) + threadIdx.x;
+    const uint2 *L = reinterpret_cast<const uint2 *>(d.links) + base;
+    const T *from = P + (long long)j * d.g.qs;
+    T *to = P + (long long)opp(j) * d.g.qs;
+    uint2 l[LINKS_PER_THREAD];
+    T v[LINKS_PER_THREAD];
 #pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            if (live0) Stor<S>::st(dst + (long long)i * g.qs + c, s0[i]);
-            if (live1) Stor<S>::st(dst + (long long)i * g.qs + c + 1, s1[i]);
-        }
+    for (int r = 0; r < LINKS_PER_THREAD; ++r) {
+        const int k = k0 + r * blockDim.x;
+        l[r] = k < n ? __ldg(L + k) : make_uint2(0u, 0u);  // (fluid cell, solid cell)
     }
-    if (FLAGS && PUSH && ((m0 | m1) & ~SOLID_BIT)) {
-        // store-side bounce-back into the solid neighbours' slots
 #pragma unroll
-        for (int j = 1; j < Q; ++j) {
-            if (live0 && ((m0 >> j) & 1u))
-                Stor<S>::st(dst + (long long)opp(j) * g.qs + push_dst(g, x0, y, z, j), s0[j]);
-            if (live1 && ((m1 >> j) & 1u))
-                Stor<S>::st(dst + (long long)opp(j) * g.qs + push_dst(g, x0 + 1, y, z, j), s1[j]);
-        }
-    }
+    for (int r = 0; r < LINKS_PER_THREAD; ++r)
+        if (k0 + r * blockDim.x < n) v[r] = from[l[r].x];
+#pragma unroll
+    for (int r = 0; r < LINKS_PER_THREAD; ++r)
+        if (k0 + r * blockDim.x < n) to[l[r].y] = v[r];
 }
 
 // ---------------------------------------------------------------------------
@@ -444,7 +491,13 @@ static cudaError_t launch_step2(const Dev &d, const void *src, void *dst, void *
 
 template <int S>
 cudaError_t Ops<S>::step(const Dev &d, const void *src, void *dst, void *tape) {
-    return d.flags ? launch_step2<S, true>(d, src, dst, tape) : launch_step2<S, false>(d, src, dst, tape);
+    if (!d.flags) return launch_step2<S, false>(d, src, dst, tape);
+    cudaError_t e = launch_step2<S, true>(d, src, dst, tape);
+    if (e != cudaSuccess || !LinkBounce<S>::value || d.link_max == 0) return e;
+    const int per_block = 256 * LINKS_PER_THREAD;
+    k_bounce<S><<<dim3((d.link_max + per_block - 1) / per_block, Q - 1), 256, 0, d.stream>>>(
+        d, static_cast<typename Stor<S>::T *>(dst));
+    return cudaGetLastError();
 }
 
 template <int S>

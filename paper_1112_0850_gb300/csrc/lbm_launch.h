@@ -18,6 +18,11 @@ struct Dev {
     const uint32_t *mask;  // padded [qs] push masks (SOLID_BIT, bounce bits), null iff flags is
     const void *Ffield;    // padded [3][qs] of R, or nullptr
     double F[3];           // uniform force (used when Ffield == nullptr)
+    double gA[9], gC[9];   // Guo constants of the uniform force per opposite pair (see collide)
+    float gAf[9], gCf[9];  // the same, rounded to float
+    const uint32_t *links; // bounce-back links (cell, solid neighbour) grouped by direction, or null
+    int link_off[20];      // links of direction j: [link_off[j], link_off[j + 1]), j = 1..18
+    int link_max;          // largest per-direction count
     bool force_on;         // Ffield != nullptr or F != 0
     double omega;          // 1 / tau
     unsigned *status;      // device status word

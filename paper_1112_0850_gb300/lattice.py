@@ -31,16 +31,16 @@ class Lattice:
     flags: optional uint8 array [nz][ny][nx] (0 fluid, nonzero solid);
     force: optional uniform body force (3,); storage: "f64" | "f32" | "f16s" |
     "bf16s". Work is enqueued on `stream` (default: torch's current stream at
-    construction).
+    construction). row_align: bytes each padded row starts on (0 = 128).
     """
 
-    def __init__(self, nx, ny, nz, tau, flags=None, force=None, storage="f32", stream=None):
+    def __init__(self, nx, ny, nz, tau, flags=None, force=None, storage="f32", stream=None, row_align=0):
         L = capi.lib()
         self.storage = _storage_code(storage)
         self.shape = (nz, ny, nx)
         self.real = _real_dtype(self.storage)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
-        opt = capi.lbm_options(self.storage, ctypes.c_void_p(self.stream.cuda_stream))
+        opt = capi.lbm_options(self.storage, ctypes.c_void_p(self.stream.cuda_stream), int(row_align))
         fl = None
         if flags is not None:
             fl = np.ascontiguousarray(np.asarray(flags.cpu() if torch.is_tensor(flags) else flags), dtype=np.uint8)

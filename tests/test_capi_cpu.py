@@ -56,17 +56,21 @@ SIZES = [(1, 1, 1), (1, 3, 2), (3, 1, 1), (2, 2, 2), (5, 4, 3), (8, 6, 5), (31, 
          (64, 3, 3), (65, 2, 3), (100, 5, 2), (256, 2, 2), (257, 3, 2), (300, 2, 1), (513, 1, 2)]
 
 
+@pytest.mark.parametrize("align", ["default", "pairs"])
 @pytest.mark.parametrize("fmt", [0, 1, 2, 3])
 @pytest.mark.parametrize("size", SIZES, ids=lambda s: "x".join(map(str, s)))
-def test_launch_indices_in_bounds(lib, size, fmt):
+def test_launch_indices_in_bounds(lib, size, fmt, align):
     nx, ny, nz = size
-    assert lib.lbm_check_launch_indices(nx, ny, nz, fmt) == 0
+    row_align = 0 if align == "default" else 2 * capi.STORAGE_BYTES[fmt]  # minimal rows: pairs only
+    assert lib.lbm_check_launch_indices(nx, ny, nz, fmt, row_align) == 0
 
 
 def test_launch_index_check_rejects_bad_sizes(lib):
-    assert lib.lbm_check_launch_indices(0, 4, 4, 1) == -1
-    assert lib.lbm_check_launch_indices(4, 4, 70000, 1) == -1
-    assert lib.lbm_check_launch_indices(4, 4, 4, 9) == -1
+    assert lib.lbm_check_launch_indices(0, 4, 4, 1, 0) == -1
+    assert lib.lbm_check_launch_indices(4, 4, 70000, 1, 0) == -1
+    assert lib.lbm_check_launch_indices(4, 4, 4, 9, 0) == -1
+    assert lib.lbm_check_launch_indices(4, 4, 4, 1, 4) == -1  # narrower than a pair of floats
+    assert lib.lbm_check_launch_indices(4, 4, 4, 1, 24) == -1  # not a power of two
 
 
 def test_status_strings(lib):

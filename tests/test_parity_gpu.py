@@ -297,3 +297,55 @@ def test_create_rejects_bad_arguments():
             Lattice(*args)
     with pytest.raises(LBMError):
         Lattice(4, 4, 4, 0.6, storage=7)
+
+
+@pytest.mark.parametrize("storage", STORAGES)
+def test_unpadded_rows_match_oracle(storage, oracle_results):
+    """Rows padded only to a pair of cells (no 128-byte alignment) give the
+    same results as the default layout."""
+    from paper_1112_0850_gb300.lattice import Lattice
+    ensure_built()
+    name = "ragged_300x5x4"
+    u0, rho0, tau, steps, flags, F, Ff = _case(name)
+    nz, ny, nx = u0.shape[1:]
+    real = REAL[storage]
+    lat = Lattice(nx, ny, nz, tau, flags=flags, force=F, storage=storage,
+                  row_align=2 * {"f64": 8, "f32": 4, "f16s": 2, "bf16s": 2}[storage])
+    assert lat.info.pitch == nx + (nx % 2)
+    lat.init_equilibrium(torch.tensor(u0, dtype=real).cuda(), torch.tensor(rho0, dtype=real).cuda())
+    lat.step(steps)
+    rho, u = lat.macros()
+    _, u_o, _ = oracle_results(name, storage)
+    m = fluid_mask(flags, u0.shape[1:])
+    assert rel_l2(u.double().cpu().numpy(), u_o, m) <= TOL_U[storage]
+    lat.close()
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16s"])
+def test_graph_replay_matches_single_launches(storage):
+    """lbm_step(n) replays captured 32-step graphs; the result equals n single
+    steps bit for bit, also after the uniform force changes (graphs rebuilt)."""
+    from paper_1112_0850_gb300.lattice import Lattice
+    ensure_built()
+    u0, rho0, tau, steps, flags, F, Ff = _case("flags_33x7x5")
+    nz, ny, nx = u0.shape[1:]
+    real = REAL[storage]
+    lats = []
+    for _ in range(2):
+        lat = Lattice(nx, ny, nz, tau, flags=flags, force=F, storage=storage)
+        lat.init_equilibrium(torch.tensor(u0, dtype=real).cuda(), torch.tensor(rho0, dtype=real).cuda())
+        lats.append(lat)
+    a, b = lats
+    a.step(70)  # 2 graph replays + 6 single steps
+    for _ in range(70):
+        b.step(1)
+    assert torch.equal(a.get_state(), b.get_state())
+    F2 = (-3e-5, 1e-5, 2e-5)
+    a.set_uniform_force(F2)
+    b.set_uniform_force(F2)
+    a.step(33)
+    for _ in range(33):
+        b.step(1)
+    assert torch.equal(a.get_state(), b.get_state())
+    a.close()
+    b.close()
