@@ -77,12 +77,22 @@ typedef enum {
 #define LBM_STATUS_DIVERGED 0x1u /* some fluid cell had rho <= 0 or non-finite rho */
 #define LBM_STATUS_INDEX    0x2u /* a checked build caught an out-of-range index */
 
+/* Streaming pattern: how the fused update moves populations through memory. */
+typedef enum {
+    LBM_PATTERN_PULL = 0, /* two lattices (Sec. 2, Sec. 6): each step gathers from the
+                             neighbours in one lattice and stores at the cell in the other */
+    LBM_PATTERN_AA = 1    /* one lattice updated in place, alternating a local step and a
+                             neighbour step (the AA pattern of Bailey et al., 2009): the
+                             same bytes per update, half the population memory */
+} lbm_pattern;
+
 typedef struct {
     lbm_storage storage; /* default LBM_F32 */
     void *cuda_stream;   /* cudaStream_t used for every launch and copy; NULL = default stream */
     int row_align;       /* bytes each padded row starts on (Sec. 6 padding): 0 = 128 (default);
                             otherwise a power of two >= 2 elements of the storage format (the
                             kernels move pairs of cells); 2 elements = no padding beyond pairs */
+    lbm_pattern pattern; /* default LBM_PATTERN_PULL */
 } lbm_options;
 
 typedef struct {
@@ -96,22 +106,25 @@ typedef struct {
     size_t lattice_bytes;       /* bytes of one padded population lattice (19 arrays) */
     size_t tape_bytes_per_step; /* bytes lbm_step_record writes per step */
     int64_t steps_done;         /* time steps since the last init or set_state */
+    lbm_pattern pattern;        /* streaming pattern (one lattice for LBM_PATTERN_AA, else two) */
 } lbm_info;
 
-/* Fill *opt with defaults (LBM_F32, default stream, 128-byte rows). */
+/* Fill *opt with defaults (LBM_F32, default stream, 128-byte rows, LBM_PATTERN_PULL). */
 lbm_status lbm_options_default(lbm_options *opt);
 
 /* Create a context for an nx * ny * nz periodic lattice (Sec. 2: the uniform
  * grid of lattice nodes, two lattices for the stream-collide update, Sec. 6).
  *   tau   relaxation time of Eq. 1; must exceed 0.5 (viscosity (tau - 1/2)/3).
- *   flags nullable (= all fluid); uint8 [nz][ny][nx], 0 = fluid, nonzero =
- *         solid (obstacle, bounce-back per Sec. 2); host or device; copied.
+ *   flags nullable (= all fluid); uint8 [nz][ny][nx], 0 = fluid, 2 = wall
+ *         moving with the velocity set by lbm_set_wall_velocity (the lid of
+ *         the paper's lid-driven cavity, Sec. 7), any other nonzero value =
+ *         solid at rest (obstacle, bounce-back per Sec. 2); host or device; copied.
  *   force nullable (= zero); host array of 3 doubles: uniform body-force
  *         density in lattice units.
  *   opt   nullable (= defaults).
  * Sizes: 1 <= nx, ny; 1 <= nz <= 65535; padded cells nz * ny * pitch < 2^31.
- * Returns LBM_ERR_OOM if two lattices do not fit in free device memory. The
- * lattices are zero (rest state) after creation. */
+ * Returns LBM_ERR_OOM if the lattices (two; one with LBM_PATTERN_AA) do not
+ * fit in free device memory. The state is the rest state after creation. */
 lbm_status lbm_create(lbm_ctx **out, int nx, int ny, int nz, double tau, const uint8_t *flags,
                       const double force[3], const lbm_options *opt);
 
@@ -122,6 +135,12 @@ lbm_status lbm_get_info(const lbm_ctx *ctx, lbm_info *info);
 
 /* Replace the uniform body force (host array of 3 doubles; NULL = zero). */
 lbm_status lbm_set_uniform_force(lbm_ctx *ctx, const double force[3]);
+
+/* Velocity u_w of the cells flagged 2 (host array of 3 doubles; NULL = rest).
+ * A population bounced back from such a wall gains 6 w_i (e_i . u_w), the
+ * halfway bounce-back rule for a moving wall (Ladd) with the wall density
+ * taken as the reference density 1. Applies from the next step on. */
+lbm_status lbm_set_wall_velocity(lbm_ctx *ctx, const double u_w[3]);
 
 /* Install a per-cell force field F: real [3][nz][ny][nx], host or device,
  * copied into the context. NULL removes the field (back to the uniform force). */
@@ -134,7 +153,9 @@ lbm_status lbm_set_force_field(lbm_ctx *ctx, const void *F);
 lbm_status lbm_init_equilibrium(lbm_ctx *ctx, const void *rho, const void *u);
 
 /* Enqueue n >= 0 fused stream-collide time steps (Sec. 2 steps 1-3 with
- * bounce-back; Sec. 6 pull-style update over two grids). Asynchronous. Whole
+ * bounce-back; Sec. 6 pull-style update over two grids, or the in-place AA
+ * update when the context was created with LBM_PATTERN_AA; both give the same
+ * f^n sequence, and every other call sees the same state). Asynchronous. Whole
  * blocks of 32 steps replay a CUDA graph captured on first use (one launch per
  * block; rebuilt after the force changes), so small lattices are not bound by
  * launch overhead; the first call that uses a graph should not be made while

@@ -37,7 +37,7 @@ class Oracle:
         L.oracle_round.argtypes = [ctypes.c_double, ci]
         L.oracle_round.restype = ctypes.c_double
         L.oracle_init.argtypes = [ci] * 3 + [vp, vp, vp, vp, ci]
-        L.oracle_run.argtypes = [ci] * 3 + [ctypes.c_double, vp, vp, ci, vp, ci, ci, ci]
+        L.oracle_run.argtypes = [ci] * 3 + [ctypes.c_double, vp, vp, ci, vp, vp, ci, ci, ci]
         L.oracle_run.restype = ci
         L.oracle_macros.argtypes = [ci] * 3 + [vp, vp, ci, vp, vp, vp]
         L.oracle_sums.argtypes = [ci] * 3 + [vp, vp, ci, vp, vp]
@@ -91,15 +91,18 @@ class Oracle:
         self.lib.oracle_init(nx, ny, nz, _vp(fl), _vp(r0), _vp(u0), _vp(f), FMT[fmt])
         return f
 
-    def run(self, f, tau, steps, flags=None, F=None, fmt=None, threads=None):
-        """Advance state f by `steps` collide-and-stream steps; returns a new array."""
+    def run(self, f, tau, steps, flags=None, F=None, fmt=None, threads=None, u_wall=None):
+        """Advance state f by `steps` collide-and-stream steps; returns a new array.
+
+        Cells flagged 2 are walls moving with velocity u_wall (3,)."""
         f = np.array(f, dtype=np.float64, order="C", copy=True)
         shape = f.shape[1:]
         nz, ny, nx = shape
         fl = _flags(flags, shape)
         Fa, per_cell = _force(F, shape)
+        uw = None if u_wall is None else _f64(u_wall)
         nt = threads if threads else self.lib.oracle_max_threads()
-        rc = self.lib.oracle_run(nx, ny, nz, float(tau), _vp(fl), _vp(Fa), per_cell, _vp(f),
+        rc = self.lib.oracle_run(nx, ny, nz, float(tau), _vp(fl), _vp(Fa), per_cell, _vp(uw), _vp(f),
                                  int(steps), FMT[fmt], int(nt))
         if rc != 0:
             raise MemoryError("oracle_run could not allocate its second lattice")
@@ -172,8 +175,8 @@ def init_equilibrium(u0, rho0=None, flags=None, fmt=None):
     return default().init_equilibrium(u0, rho0, flags, fmt)
 
 
-def run(f, tau, steps, flags=None, F=None, fmt=None, threads=None):
-    return default().run(f, tau, steps, flags, F, fmt, threads)
+def run(f, tau, steps, flags=None, F=None, fmt=None, threads=None, u_wall=None):
+    return default().run(f, tau, steps, flags, F, fmt, threads, u_wall)
 
 
 def macros(f, flags=None, F=None):

@@ -49,8 +49,11 @@ def moments(f, F, fluid):
     return rho, u
 
 
-def step(f, tau, fluid, F):
-    """One collide-and-push step (Sec. 2 steps 1-3 and the bounce-back rule)."""
+def step(f, tau, fluid, F, moving=None, u_wall=None):
+    """One collide-and-push step (Sec. 2 steps 1-3 and the bounce-back rule).
+
+    moving: bool mask of walls moving with u_wall; a population reflected off
+    one loses 6 w_i (e_i . u_wall) (halfway bounce-back for a moving wall)."""
     rho, u = moments(f, F, fluid)
     feq = equilibrium(rho, u)
     uF = (u * F).sum(0)
@@ -65,33 +68,40 @@ def step(f, tau, fluid, F):
         dest_fluid = torch.roll(fluid, shifts=(-ez, -ey, -ex), dims=(0, 1, 2))
         pushed = torch.where(fluid & dest_fluid, fstar, torch.zeros_like(fstar))
         new[i] = new[i] + torch.roll(pushed, shifts=(ez, ey, ex), dims=(0, 1, 2))
-        bounced = torch.where(fluid & ~dest_fluid, fstar, torch.zeros_like(fstar))
+        refl = fstar
+        if moving is not None and u_wall is not None:
+            dest_moving = torch.roll(moving, shifts=(-ez, -ey, -ex), dims=(0, 1, 2))
+            eu_w = ex * float(u_wall[0]) + ey * float(u_wall[1]) + ez * float(u_wall[2])
+            refl = fstar - 6.0 * w * eu_w * dest_moving.to(fstar.dtype)
+        bounced = torch.where(fluid & ~dest_fluid, refl, torch.zeros_like(fstar))
         new[_OPP[i]] = new[_OPP[i]] + bounced
     return torch.stack(new)
 
 
-def forward(u0, F, tau, steps, flags=None, rho0=None):
-    """f^0 = f_eq(rho0, u0) at fluid cells, then `steps` updates; returns (rho_T, u_T, f_T)."""
+def forward(u0, F, tau, steps, flags=None, rho0=None, u_wall=None):
+    """f^0 = f_eq(rho0, u0) at fluid cells, then `steps` updates; returns (rho_T, u_T, f_T).
+    Cells flagged 2 are walls moving with u_wall."""
     shape = u0.shape[1:]
     fluid = _fluid_mask(flags, shape)
+    moving = None if flags is None else torch.as_tensor(flags) == 2
     rho_init = torch.ones(shape, dtype=u0.dtype) if rho0 is None else rho0
     f = equilibrium(rho_init, u0) * fluid
     for _ in range(steps):
-        f = step(f, tau, fluid, F)
+        f = step(f, tau, fluid, F, moving, u_wall)
     rho, u = moments(f, F, fluid)
     return rho * fluid, u * fluid, f
 
 
-def velocity_loss(u0, F, tau, steps, u_target, flags=None):
+def velocity_loss(u0, F, tau, steps, u_target, flags=None, u_wall=None):
     """L = 1/2 sum over fluid cells of |u(T) - u_target|^2."""
     shape = u0.shape[1:]
     fluid = _fluid_mask(flags, shape)
-    _, u, _ = forward(u0, F, tau, steps, flags)
+    _, u, _ = forward(u0, F, tau, steps, flags, u_wall=u_wall)
     r = (u - u_target) * fluid
     return 0.5 * (r * r).sum()
 
 
-def gradients(u0, F, tau, steps, u_target, flags=None):
+def gradients(u0, F, tau, steps, u_target, flags=None, u_wall=None):
     """(L, dL/du0 [3][nz][ny][nx], dL/dF [3][nz][ny][nx]) in float64 by autograd.
 
     u0, F and u_target are numpy or torch arrays; F is a per-cell force field.
@@ -99,7 +109,7 @@ def gradients(u0, F, tau, steps, u_target, flags=None):
     u0 = torch.as_tensor(u0, dtype=torch.float64).clone().requires_grad_(True)
     F = torch.as_tensor(F, dtype=torch.float64).clone().requires_grad_(True)
     ut = torch.as_tensor(u_target, dtype=torch.float64)
-    L = velocity_loss(u0, F, tau, steps, ut, flags)
+    L = velocity_loss(u0, F, tau, steps, ut, flags, u_wall)
     gu, gF = torch.autograd.grad(L, (u0, F))
     fluid = _fluid_mask(flags, u0.shape[1:])
     return L.item(), (gu * fluid).numpy(), (gF * fluid).numpy()

@@ -22,6 +22,10 @@
  *     S_i = (1 - 1/(2 tau)) w_i [3 (e_i - u) + 9 (e_i.u) e_i] . F.
  *   - bounce-back is the halfway rule: a population pushed into a solid cell
  *     returns to its origin with the opposite velocity in the same step.
+ *   - a solid cell flagged 2 is a wall moving with velocity u_w (the paper's
+ *     lid-driven cavity, Sec. 7): the reflected population loses
+ *     2 w_i rho_w (e_i . u_w) / c_s^2 = 6 w_i (e_i . u_w), with the wall
+ *     density rho_w taken as the reference density 1 (Ladd's rule).
  *   - all three axes are periodic; walls are solid flag layers.
  * The state is the pre-collision populations f^n (push form), canonical layout
  * f[i][z][y][x], x fastest. Solid cells hold zeros.
@@ -143,6 +147,11 @@ static int is_fluid(const uint8_t *flags, int64_t c)
     return flags == NULL || flags[c] == 0;
 }
 
+static int is_moving_wall(const uint8_t *flags, int64_t c)
+{
+    return flags != NULL && flags[c] == 2;
+}
+
 /* ---- storage rounding emulation (ties to even) ---------------------------
  * A binary format with `mant` stored mantissa bits and smallest normal
  * exponent emin: values in [2^e, 2^(e+1)) are spaced 2^(max(e,emin) - mant)
@@ -205,8 +214,8 @@ void oracle_init(int nx, int ny, int nz, const uint8_t *flags, const double *rho
 /* One collide-and-push step from cur to nxt (Sec. 2 steps 1-3 plus the
  * bounce-back rule). Every fluid entry of nxt is written exactly once. */
 static void step_once(int nx, int ny, int nz, double tau, const uint8_t *flags,
-                      const double *F, int F_per_cell, const double *cur, double *nxt,
-                      int nthreads)
+                      const double *F, int F_per_cell, const double *u_wall, const double *cur,
+                      double *nxt, int nthreads)
 {
     int64_t N = (int64_t)nx * ny * nz;
     memset(nxt, 0, sizeof(double) * Q * N);
@@ -226,10 +235,15 @@ static void step_once(int nx, int ny, int nz, double tau, const uint8_t *flags,
                     int xd = wrap(x + E[i][0], nx), yd = wrap(y + E[i][1], ny),
                         zd = wrap(z + E[i][2], nz);
                     int64_t d = cell(xd, yd, zd, nx, ny);
-                    if (is_fluid(flags, d))
+                    if (is_fluid(flags, d)) {
                         nxt[i * N + d] = fs[i];        /* stream to x + e_i */
-                    else
-                        nxt[opposite(i) * N + c] = fs[i]; /* halfway bounce-back */
+                    } else {
+                        double moving = 0.0;           /* halfway bounce-back */
+                        if (u_wall && is_moving_wall(flags, d))
+                            moving = 6.0 * weight(i) *
+                                     (E[i][0] * u_wall[0] + E[i][1] * u_wall[1] + E[i][2] * u_wall[2]);
+                        nxt[opposite(i) * N + c] = fs[i] - moving;
+                    }
                 }
             }
         }
@@ -237,9 +251,10 @@ static void step_once(int nx, int ny, int nz, double tau, const uint8_t *flags,
     (void)nthreads;
 }
 
-/* Advance f (in place) by nsteps. Returns 0, or -1 if scratch allocation failed. */
+/* Advance f (in place) by nsteps; u_wall (nullable) is the velocity of the
+ * cells flagged 2. Returns 0, or -1 if scratch allocation failed. */
 int oracle_run(int nx, int ny, int nz, double tau, const uint8_t *flags, const double *F,
-               int F_per_cell, double *f, int nsteps, int fmt, int nthreads)
+               int F_per_cell, const double *u_wall, double *f, int nsteps, int fmt, int nthreads)
 {
     int64_t N = (int64_t)nx * ny * nz;
     double *tmp = (double *)malloc(sizeof(double) * Q * N);
@@ -247,7 +262,7 @@ int oracle_run(int nx, int ny, int nz, double tau, const uint8_t *flags, const d
     if (nthreads < 1) nthreads = 1;
     double *a = f, *b = tmp;
     for (int s = 0; s < nsteps; ++s) {
-        step_once(nx, ny, nz, tau, flags, F, F_per_cell, a, b, nthreads);
+        step_once(nx, ny, nz, tau, flags, F, F_per_cell, u_wall, a, b, nthreads);
         round_storage(b, flags, N, fmt);
         double *t = a; a = b; b = t;
     }

@@ -1,0 +1,244 @@
+// AA-pattern stream-collide: one lattice A updated in place.
+//
+// The fused update of Sec. 2 needs two grids when populations move to their
+// neighbours in every step. The AA pattern (Bailey et al., 2009) alternates
+// two kinds of step on one lattice instead, each moving the same bytes as a
+// two-grid step. Two layouts of the pre-collision state f^n alternate:
+//   natural (before an even step): slot i of cell x holds f^n_i(x);
+//   swapped (before an odd step):  slot opp(i) of x holds P^{n-1}_i(x), the
+//     post-collision value of the even step, so f^n_i(x) is slot opp(i) of
+//     x - e_i if that cell is fluid, else slot i of x itself (halfway
+//     bounce-back, plus the moving-wall term).
+// Even step: cell x reads slot i of x, collides, and writes P_i(x) to slot
+// opp(i) of x; no neighbour is touched. Odd step: cell x gathers from the
+// swapped layout, collides, and writes P_i(x) to slot i of x + e_i (where the
+// next even step reads f_i(x + e_i)); if x + e_i is solid, the bounced value
+// goes to slot opp(i) of x instead. In both steps the slots a cell writes are
+// exactly the slots it read, each read before it is written by the same
+// thread, so the in-place update has no races (and the read-only load path is
+// safe: nothing is written before it is read within a launch).
+//
+// Solid cells hold NaN in every slot and are never written. A NaN read in the
+// odd step therefore marks a solid neighbour x - e_j, which is also the target
+// x + e_opp(j) of the outgoing population opp(j): one test finds both the
+// bounced reads and the bounced writes. As in the two-grid kernel, a NaN makes
+// rho NaN, so only cells next to a solid test their populations one by one.
+#pragma once
+
+#include "lbm_kernels.cuh"
+
+namespace lbm {
+
+// Live lanes of the pair (x0, x0 + 1): fluid and inside the row.
+template <bool FLAGS>
+__device__ __forceinline__ void pair_live(const Dev &d, int c, bool has1, bool &live0, bool &live1) {
+    live0 = true;
+    live1 = has1;
+    if (FLAGS) {
+        const uchar2 fl = __ldg(reinterpret_cast<const uchar2 *>(d.flags + c));
+        live0 = !fl.x;
+        live1 = has1 && !fl.y;
+    }
+}
+
+template <class R, int FORCE>
+__device__ __forceinline__ void pair_force(const Dev &d, int c, typename Pair2<R>::V &Fx, typename Pair2<R>::V &Fy,
+                                           typename Pair2<R>::V &Fz, Guo2<R> &G) {
+    Fx = Fy = Fz = vsplat(R(0));
+    if (FORCE == 1) {
+        Fx = vsplat(R(d.F[0]));
+        Fy = vsplat(R(d.F[1]));
+        Fz = vsplat(R(d.F[2]));
+        G = uniform_guo<R>(d);
+    } else if (FORCE == 2) {
+        const R *F = static_cast<const R *>(d.Ffield);
+        ld2_real(F + c, Fx.x, Fx.y);
+        ld2_real(F + d.g.qs + c, Fy.x, Fy.y);
+        ld2_real(F + 2 * d.g.qs + c, Fz.x, Fz.y);
+        G = guo2<R>(R(d.omega), Fx, Fy, Fz);
+    }
+}
+
+template <class R, bool RECORD>
+__device__ __forceinline__ void pair_check_record(const Dev &d, int c, bool live0, bool live1, const Mom2<R> &m,
+                                                  R *tape) {
+    const bool bad0 = live0 && !(m.rho.x > R(0) && m.rho.x < R(1e30));
+    const bool bad1 = live1 && !(m.rho.y > R(0) && m.rho.y < R(1e30));
+    if (bad0 || bad1) atomicOr(d.status, LBM_STATUS_DIVERGED);
+    if (RECORD) {
+        const long long qs = d.g.qs;
+        st2_real(tape + c, m.rho.x, m.rho.y);
+        st2_real(tape + qs + c, m.ux.x, m.ux.y);
+        st2_real(tape + 2 * qs + c, m.uy.x, m.uy.y);
+        st2_real(tape + 3 * qs + c, m.uz.x, m.uz.y);
+    }
+}
+
+// Even step (natural -> swapped): local, every access an aligned pair.
+template <int S, bool FLAGS, int FORCE, bool RECORD>
+__global__ void __launch_bounds__(256, StepBlocks<S>::value)
+    k_aa_even(const Dev d, typename Stor<S>::T *__restrict__ A, typename Stor<S>::R *__restrict__ tape) {
+    typedef typename Stor<S>::R R;
+    typedef typename Pair2<R>::V V;
+    int x0, y, z;
+    if (!pair_cell(d.g, d.P.nxb, blockDim.x, blockDim.y, blockIdx.x, blockIdx.y, threadIdx.x, threadIdx.y, x0,
+                   y, z))
+        return;
+    const long long qs = d.g.qs;
+    const int c = cell_index(d.g, x0, y, z);
+    bool live0, live1;
+    pair_live<FLAGS>(d, c, x0 + 1 < d.g.nx, live0, live1);
+    if (FLAGS && !live0 && !live1) return;
+    V s[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) Stor<S>::ld2(A + (long long)i * qs + c, s[i].x, s[i].y);
+    V Fx, Fy, Fz;
+    Guo2<R> G;
+    pair_force<R, FORCE>(d, c, Fx, Fy, Fz, G);
+    const Mom2<R> m = moments2<R, FORCE != 0>(s, Fx, Fy, Fz);
+    pair_check_record<R, RECORD>(d, c, live0, live1, m, tape);
+    collide2<R, FORCE != 0>(s, m, R(d.omega), Fx, Fy, Fz, G);
+    // a solid lane writes its NaN back (its slots stay marked)
+    const R nan = quiet_nan<R>();
+#pragma unroll
+    for (int i = 0; i < Q; ++i)
+        Stor<S>::st2(A + (long long)opp(i) * qs + c, !FLAGS || live0 ? s[i].x : nan, !FLAGS || live1 ? s[i].y : nan);
+}
+
+// Odd step (swapped -> natural): gather from the neighbours, scatter to them.
+template <int S, bool FLAGS, int FORCE, bool RECORD>
+__global__ void __launch_bounds__(256, StepBlocks<S>::value)
+    k_aa_odd(const Dev d, typename Stor<S>::T *__restrict__ A, typename Stor<S>::R *__restrict__ tape) {
+    typedef typename Stor<S>::T T;
+    typedef typename Stor<S>::R R;
+    typedef typename Pair2<R>::V V;
+    int x0, y, z;
+    if (!pair_cell(d.g, d.P.nxb, blockDim.x, blockDim.y, blockIdx.x, blockIdx.y, threadIdx.x, threadIdx.y, x0,
+                   y, z))
+        return;
+    const Geom &g = d.g;
+    const long long qs = g.qs;
+    const bool has1 = x0 + 1 < g.nx;
+    const int c = cell_index(g, x0, y, z);
+    bool live0, live1;
+    pair_live<FLAGS>(d, c, has1, live0, live1);
+    if (FLAGS && !live0 && !live1) return;
+    // neighbour columns: x0 - 1, x0 + 1, x0 + 2 (the last only for a full pair)
+    const int xa = wrap1(x0 - 1, g.nx);
+    const int xb = wrap1(x0 + 1, g.nx);
+    const int xc = has1 ? wrap1(x0 + 2, g.nx) : x0;
+    V s[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        // f_i(x) = slot opp(i) of x - e_i
+        const int row = (wrap1(z - ez(i), g.nz) * g.ny + wrap1(y - ey(i), g.ny)) * g.pitch;
+        const T *Pi = A + (long long)opp(i) * qs + row;
+        if (ex(i) == 0) {
+            Stor<S>::ld2(Pi + x0, s[i].x, s[i].y);
+        } else {
+            s[i].x = Stor<S>::ld(Pi + (ex(i) > 0 ? xa : xb));
+            s[i].y = Stor<S>::ld(Pi + (ex(i) > 0 ? x0 : xc));
+        }
+    }
+    V Fx, Fy, Fz;
+    Guo2<R> G;
+    pair_force<R, FORCE>(d, c, Fx, Fy, Fz, G);
+    Mom2<R> m = moments2<R, FORCE != 0>(s, Fx, Fy, Fz);
+    // bit i of n0 / n1: x - e_i is solid (so x + e_opp(i) is too)
+    uint32_t n0 = 0u, n1 = 0u;
+    if (FLAGS && ((live0 && m.rho.x != m.rho.x) || (live1 && m.rho.y != m.rho.y))) {
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+            const T *Po = A + (long long)i * qs + c;  // slot i of x: P_opp(i)(x)
+            if (live0 && s[i].x != s[i].x) {
+                n0 |= 1u << i;
+                s[i].x = Stor<S>::ld(Po);
+                if (d.moving_on && d.flags[pull_src(g, x0, y, z, i)] == 2) s[i].x += wall_term<R>(d, i);
+            }
+            if (live1 && s[i].y != s[i].y) {
+                n1 |= 1u << i;
+                s[i].y = Stor<S>::ld(Po + 1);
+                if (d.moving_on && d.flags[pull_src(g, x0 + 1, y, z, i)] == 2) s[i].y += wall_term<R>(d, i);
+            }
+        }
+        m = moments2<R, FORCE != 0>(s, Fx, Fy, Fz);
+    }
+    pair_check_record<R, RECORD>(d, c, live0, live1, m, tape);
+    collide2<R, FORCE != 0>(s, m, R(d.omega), Fx, Fy, Fz, G);
+    if (live0 && live1 && !(n0 | n1)) {
+        // both cells fluid, no solid neighbour: P_i(x) to slot i of x + e_i
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const int row = (wrap1(z + ez(i), g.nz) * g.ny + wrap1(y + ey(i), g.ny)) * g.pitch;
+            T *Pi = A + (long long)i * qs + row;
+            if (ex(i) == 0) {
+                Stor<S>::st2(Pi + x0, s[i].x, s[i].y);
+            } else {
+                Stor<S>::st(Pi + (ex(i) > 0 ? xb : xa), s[i].x);
+                Stor<S>::st(Pi + (ex(i) > 0 ? xc : x0), s[i].y);
+            }
+        }
+        return;
+    }
+    // cells next to a solid, or a pair with one solid or missing cell: per
+    // cell, a population headed into a solid goes back to slot opp(i) of x
+    // (minus the moving-wall term of the direction it arrives from there)
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const int row = (wrap1(z + ez(i), g.nz) * g.ny + wrap1(y + ey(i), g.ny)) * g.pitch;
+        T *Pi = A + (long long)i * qs + row;
+        T *Po = A + (long long)opp(i) * qs + c;
+        if (live0) {
+            if ((n0 >> opp(i)) & 1u) {
+                R v = s[i].x;
+                if (d.moving_on && d.flags[push_dst(g, x0, y, z, i)] == 2) v -= wall_term<R>(d, i);
+                Stor<S>::st(Po, v);
+            } else {
+                Stor<S>::st(Pi + (ex(i) > 0 ? xb : (ex(i) < 0 ? xa : x0)), s[i].x);
+            }
+        }
+        if (live1) {
+            if ((n1 >> opp(i)) & 1u) {
+                R v = s[i].y;
+                if (d.moving_on && d.flags[push_dst(g, x0 + 1, y, z, i)] == 2) v -= wall_term<R>(d, i);
+                Stor<S>::st(Po + 1, v);
+            } else {
+                Stor<S>::st(Pi + (ex(i) > 0 ? xc : (ex(i) < 0 ? x0 : x0 + 1)), s[i].y);
+            }
+        }
+    }
+}
+
+template <int S, bool FLAGS, int FORCE>
+static cudaError_t launch_aa3(const Dev &d, void *A, int odd, void *tape) {
+    typedef typename Stor<S>::T T;
+    typedef typename Stor<S>::R R;
+    T *a = static_cast<T *>(A);
+    R *t = static_cast<R *>(tape);
+    if (odd) {
+        if (tape)
+            k_aa_odd<S, FLAGS, FORCE, true><<<step_grid(d), step_block(d), 0, d.stream>>>(d, a, t);
+        else
+            k_aa_odd<S, FLAGS, FORCE, false><<<step_grid(d), step_block(d), 0, d.stream>>>(d, a, nullptr);
+    } else {
+        if (tape)
+            k_aa_even<S, FLAGS, FORCE, true><<<step_grid(d), step_block(d), 0, d.stream>>>(d, a, t);
+        else
+            k_aa_even<S, FLAGS, FORCE, false><<<step_grid(d), step_block(d), 0, d.stream>>>(d, a, nullptr);
+    }
+    return cudaGetLastError();
+}
+
+template <int S, bool FLAGS>
+static cudaError_t launch_aa2(const Dev &d, void *A, int odd, void *tape) {
+    if (d.Ffield) return launch_aa3<S, FLAGS, 2>(d, A, odd, tape);
+    if (d.force_on) return launch_aa3<S, FLAGS, 1>(d, A, odd, tape);
+    return launch_aa3<S, FLAGS, 0>(d, A, odd, tape);
+}
+
+template <int S>
+cudaError_t AaOps<S>::step(const Dev &d, void *A, int odd, void *tape) {
+    return d.flags ? launch_aa2<S, true>(d, A, odd, tape) : launch_aa2<S, false>(d, A, odd, tape);
+}
+
+}  // namespace lbm

@@ -16,10 +16,14 @@ struct lbm_ctx {
     lbm_storage storage;
     double tau;
     double F[3];
+    double u_wall[3];   // velocity of the cells flagged 2
+    bool has_moving;    // some cell is flagged 2
     cudaStream_t stream;
     int device;
-    void *lat[2];       // lat[cur] holds the latest post-collision populations
-    int cur;
+    lbm_pattern pattern;
+    void *lat[2];       // pull: lat[cur] holds the latest post-collision populations;
+                        // AA: lat[0] is the one lattice, lat[1] is null
+    int cur;            // pull: current lattice; AA: 0 = natural layout, 1 = swapped
     uint8_t *flags_d;   // padded [qs], 1 = solid (padding included), or null
     uint32_t *mask_d;   // padded [qs] push masks for the step kernels, or null
     uint32_t *links_d;  // bounce-back links (fluid cell, solid cell), grouped by direction
@@ -102,12 +106,19 @@ Dev make_dev(const lbm_ctx *ctx) {
         d.gAf[p] = (float)d.gA[p];
         d.gCf[p] = (float)d.gC[p];
     }
+    d.has_moving = ctx->has_moving;
+    d.moving_on = ctx->has_moving && (ctx->u_wall[0] != 0.0 || ctx->u_wall[1] != 0.0 || ctx->u_wall[2] != 0.0);
+    for (int i = 0; i < Q; ++i) {
+        d.wc[i] = 6.0 * weight(i) * (ex(i) * ctx->u_wall[0] + ey(i) * ctx->u_wall[1] + ez(i) * ctx->u_wall[2]);
+        d.wcf[i] = (float)d.wc[i];
+    }
     d.links = ctx->links_d;
     for (int j = 0; j < 20; ++j) d.link_off[j] = ctx->link_off[j];
     d.link_max = ctx->link_max;
     d.status = ctx->status_d;
     d.stream = ctx->stream;
     d.n_cells = (long long)ctx->g.nx * ctx->g.ny * ctx->g.nz;
+    d.layout = ctx->pattern == LBM_PATTERN_AA ? (ctx->cur ? LAYOUT_AA_SWAP : LAYOUT_AA_NAT) : LAYOUT_PULL;
     return d;
 }
 
@@ -190,6 +201,21 @@ struct Staged {
      : (ctx)->storage == LBM_F32  ? Ops<LBM_F32>::call                      \
      : (ctx)->storage == LBM_F16S ? Ops<LBM_F16S>::call                     \
                                   : Ops<LBM_BF16S>::call)
+#define LBM_AA_DISPATCH(ctx, call)                                          \
+    ((ctx)->storage == LBM_F64    ? AaOps<LBM_F64>::call                    \
+     : (ctx)->storage == LBM_F32  ? AaOps<LBM_F32>::call                    \
+     : (ctx)->storage == LBM_F16S ? AaOps<LBM_F16S>::call                   \
+                                  : AaOps<LBM_BF16S>::call)
+
+// The lattice holding the state f^n (in the layout make_dev reports).
+void *state_lat(const lbm_ctx *ctx) { return ctx->pattern == LBM_PATTERN_AA ? ctx->lat[0] : ctx->lat[ctx->cur]; }
+
+// One step from parity / lattice c (pull: lat[c] -> lat[c ^ 1]; AA: the even
+// step for c = 0, the odd one for c = 1).
+cudaError_t step_from(const lbm_ctx *ctx, const Dev &d, int c, void *tape) {
+    if (ctx->pattern == LBM_PATTERN_AA) return LBM_AA_DISPATCH(ctx, step(d, ctx->lat[0], c, tape));
+    return LBM_DISPATCH(ctx, step(d, ctx->lat[c], ctx->lat[c ^ 1], tape));
+}
 
 lbm_status check_ctx(const lbm_ctx *ctx) {
     if (!ctx) return LBM_ERR_ARG;
@@ -228,6 +254,7 @@ lbm_status lbm_options_default(lbm_options *opt) {
     opt->storage = LBM_F32;
     opt->cuda_stream = nullptr;
     opt->row_align = 0;
+    opt->pattern = LBM_PATTERN_PULL;
     return LBM_OK;
 }
 
@@ -238,8 +265,10 @@ lbm_status lbm_create(lbm_ctx **out, int nx, int ny, int nz, double tau, const u
     lbm_options o;
     lbm_options_default(&o);
     if (opt) o = *opt;
-    if (nx < 1 || ny < 1 || nz < 1 || nz > 65535 || !(tau > 0.5) || !valid_storage(o.storage))
+    if (nx < 1 || ny < 1 || nz < 1 || nz > 65535 || !(tau > 0.5) || !valid_storage(o.storage) ||
+        (o.pattern != LBM_PATTERN_PULL && o.pattern != LBM_PATTERN_AA))
         return LBM_ERR_ARG;
+    const bool aa = o.pattern == LBM_PATTERN_AA;
     const int pitch = pitch_for(nx, o.storage, o.row_align);
     if (pitch < 0) return LBM_ERR_ARG;
     const long long qs = (long long)nz * ny * pitch;
@@ -255,8 +284,11 @@ lbm_status lbm_create(lbm_ctx **out, int nx, int ny, int nz, double tau, const u
     ctx->g.qs = qs;
     ctx->L = row_launch(ctx->g);
     ctx->storage = o.storage;
+    ctx->pattern = o.pattern;
     ctx->tau = tau;
     for (int a = 0; a < 3; ++a) ctx->F[a] = force ? force[a] : 0.0;
+    for (int a = 0; a < 3; ++a) ctx->u_wall[a] = 0.0;
+    ctx->has_moving = false;
     ctx->stream = static_cast<cudaStream_t>(o.cuda_stream);
     ctx->lat[0] = ctx->lat[1] = nullptr;
     ctx->cur = 0;
@@ -289,7 +321,9 @@ lbm_status lbm_create(lbm_ctx **out, int nx, int ny, int nz, double tau, const u
         delete ctx;
         return LBM_ERR_CUDA;
     }
-    const size_t need = 2 * lat_bytes + (flags ? 5 * (size_t)qs : 0) + ((size_t)RED_BLOCKS * 4 + 8) * sizeof(double);
+    // lattices, flags (+ push masks for the two-grid kernels), reduction scratch
+    const size_t need = (aa ? 1 : 2) * lat_bytes + (flags ? (aa ? 1 : 5) * (size_t)qs : 0) +
+                        ((size_t)RED_BLOCKS * 4 + 8) * sizeof(double);
     if (need > free_b) {
         delete ctx;
         return LBM_ERR_OOM;
@@ -314,78 +348,76 @@ lbm_status lbm_create(lbm_ctx **out, int nx, int ny, int nz, double tau, const u
         for (long long z = 0; z < nz; ++z)
             for (long long y = 0; y < ny; ++y)
                 for (long long x = 0; x < nx; ++x) {
-                    uint8_t f = canon[(size_t)(x + nx * (y + ny * z))] ? 1 : 0;
+                    const uint8_t v = canon[(size_t)(x + nx * (y + ny * z))];
+                    const uint8_t f = v == 0 ? 0 : (v == 2 ? 2 : 1);  // fluid, moving wall, solid
                     hflags[(size_t)((z * ny + y) * pitch + x)] = f;
                     n_fluid += f ? 0 : 1;
+                    if (f == 2) ctx->has_moving = true;
                 }
     }
     ctx->n_fluid = n_fluid;
-    // Push masks: bit j when the neighbour x + e_j is solid (periodic), where
-    // the step kernel stores bounce-back values; SOLID_BIT on solid cells and padding.
-    // Bounce-back links for the separate-kernel form: (fluid cell, solid
-    // neighbour x + e_j) grouped by direction j, cells in increasing order.
-    std::vector<uint32_t> hlinks;
-    if (flags) {
-        std::vector<std::vector<uint32_t>> per(Q);
-        for (int z = 0; z < nz; ++z)
-            for (int y = 0; y < ny; ++y)
-                for (int x = 0; x < nx; ++x) {
-                    const int c = cell_index(ctx->g, x, y, z);
-                    if (hflags[(size_t)c]) continue;
-                    for (int j = 1; j < Q; ++j) {
-                        const int t = push_dst(ctx->g, x, y, z, j);
-                        if (hflags[(size_t)t]) {
-                            per[j].push_back((uint32_t)c);
-                            per[j].push_back((uint32_t)t);
-                        }
-                    }
-                }
-        ctx->link_off[0] = ctx->link_off[1] = 0;
-        for (int j = 1; j < Q; ++j) {
-            const int cnt = (int)(per[j].size() / 2);
-            ctx->link_off[j + 1] = ctx->link_off[j] + cnt;
-            if (cnt > ctx->link_max) ctx->link_max = cnt;
-            hlinks.insert(hlinks.end(), per[j].begin(), per[j].end());
-        }
-    }
-    std::vector<uint32_t> hmask;
-    if (flags) {
-        hmask.assign((size_t)qs, SOLID_BIT);
-        for (int z = 0; z < nz; ++z)
-            for (int y = 0; y < ny; ++y)
-                for (int x = 0; x < nx; ++x) {
-                    const int c = cell_index(ctx->g, x, y, z);
-                    uint32_t m = hflags[(size_t)c] ? SOLID_BIT : 0u;
-                    for (int j = 1; j < Q; ++j)
-                        if (hflags[(size_t)push_dst(ctx->g, x, y, z, j)]) m |= 1u << j;
-                    hmask[(size_t)c] = m;
-                }
-    }
-
     bool ok = cudaMalloc(&ctx->lat[0], lat_bytes) == cudaSuccess &&
-              cudaMalloc(&ctx->lat[1], lat_bytes) == cudaSuccess &&
+              (aa || cudaMalloc(&ctx->lat[1], lat_bytes) == cudaSuccess) &&
               cudaMalloc((void **)&ctx->red_partials, (size_t)RED_BLOCKS * 4 * sizeof(double)) == cudaSuccess &&
               cudaMalloc((void **)&ctx->red_out, 4 * sizeof(double)) == cudaSuccess &&
               cudaMalloc((void **)&ctx->status_d, sizeof(unsigned)) == cudaSuccess;
     if (ok && flags) ok = cudaMalloc((void **)&ctx->flags_d, (size_t)qs) == cudaSuccess;
-    if (ok && flags) ok = cudaMalloc((void **)&ctx->mask_d, (size_t)qs * sizeof(uint32_t)) == cudaSuccess;
-    if (ok && !hlinks.empty())
-        ok = cudaMalloc((void **)&ctx->links_d, hlinks.size() * sizeof(uint32_t)) == cudaSuccess;
+    if (ok && flags && !aa) ok = cudaMalloc((void **)&ctx->mask_d, (size_t)qs * sizeof(uint32_t)) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         free_ctx(ctx);
         return LBM_ERR_OOM;
     }
     ok = cudaMemsetAsync(ctx->lat[0], 0, lat_bytes, ctx->stream) == cudaSuccess &&
-         cudaMemsetAsync(ctx->lat[1], 0, lat_bytes, ctx->stream) == cudaSuccess &&
+         (aa || cudaMemsetAsync(ctx->lat[1], 0, lat_bytes, ctx->stream) == cudaSuccess) &&
          cudaMemsetAsync(ctx->status_d, 0, sizeof(unsigned), ctx->stream) == cudaSuccess;
-    if (ok && flags) ok = cudaMemcpy(ctx->flags_d, hflags.data(), (size_t)qs, cudaMemcpyHostToDevice) == cudaSuccess;
+    // (copies are ordered on the context's stream, ahead of the kernels that read them)
     if (ok && flags)
-        ok = cudaMemcpy(ctx->mask_d, hmask.data(), (size_t)qs * sizeof(uint32_t), cudaMemcpyHostToDevice) ==
+        ok = cudaMemcpyAsync(ctx->flags_d, hflags.data(), (size_t)qs, cudaMemcpyHostToDevice, ctx->stream) ==
              cudaSuccess;
-    if (ok && !hlinks.empty())
-        ok = cudaMemcpy(ctx->links_d, hlinks.data(), hlinks.size() * sizeof(uint32_t), cudaMemcpyHostToDevice) ==
-             cudaSuccess;
+    // push masks of the two-grid kernels, built on the device from the padded flags
+    if (ok && flags && !aa) ok = build_push_mask(ctx->g, ctx->flags_d, ctx->mask_d, ctx->stream) == cudaSuccess;
+    if (ok && flags) {
+        Dev d = make_dev(ctx);
+        ok = LBM_DISPATCH(ctx, fill_solid(d, ctx->lat[0])) == cudaSuccess &&
+             (aa || LBM_DISPATCH(ctx, fill_solid(d, ctx->lat[1])) == cudaSuccess);
+    }
+    // Bounce-back links of the separate-kernel form (16-bit storage): every
+    // (fluid cell, solid neighbour x + e_j at rest), grouped by direction j,
+    // cells in increasing order; read off the masks of the cells next to solids.
+    if (ok && flags && !aa && bounce_mode(o.storage) == BB_LINKS) {
+        std::vector<uint32_t> hmask((size_t)qs);
+        ok = cudaMemcpyAsync(hmask.data(), ctx->mask_d, (size_t)qs * sizeof(uint32_t), cudaMemcpyDeviceToHost,
+                             ctx->stream) == cudaSuccess &&
+             cudaStreamSynchronize(ctx->stream) == cudaSuccess;
+        std::vector<std::vector<uint32_t>> per(Q);
+        for (int z = 0; ok && z < nz; ++z)
+            for (int y = 0; y < ny; ++y)
+                for (int x = 0; x < nx; ++x) {
+                    const int c = cell_index(ctx->g, x, y, z);
+                    const uint32_t m = hmask[(size_t)c];
+                    if ((m & SOLID_BIT) || !m) continue;
+                    for (int j = 1; j < Q; ++j)
+                        if ((m >> j) & 1u) {
+                            const int t = push_dst(ctx->g, x, y, z, j);
+                            if (hflags[(size_t)t] == 2) continue;  // moving wall: written by the step
+                            per[j].push_back((uint32_t)c);
+                            per[j].push_back((uint32_t)t);
+                        }
+                }
+        std::vector<uint32_t> hlinks;
+        for (int j = 1; j < Q; ++j) {
+            const int cnt = (int)(per[j].size() / 2);
+            ctx->link_off[j + 1] = ctx->link_off[j] + cnt;
+            if (cnt > ctx->link_max) ctx->link_max = cnt;
+            hlinks.insert(hlinks.end(), per[j].begin(), per[j].end());
+        }
+        if (ok && !hlinks.empty())
+            ok = cudaMalloc((void **)&ctx->links_d, hlinks.size() * sizeof(uint32_t)) == cudaSuccess &&
+                 cudaMemcpyAsync(ctx->links_d, hlinks.data(), hlinks.size() * sizeof(uint32_t),
+                                 cudaMemcpyHostToDevice, ctx->stream) == cudaSuccess &&
+                 cudaStreamSynchronize(ctx->stream) == cudaSuccess;
+    }
     if (ok) ok = cudaStreamSynchronize(ctx->stream) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
@@ -412,6 +444,7 @@ lbm_status lbm_get_info(const lbm_ctx *ctx, lbm_info *info) {
     info->lattice_bytes = (size_t)Q * (size_t)ctx->g.qs * storage_bytes(ctx->storage);
     info->tape_bytes_per_step = 4 * (size_t)ctx->g.qs * real_size(ctx->storage);
     info->steps_done = ctx->steps_done;
+    info->pattern = ctx->pattern;
     return LBM_OK;
 }
 
@@ -420,6 +453,14 @@ lbm_status lbm_set_uniform_force(lbm_ctx *ctx, const double force[3]) {
     cudaStreamSynchronize(ctx->stream);
     drop_graphs(ctx);  // the force is a kernel argument baked into the graphs
     for (int a = 0; a < 3; ++a) ctx->F[a] = force ? force[a] : 0.0;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_wall_velocity(lbm_ctx *ctx, const double u_w[3]) {
+    if (check_ctx(ctx)) return LBM_ERR_ARG;
+    cudaStreamSynchronize(ctx->stream);
+    drop_graphs(ctx);  // the wall terms are kernel arguments baked into the graphs
+    for (int a = 0; a < 3; ++a) ctx->u_wall[a] = u_w ? u_w[a] : 0.0;
     return LBM_OK;
 }
 
@@ -469,8 +510,9 @@ lbm_status lbm_init_equilibrium(lbm_ctx *ctx, const void *rho, const void *u) {
     int iu = st.add(u, 3 * N * rs, false);
     lbm_status s = st.prepare();
     if (s) return s;
+    if (ctx->pattern == LBM_PATTERN_AA) ctx->cur = 0;  // written in the natural layout
     Dev d = make_dev(ctx);
-    cudaError_t e = LBM_DISPATCH(ctx, init_eq(d, ctx->lat[ctx->cur], ir >= 0 ? st.dev(ir) : nullptr, st.dev(iu)));
+    cudaError_t e = LBM_DISPATCH(ctx, init_eq(d, state_lat(ctx), ir >= 0 ? st.dev(ir) : nullptr, st.dev(iu)));
     if (e != cudaSuccess) return cuda_fail(ctx, e, "init_equilibrium launch");
     ctx->steps_done = 0;
     ctx->lam_valid = false;
@@ -492,7 +534,7 @@ static bool build_graph(lbm_ctx *ctx, int from) {
     bool ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
     for (int k = 0; ok && k < GRAPH_STEPS; ++k) {
         const int c = from ^ (k & 1);
-        ok = LBM_DISPATCH(ctx, step(d, ctx->lat[c], ctx->lat[c ^ 1], nullptr)) == cudaSuccess;
+        ok = step_from(ctx, d, c, nullptr) == cudaSuccess;
     }
     const bool ended = cudaStreamEndCapture(cs, &graph) == cudaSuccess;
     ok = ok && ended && graph && cudaGraphInstantiate(&ctx->graph[from], graph, 0) == cudaSuccess;
@@ -522,7 +564,7 @@ lbm_status lbm_step(lbm_ctx *ctx, int n) {
     }
     Dev d = make_dev(ctx);
     for (int k = 0; k < n; ++k) {
-        cudaError_t e = LBM_DISPATCH(ctx, step(d, ctx->lat[ctx->cur], ctx->lat[ctx->cur ^ 1], nullptr));
+        cudaError_t e = step_from(ctx, d, ctx->cur, nullptr);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "stream-collide launch");
         ctx->cur ^= 1;
         ctx->steps_done++;
@@ -538,7 +580,7 @@ lbm_status lbm_step_record(lbm_ctx *ctx, int n, void *tape) {
     Dev d = make_dev(ctx);
     for (int k = 0; k < n; ++k) {
         void *tk = static_cast<char *>(tape) + per * (size_t)k;
-        cudaError_t e = LBM_DISPATCH(ctx, step(d, ctx->lat[ctx->cur], ctx->lat[ctx->cur ^ 1], tk));
+        cudaError_t e = step_from(ctx, d, ctx->cur, tk);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "stream-collide (record) launch");
         ctx->cur ^= 1;
         ctx->steps_done++;
@@ -556,7 +598,7 @@ lbm_status lbm_macros(lbm_ctx *ctx, void *rho, void *u) {
     lbm_status s = st.prepare();
     if (s) return s;
     Dev d = make_dev(ctx);
-    cudaError_t e = LBM_DISPATCH(ctx, macros(d, ctx->lat[ctx->cur], ir >= 0 ? st.dev(ir) : nullptr, st.dev(iu)));
+    cudaError_t e = LBM_DISPATCH(ctx, macros(d, state_lat(ctx), ir >= 0 ? st.dev(ir) : nullptr, st.dev(iu)));
     if (e != cudaSuccess) return cuda_fail(ctx, e, "macros launch");
     return st.finish();
 }
@@ -565,7 +607,7 @@ lbm_status lbm_reduce(lbm_ctx *ctx, double out[4]) {
     if (check_ctx(ctx)) return LBM_ERR_ARG;
     if (!out) return fail(ctx, LBM_ERR_ARG, "out is required");
     Dev d = make_dev(ctx);
-    cudaError_t e = LBM_DISPATCH(ctx, reduce(d, ctx->lat[ctx->cur], ctx->red_partials, ctx->red_out));
+    cudaError_t e = LBM_DISPATCH(ctx, reduce(d, state_lat(ctx), ctx->red_partials, ctx->red_out));
     if (e != cudaSuccess) return cuda_fail(ctx, e, "reduce launch");
     e = cudaMemcpyAsync(out, ctx->red_out, 4 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
@@ -582,7 +624,7 @@ lbm_status lbm_get_state(lbm_ctx *ctx, void *dst, lbm_storage fmt) {
     lbm_status s = st.prepare();
     if (s) return s;
     Dev d = make_dev(ctx);
-    cudaError_t e = LBM_DISPATCH(ctx, get_state(d, ctx->lat[ctx->cur], st.dev(k), (int)fmt));
+    cudaError_t e = LBM_DISPATCH(ctx, get_state(d, state_lat(ctx), st.dev(k), (int)fmt));
     if (e != cudaSuccess) return cuda_fail(ctx, e, "get_state launch");
     return st.finish();
 }
@@ -595,8 +637,9 @@ lbm_status lbm_set_state(lbm_ctx *ctx, const void *src, lbm_storage fmt) {
     int k = st.add(src, (size_t)Q * N * storage_bytes(fmt), false);
     lbm_status s = st.prepare();
     if (s) return s;
+    if (ctx->pattern == LBM_PATTERN_AA) ctx->cur = 0;  // written in the natural layout
     Dev d = make_dev(ctx);
-    cudaError_t e = LBM_DISPATCH(ctx, set_state(d, ctx->lat[ctx->cur], st.dev(k), (int)fmt));
+    cudaError_t e = LBM_DISPATCH(ctx, set_state(d, state_lat(ctx), st.dev(k), (int)fmt));
     if (e != cudaSuccess) return cuda_fail(ctx, e, "set_state launch");
     ctx->steps_done = 0;
     return LBM_OK;
@@ -629,7 +672,7 @@ lbm_status lbm_adjoint_seed(lbm_ctx *ctx, const void *dL_du, const void *dL_drho
     s = st.prepare();
     if (s) return s;
     Dev d = make_dev(ctx);
-    cudaError_t e = LBM_DISPATCH(ctx, adj_seed(d, ctx->lat[ctx->cur], st.dev(iu), ir >= 0 ? st.dev(ir) : nullptr,
+    cudaError_t e = LBM_DISPATCH(ctx, adj_seed(d, state_lat(ctx), st.dev(iu), ir >= 0 ? st.dev(ir) : nullptr,
                                                ctx->lam[ctx->lcur], grad_F));
     if (e != cudaSuccess) return cuda_fail(ctx, e, "adjoint seed launch");
     ctx->lam_valid = true;

@@ -220,6 +220,8 @@ LBM_HD bool pair_cell(const Geom &g, int nxb, int bdx, int bdy, int bx, int bz, 
 // 1 <= j <= 18, is set when the neighbour x + e_j is solid, so population j
 // bounces back; SOLID_BIT is set on solid cells and on row padding.
 constexpr uint32_t SOLID_BIT = 0x80000000u;
+// Set in the push mask of a cell with a moving-wall neighbour.
+constexpr uint32_t MOVING_BIT = 0x40000000u;
 
 // Cell owned by thread (tx, ty) of block (bx, bz); false for threads past the edge.
 LBM_HD bool row_cell(const Geom &g, int nxb, int bdx, int bdy, int bx, int bz, int tx, int ty,
@@ -259,6 +261,10 @@ LBM_HD long long canon_index(const Geom &g, int x, int y, int z) {
 //   seq_i = f_eq_i - w_i = w_i [(rho - 1) + rho (3 e.u + 9/2 (e.u)^2 - 3/2 u.u)]
 //   S_i = (1 - omega/2) w_i [3 (e_i - u) + 9 (e_i.u) e_i] . F
 // Opposite directions share the even part and flip the odd part.
+// Correctly rounded 1/x (the same value as an IEEE division 1/x).
+__device__ __forceinline__ float rcp_rn(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double rcp_rn(double x) { return __drcp_rn(x); }
+
 template <class R> struct Mom {
     R rho1, rho, ux, uy, uz;
 };
@@ -271,68 +277,181 @@ __device__ __forceinline__ Mom<R> moments(const R s[Q], R Fx, R Fy, R Fz) {
     R r = s[0];
 #pragma unroll
     for (int p = 0; p < NPAIR; ++p) r += s[pair_first(p)] + s[opp(pair_first(p))];
-    R jx = (s[1] - s[2]) + (s[7] - s[10]) + (s[8] - s[9]) + (s[11] - s[14]) + (s[12] - s[13]);
-    R jy = (s[3] - s[4]) + (s[7] - s[10]) + (s[9] - s[8]) + (s[15] - s[18]) + (s[16] - s[17]);
-    R jz = (s[5] - s[6]) + (s[11] - s[14]) + (s[13] - s[12]) + (s[15] - s[18]) + (s[17] - s[16]);
+    // the association of moments2, so the two agree bit for bit
+    R jx = (((s[1] - s[2]) + (s[7] - s[10])) + ((s[8] - s[9]) + (s[11] - s[14]))) + (s[12] - s[13]);
+    R jy = (((s[3] - s[4]) + (s[7] - s[10])) + ((s[9] - s[8]) + (s[15] - s[18]))) + (s[16] - s[17]);
+    R jz = (((s[5] - s[6]) + (s[11] - s[14])) + ((s[13] - s[12]) + (s[15] - s[18]))) + (s[17] - s[16]);
     m.rho1 = r;
     m.rho = R(1) + r;
-    R inv = R(1) / m.rho;
+    R inv = rcp_rn(m.rho);
     m.ux = (jx + R(0.5) * Fx) * inv;
     m.uy = (jy + R(0.5) * Fy) * inv;
     m.uz = (jz + R(0.5) * Fz) * inv;
     return m;
 }
 
-// Guo source of one cell with c = 1 - omega/2: rest S_0 = -c uF (3 w_0 = 1),
-// and per opposite pair p (direction i = pair_first(p)):
+// ---------------------------------------------------------------------------
+// Arithmetic on the two cells of a pair at once: lane x is cell x0, lane y is
+// cell x0 + 1. FP32 uses the packed FP32x2 instructions of sm_100 and later
+// (one instruction for both cells, each lane rounded as its scalar operation
+// would be); FP64 works lane by lane. vsub is b * (-1) + a fused: the product
+// is exact, so it rounds once, like a - b.
+template <class R> struct Pair2;
+template <> struct Pair2<float> {
+    typedef float2 V;
+};
+template <> struct Pair2<double> {
+    typedef double2 V;
+};
+
+__device__ __forceinline__ float2 vsplat(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 vadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 vmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 vsub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+__device__ __forceinline__ float2 vrcp(float2 a) { return make_float2(rcp_rn(a.x), rcp_rn(a.y)); }
+
+__device__ __forceinline__ double2 vsplat(double a) { return make_double2(a, a); }
+__device__ __forceinline__ double2 vadd(double2 a, double2 b) {
+    return make_double2(__dadd_rn(a.x, b.x), __dadd_rn(a.y, b.y));
+}
+__device__ __forceinline__ double2 vmul(double2 a, double2 b) {
+    return make_double2(__dmul_rn(a.x, b.x), __dmul_rn(a.y, b.y));
+}
+__device__ __forceinline__ double2 vfma(double2 a, double2 b, double2 c) {
+    return make_double2(__fma_rn(a.x, b.x, c.x), __fma_rn(a.y, b.y, c.y));
+}
+__device__ __forceinline__ double2 vsub(double2 a, double2 b) {
+    return make_double2(__dsub_rn(a.x, b.x), __dsub_rn(a.y, b.y));
+}
+__device__ __forceinline__ double2 vrcp(double2 a) { return make_double2(rcp_rn(a.x), rcp_rn(a.y)); }
+
+// e_i . v for i = pair_first(p): the first non-zero component of e_i is +1,
+// the second 0 or +-1, so this is one component or one sum/difference.
+template <class V> __device__ __forceinline__ V edot_first(int i, V vx, V vy, V vz) {
+    if (ex(i)) {
+        if (ey(i)) return ey(i) > 0 ? vadd(vx, vy) : vsub(vx, vy);
+        if (ez(i)) return ez(i) > 0 ? vadd(vx, vz) : vsub(vx, vz);
+        return vx;
+    }
+    if (ey(i)) {
+        if (ez(i)) return ez(i) > 0 ? vadd(vy, vz) : vsub(vy, vz);
+        return vy;
+    }
+    return vz;
+}
+
+template <class R> struct Mom2 {
+    typedef typename Pair2<R>::V V;
+    V rho1, rho, ux, uy, uz;
+};
+
+// Moments of both cells: rho - 1 summed over opposite pairs first (the odd
+// parts of s_i and s_opp(i) cancel exactly before the total is rounded),
+// u = (j + F/2) / rho.
+template <class R, bool FORCE>
+__device__ __forceinline__ Mom2<R> moments2(const typename Pair2<R>::V s[Q], typename Pair2<R>::V Fx,
+                                            typename Pair2<R>::V Fy, typename Pair2<R>::V Fz) {
+    typedef typename Pair2<R>::V V;
+    Mom2<R> m;
+    V r = s[0];
+#pragma unroll
+    for (int p = 0; p < NPAIR; ++p) r = vadd(r, vadd(s[pair_first(p)], s[opp(pair_first(p))]));
+    V jx = vadd(vadd(vadd(vsub(s[1], s[2]), vsub(s[7], s[10])), vadd(vsub(s[8], s[9]), vsub(s[11], s[14]))),
+                vsub(s[12], s[13]));
+    V jy = vadd(vadd(vadd(vsub(s[3], s[4]), vsub(s[7], s[10])), vadd(vsub(s[9], s[8]), vsub(s[15], s[18]))),
+                vsub(s[16], s[17]));
+    V jz = vadd(vadd(vadd(vsub(s[5], s[6]), vsub(s[11], s[14])), vadd(vsub(s[13], s[12]), vsub(s[15], s[18]))),
+                vsub(s[17], s[16]));
+    if (FORCE) {
+        const V h = vsplat(R(0.5));
+        jx = vfma(h, Fx, jx);
+        jy = vfma(h, Fy, jy);
+        jz = vfma(h, Fz, jz);
+    }
+    m.rho1 = r;
+    m.rho = vadd(vsplat(R(1)), r);
+    const V inv = vrcp(m.rho);
+    m.ux = vmul(jx, inv);
+    m.uy = vmul(jy, inv);
+    m.uz = vmul(jz, inv);
+    return m;
+}
+
+// Guo source with c = 1 - omega/2: rest S_0 = -c u.F (3 w_0 = 1), and per
+// opposite pair p (direction i = pair_first(p)):
 //   even part  (e_i.u) A_p - 3 c w_p (u.F),   odd part  C_p,
 //   A_p = 9 c w_p (e_i.F),  C_p = 3 c w_p (e_i.F).
 // A and C depend only on F and tau: a uniform force passes them in precomputed.
-template <class R> struct Guo {
-    R A[NPAIR], C[NPAIR];
+template <class R> struct Guo2 {
+    typedef typename Pair2<R>::V V;
+    V A[NPAIR], C[NPAIR];
 };
 
 template <class R>
-__device__ __forceinline__ Guo<R> guo_terms(R omega, R Fx, R Fy, R Fz) {
-    Guo<R> t;
+__device__ __forceinline__ Guo2<R> guo2(R omega, typename Pair2<R>::V Fx, typename Pair2<R>::V Fy,
+                                        typename Pair2<R>::V Fz) {
+    Guo2<R> t;
     const R cF = R(1) - R(0.5) * omega;
 #pragma unroll
     for (int p = 0; p < NPAIR; ++p) {
         const int i = pair_first(p);
         const R w = i <= 6 ? R(1.0 / 18.0) : R(1.0 / 36.0);
-        const R eF = R(ex(i)) * Fx + R(ey(i)) * Fy + R(ez(i)) * Fz;
-        t.A[p] = R(9) * cF * w * eF;
-        t.C[p] = R(3) * cF * w * eF;
+        const typename Pair2<R>::V eF = edot_first(i, Fx, Fy, Fz);
+        t.A[p] = vmul(vsplat(R(9) * cF * w), eF);
+        t.C[p] = vmul(vsplat(R(3) * cF * w), eF);
     }
     return t;
 }
 
+// BGK relaxation (Eq. 1) with the Qian equilibrium and the Guo source, both
+// cells of the pair, populations in shifted form. With e = e_i . u, weight w
+// and t = 9/2 e^2 - 3/2 u.u,
+//   s_i <- (1 - omega) s_i + E + P,   s_opp(i) <- (1 - omega) s_opp(i) + E - P,
+//   E = a + b t [+ e A],   P = 3 b e [+ C],
+//   a = omega w rho1 [- 3 w c u.F],   b = omega w rho,
+// i.e. omega times the even and odd parts of the shifted equilibrium plus the
+// even and odd parts of the source (bracketed terms only with a force).
+// Without a force E +- P = a + b (t +- 3 e). a and b are formed per weight
+// class, the diagonal ones (w = 1/36) by halving the axis ones (w = 1/18),
+// so only one class's factors are held at a time.
 template <class R, bool FORCE>
-__device__ __forceinline__ void collide(R s[Q], const Mom<R> &m, R omega, R Fx, R Fy, R Fz, const Guo<R> &G) {
-    const R usq15 = R(1.5) * (m.ux * m.ux + m.uy * m.uy + m.uz * m.uz);
+__device__ __forceinline__ void collide2(typename Pair2<R>::V s[Q], const Mom2<R> &m, R omega,
+                                         typename Pair2<R>::V Fx, typename Pair2<R>::V Fy,
+                                         typename Pair2<R>::V Fz, const Guo2<R> &G) {
+    typedef typename Pair2<R>::V V;
+    const V omc = vsplat(R(1) - omega);
+    const V nusq15 = vmul(vsplat(R(-1.5)), vfma(m.uz, m.uz, vfma(m.uy, m.uy, vmul(m.ux, m.ux))));
     const R cF = R(1) - R(0.5) * omega;
-    const R uF = FORCE ? (m.ux * Fx + m.uy * Fy + m.uz * Fz) : R(0);
-    {
-        const R w = R(1.0 / 3.0);
-        R seq = w * (m.rho1 - m.rho * usq15);
-        R src = FORCE ? -cF * uF : R(0);
-        s[0] = s[0] + omega * (seq - s[0]) + src;
+    V uF = vsplat(R(0));
+    if (FORCE) uF = vfma(m.uz, Fz, vfma(m.uy, Fy, vmul(m.ux, Fx)));
+    {  // rest population, w = 1/3 (3 w c = c)
+        V a0 = vmul(vsplat(omega * R(1.0 / 3.0)), m.rho1);
+        if (FORCE) a0 = vfma(vsplat(-cF), uF, a0);
+        const V b0 = vmul(vsplat(omega * R(1.0 / 3.0)), m.rho);
+        s[0] = vfma(omc, s[0], vfma(b0, nusq15, a0));
     }
+    V a = vmul(vsplat(omega * R(1.0 / 18.0)), m.rho1);
+    if (FORCE) a = vfma(vsplat(R(-1.0 / 6.0) * cF), uF, a);
+    V b = vmul(vsplat(omega * R(1.0 / 18.0)), m.rho);
 #pragma unroll
     for (int p = 0; p < NPAIR; ++p) {
-        const int i = pair_first(p), o = opp(i);
-        const R w = i <= 6 ? R(1.0 / 18.0) : R(1.0 / 36.0);
-        const R eu = R(ex(i)) * m.ux + R(ey(i)) * m.uy + R(ez(i)) * m.uz;
-        const R even = w * (m.rho1 + m.rho * (R(4.5) * eu * eu - usq15));
-        const R odd = w * R(3) * m.rho * eu;
-        R fe = R(0), fo = R(0);
-        if (FORCE) {
-            fe = eu * G.A[p] - (R(3) * w) * cF * uF;
-            fo = G.C[p];
+        const int i = pair_first(p), io = opp(i);
+        if (p == 3) {  // first diagonal pair: w halves
+            a = vmul(vsplat(R(0.5)), a);
+            b = vmul(vsplat(R(0.5)), b);
         }
-        const R a = s[i], b = s[o];
-        s[i] = a + omega * (even + odd - a) + (fe + fo);
-        s[o] = b + omega * (even - odd - b) + (fe - fo);
+        const V e = edot_first(i, m.ux, m.uy, m.uz);
+        const V t = vfma(vsplat(R(4.5)), vmul(e, e), nusq15);
+        if (FORCE) {
+            const V E = vfma(e, G.A[p], vfma(b, t, a));
+            const V P = vfma(vmul(vsplat(R(3)), b), e, G.C[p]);
+            s[i] = vfma(omc, s[i], vadd(E, P));
+            s[io] = vfma(omc, s[io], vsub(E, P));
+        } else {
+            s[i] = vfma(omc, s[i], vfma(b, vfma(vsplat(R(3)), e, t), a));
+            s[io] = vfma(omc, s[io], vfma(b, vfma(vsplat(R(-3)), e, t), a));
+        }
     }
 }
 

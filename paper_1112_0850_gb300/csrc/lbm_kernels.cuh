@@ -42,6 +42,11 @@ template <> struct IOFmt<LBM_BF16S> {
 
 __device__ __forceinline__ bool is_solid(const uint8_t *flags, int c) { return flags && flags[c]; }
 
+// Moving-wall term of a population bounced into direction i: 6 w_i (e_i . u_w).
+template <class R> __device__ __forceinline__ R wall_term(const Dev &d, int i);
+template <> __device__ __forceinline__ float wall_term<float>(const Dev &d, int i) { return d.wcf[i]; }
+template <> __device__ __forceinline__ double wall_term<double>(const Dev &d, int i) { return d.wc[i]; }
+
 template <class R> __device__ __forceinline__ void force_at(const Dev &d, int c, R &Fx, R &Fy, R &Fz) {
     if (d.Ffield) {
         const R *F = static_cast<const R *>(d.Ffield);
@@ -55,18 +60,37 @@ template <class R> __device__ __forceinline__ void force_at(const Dev &d, int c,
     }
 }
 
-// Gather the 19 pre-collision populations of fluid cell (x, y, z) from P.
+// Gather the 19 pre-collision populations of fluid cell (x, y, z) from P in
+// the layout d.layout. In the link form a solid source's slot already holds
+// the bounced value (what the next step will read), so the gather there
+// ignores flags; the AA swapped layout is the pull layout with slot i and
+// slot opp(i) exchanged.
 template <int S, bool FLAGS>
 __device__ __forceinline__ void gather(const Dev &d, const typename Stor<S>::T *P, int x, int y, int z,
                                        int c, typename Stor<S>::R s[Q]) {
     const long long qs = d.g.qs;
+    if (d.layout == LAYOUT_AA_NAT) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) s[i] = Stor<S>::ld(P + (long long)i * qs + c);
+        return;
+    }
+    const bool mirror = d.layout == LAYOUT_AA_SWAP;
+    const bool flag_free = bounce_mode(S) == BB_LINKS && !mirror;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         int src = pull_src(d.g, x, y, z, i);
-        long long off = (long long)i * qs + src;
-        if (FLAGS && i > 0 && d.flags[src]) off = (long long)opp(i) * qs + c;
+        long long off = (long long)(mirror ? opp(i) : i) * qs + src;
+        uint8_t f = 0;
+        if (FLAGS && i > 0 && !flag_free) f = d.flags[src];
+        if (f) off = (long long)(mirror ? i : opp(i)) * qs + c;
         s[i] = Stor<S>::ld(P + off);
+        if (f == 2 && d.moving_on) s[i] += wall_term<typename Stor<S>::R>(d, i);
     }
+}
+
+// NaN marks solid slots in the NaN-mark form and in the AA pattern.
+template <int S> __device__ __forceinline__ bool nan_marked(const Dev &d) {
+    return bounce_mode(S) == BB_NANS || d.layout != LAYOUT_PULL;
 }
 
 // ---------------------------------------------------------------------------
@@ -76,23 +100,28 @@ __device__ __forceinline__ void gather(const Dev &d, const typename Stor<S>::T *
 // populations with e_x = 0 (rest, +-y, +-z and the yz diagonals) move as one
 // aligned pair per load and every population is stored as one aligned pair;
 // populations with e_x = +-1 come from sources shifted by one cell and are
-// loaded per cell. Halfway bounce-back takes one of two forms, chosen per
-// storage format by measurement:
+// loaded per cell. Every pair is stored whole, solid cells included, so
+// 32-byte sectors are written complete. Halfway bounce-back takes one of three
+// forms, chosen per storage format by measurement (Bounce<S>):
 //
-//  - load side (FP64, FP32): a 32-bit push mask per cell (bit j: x + e_j is
-//    solid) is loaded first; a population whose source x - e_i is solid (bit
-//    opp(i)) loads the opposite population of the cell itself, so each value
-//    costs one load; threads whose two cells are solid skip everything.
+//  - load side (FP64): a 32-bit push mask per cell (bit j: x + e_j is solid)
+//    is loaded first; a population whose source x - e_i is solid (bit opp(i))
+//    loads the opposite population of the cell itself, so each value costs one
+//    load; threads whose two cells are solid skip everything.
+//  - NaN marks (FP32): every slot of a solid cell holds NaN (written at
+//    create, init and set_state, and stored by the step for solid cells). The
+//    gather loads all 19 values without looking at flags; a NaN marks a solid
+//    source, and only those lanes then load the opposite population of the
+//    cell itself. No dependent load in front of the gather, no extra kernel.
 //  - separate kernel (16-bit storage), the paper's arrangement (Sec. 7: the
-//    non-fluid cells are treated in a separate kernel): the gather never looks
-//    at flags, because a solid cell s keeps in slot i the value that its fluid
-//    neighbour s + e_i pulls next step (that neighbour's post-collision
-//    population opp(i)). After the step, k_bounce copies those values along a
-//    precomputed list of boundary links. This keeps a dependent load out of
-//    the gather, which the 2-byte formats, with few bytes per thread, cannot
-//    hide.
-// Either way the fluid cells' own slots hold the post-collision populations,
-// which is what every flag-aware reader (macros, state, reduction) gathers.
+//    non-fluid cells are treated in a separate kernel): a solid cell s keeps in
+//    slot i the value that its fluid neighbour s + e_i pulls next step (that
+//    neighbour's post-collision population opp(i)); after the step, k_bounce
+//    copies those values along a precomputed list of boundary links. Fewest
+//    instructions in the step kernel, which is what the 2-byte formats need.
+// In every form the fluid cells' own slots hold the post-collision
+// populations, which is what the flag-aware readers (macros, state, reduction,
+// adjoint) gather.
 //
 // Resident blocks of 256 threads per SM the step kernels are compiled for:
 // FP64 arithmetic 1 (<= 255 registers), FP32 storage 3 (<= 80), 16-bit
@@ -100,26 +129,35 @@ __device__ __forceinline__ void gather(const Dev &d, const typename Stor<S>::T *
 template <int S> struct StepBlocks {
     static constexpr int value = S == LBM_F64 ? 1 : (S == LBM_F32 ? 3 : 4);
 };
+template <int S> struct Bounce {
+    static constexpr int mode = bounce_mode(S);
+};
 template <int S> struct LinkBounce {
-    static constexpr bool value = S == LBM_F16S || S == LBM_BF16S;
+    static constexpr bool value = Bounce<S>::mode == BB_LINKS;
 };
 
-template <class R> __device__ __forceinline__ Guo<R> uniform_guo(const Dev &d);
-template <> __device__ __forceinline__ Guo<float> uniform_guo<float>(const Dev &d) {
-    Guo<float> t;
+template <class R> __device__ __forceinline__ R quiet_nan();
+template <> __device__ __forceinline__ float quiet_nan<float>() { return __int_as_float(0x7fffffff); }
+template <> __device__ __forceinline__ double quiet_nan<double>() {
+    return __longlong_as_double(0x7fffffffffffffffLL);
+}
+
+template <class R> __device__ __forceinline__ Guo2<R> uniform_guo(const Dev &d);
+template <> __device__ __forceinline__ Guo2<float> uniform_guo<float>(const Dev &d) {
+    Guo2<float> t;
 #pragma unroll
     for (int p = 0; p < NPAIR; ++p) {
-        t.A[p] = d.gAf[p];
-        t.C[p] = d.gCf[p];
+        t.A[p] = vsplat(d.gAf[p]);
+        t.C[p] = vsplat(d.gCf[p]);
     }
     return t;
 }
-template <> __device__ __forceinline__ Guo<double> uniform_guo<double>(const Dev &d) {
-    Guo<double> t;
+template <> __device__ __forceinline__ Guo2<double> uniform_guo<double>(const Dev &d) {
+    Guo2<double> t;
 #pragma unroll
     for (int p = 0; p < NPAIR; ++p) {
-        t.A[p] = d.gA[p];
-        t.C[p] = d.gC[p];
+        t.A[p] = vsplat(d.gA[p]);
+        t.C[p] = vsplat(d.gC[p]);
     }
     return t;
 }
@@ -130,7 +168,9 @@ __global__ void __launch_bounds__(256, StepBlocks<S>::value)
            typename Stor<S>::R *__restrict__ tape) {
     typedef typename Stor<S>::T T;
     typedef typename Stor<S>::R R;
-    constexpr bool LINKS = LinkBounce<S>::value;
+    typedef typename Pair2<R>::V V;  // lane x: cell x0, lane y: cell x0 + 1
+    constexpr bool LINKS = Bounce<S>::mode != BB_LOAD;  // flag-free gather (links or NaN marks)
+    constexpr bool NANS = Bounce<S>::mode == BB_NANS;
     int x0, y, z;
     if (!pair_cell(d.g, d.P.nxb, blockDim.x, blockDim.y, blockIdx.x, blockIdx.y, threadIdx.x, threadIdx.y, x0,
                    y, z))
@@ -156,7 +196,7 @@ __global__ void __launch_bounds__(256, StepBlocks<S>::value)
     const int xa = wrap1(x0 - 1, g.nx);              // e_x = +1, cell x0
     const int xb = wrap1(x0 + 1, g.nx);              // e_x = -1, cell x0
     const int xc = has1 ? wrap1(x0 + 2, g.nx) : x0;  // e_x = -1, cell x0 + 1 (e_x = +1 pulls from x0)
-    R s0[Q], s1[Q];
+    V s[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const int row = (wrap1(z - ez(i), g.nz) * g.ny + wrap1(y - ey(i), g.ny)) * g.pitch;
@@ -166,62 +206,114 @@ __global__ void __launch_bounds__(256, StepBlocks<S>::value)
             const bool b0 = (m0 >> opp(i)) & 1u, b1 = (m1 >> opp(i)) & 1u;
             if (ex(i) == 0) {
                 if (b0 == b1) {
-                    Stor<S>::ld2(b0 ? Po : Pi + x0, s0[i], s1[i]);
+                    Stor<S>::ld2(b0 ? Po : Pi + x0, s[i].x, s[i].y);
                 } else {
-                    s0[i] = Stor<S>::ld(b0 ? Po : Pi + x0);
-                    s1[i] = Stor<S>::ld(b1 ? Po + 1 : Pi + x0 + 1);
+                    s[i].x = Stor<S>::ld(b0 ? Po : Pi + x0);
+                    s[i].y = Stor<S>::ld(b1 ? Po + 1 : Pi + x0 + 1);
                 }
             } else {
-                s0[i] = Stor<S>::ld(b0 ? Po : Pi + (ex(i) > 0 ? xa : xb));
-                s1[i] = Stor<S>::ld(b1 ? Po + 1 : Pi + (ex(i) > 0 ? x0 : xc));
+                s[i].x = Stor<S>::ld(b0 ? Po : Pi + (ex(i) > 0 ? xa : xb));
+                s[i].y = Stor<S>::ld(b1 ? Po + 1 : Pi + (ex(i) > 0 ? x0 : xc));
             }
         } else if (ex(i) == 0) {
-            Stor<S>::ld2(Pi + x0, s0[i], s1[i]);
+            Stor<S>::ld2(Pi + x0, s[i].x, s[i].y);
         } else {
-            s0[i] = Stor<S>::ld(Pi + (ex(i) > 0 ? xa : xb));
-            s1[i] = Stor<S>::ld(Pi + (ex(i) > 0 ? x0 : xc));
+            s[i].x = Stor<S>::ld(Pi + (ex(i) > 0 ? xa : xb));
+            s[i].y = Stor<S>::ld(Pi + (ex(i) > 0 ? x0 : xc));
         }
     }
-    R F0x = R(0), F0y = R(0), F0z = R(0), F1x = R(0), F1y = R(0), F1z = R(0);
-    Guo<R> G0, G1;
+    if (FLAGS && !LINKS && d.moving_on && ((m0 | m1) & MOVING_BIT)) {
+        // load side next to a moving wall: add its term to the bounced values
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+            if (((m0 >> opp(i)) & 1u) && d.flags[pull_src(g, x0, y, z, i)] == 2) s[i].x += wall_term<R>(d, i);
+            if (((m1 >> opp(i)) & 1u) && d.flags[pull_src(g, x0 + 1, y, z, i)] == 2) s[i].y += wall_term<R>(d, i);
+        }
+    }
+    V Fx = vsplat(R(0)), Fy = vsplat(R(0)), Fz = vsplat(R(0));
+    Guo2<R> G;
     if (FORCE == 1) {
-        F0x = F1x = R(d.F[0]);
-        F0y = F1y = R(d.F[1]);
-        F0z = F1z = R(d.F[2]);
-        G0 = uniform_guo<R>(d);
-        G1 = G0;
+        Fx = vsplat(R(d.F[0]));
+        Fy = vsplat(R(d.F[1]));
+        Fz = vsplat(R(d.F[2]));
+        G = uniform_guo<R>(d);
     } else if (FORCE == 2) {
         const R *F = static_cast<const R *>(d.Ffield);
-        ld2_real(F + c, F0x, F1x);
-        ld2_real(F + g.qs + c, F0y, F1y);
-        ld2_real(F + 2 * g.qs + c, F0z, F1z);
-        G0 = guo_terms<R>(R(d.omega), F0x, F0y, F0z);
-        G1 = guo_terms<R>(R(d.omega), F1x, F1y, F1z);
+        ld2_real(F + c, Fx.x, Fx.y);
+        ld2_real(F + g.qs + c, Fy.x, Fy.y);
+        ld2_real(F + 2 * g.qs + c, Fz.x, Fz.y);
+        G = guo2<R>(R(d.omega), Fx, Fy, Fz);
     }
-    const Mom<R> ma = moments<R>(s0, F0x, F0y, F0z);
-    const Mom<R> mb = moments<R>(s1, F1x, F1y, F1z);
-    const bool bad0 = live0 && !(ma.rho > R(0) && ma.rho < R(1e30));
-    const bool bad1 = live1 && !(mb.rho > R(0) && mb.rho < R(1e30));
+    Mom2<R> m = moments2<R, FORCE != 0>(s, Fx, Fy, Fz);
+    if (FLAGS && NANS && ((live0 && m.rho.x != m.rho.x) || (live1 && m.rho.y != m.rho.y))) {
+        // A solid source slot holds NaN, and a NaN anywhere makes rho NaN, so
+        // one test per cell finds the cells next to a solid. Only those reload
+        // each NaN population from the opposite slot of the cell itself
+        // (halfway bounce-back, plus the moving-wall term) and take their
+        // moments again.
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+            const T *Po = src + (long long)opp(i) * g.qs + c;
+            if (live0 && s[i].x != s[i].x) {
+                s[i].x = Stor<S>::ld(Po);
+                if (d.moving_on && d.flags[pull_src(g, x0, y, z, i)] == 2) s[i].x += wall_term<R>(d, i);
+            }
+            if (live1 && s[i].y != s[i].y) {
+                s[i].y = Stor<S>::ld(Po + 1);
+                if (d.moving_on && d.flags[pull_src(g, x0 + 1, y, z, i)] == 2) s[i].y += wall_term<R>(d, i);
+            }
+        }
+        m = moments2<R, FORCE != 0>(s, Fx, Fy, Fz);
+    }
+    const bool bad0 = live0 && !(m.rho.x > R(0) && m.rho.x < R(1e30));
+    const bool bad1 = live1 && !(m.rho.y > R(0) && m.rho.y < R(1e30));
     if (bad0 || bad1) atomicOr(d.status, LBM_STATUS_DIVERGED);
     if (RECORD) {
         const long long qs = g.qs;
-        st2_real(tape + c, ma.rho, mb.rho);
-        st2_real(tape + qs + c, ma.ux, mb.ux);
-        st2_real(tape + 2 * qs + c, ma.uy, mb.uy);
-        st2_real(tape + 3 * qs + c, ma.uz, mb.uz);
+        st2_real(tape + c, m.rho.x, m.rho.y);
+        st2_real(tape + qs + c, m.ux.x, m.ux.y);
+        st2_real(tape + 2 * qs + c, m.uy.x, m.uy.y);
+        st2_real(tape + 3 * qs + c, m.uz.x, m.uz.y);
     }
-    collide<R, FORCE != 0>(s0, ma, R(d.omega), F0x, F0y, F0z, G0);
-    collide<R, FORCE != 0>(s1, mb, R(d.omega), F1x, F1y, F1z, G1);
+    collide2<R, FORCE != 0>(s, m, R(d.omega), Fx, Fy, Fz, G);
     // Every pair is stored whole, solid cells included, so 32-byte sectors are
-    // written complete; a solid cell's values are never read (load side), or
-    // its bounce-back slots are overwritten by k_bounce right after (links).
+    // written complete; a solid cell's values are never read (load side), its
+    // bounce-back slots are overwritten by k_bounce right after (links), or
+    // it stores the NaN that marks it (NaN marks).
+    if (FLAGS && NANS) {
+        const R nan = quiet_nan<R>();
 #pragma unroll
-    for (int i = 0; i < Q; ++i) Stor<S>::st2(dst + (long long)i * g.qs + c, s0[i], s1[i]);
+        for (int i = 0; i < Q; ++i)
+            Stor<S>::st2(dst + (long long)i * g.qs + c, live0 ? s[i].x : nan, live1 ? s[i].y : nan);
+    } else {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) Stor<S>::st2(dst + (long long)i * g.qs + c, s[i].x, s[i].y);
+    }
+    if (FLAGS && LinkBounce<S>::value && d.has_moving) {
+        // Links into a moving wall (not in the link list): slot opp(j) of the
+        // wall cell x + e_j gets P_j(x) + 6 w_opp(j) (e_opp(j) . u_w), formed
+        // from the unrounded P_j(x) so that it is rounded to storage once.
+        const uint2 mm = __ldg(reinterpret_cast<const uint2 *>(d.mask + c));
+        if ((mm.x | mm.y) & MOVING_BIT) {
+#pragma unroll
+            for (int j = 1; j < Q; ++j) {
+                if (live0 && ((mm.x >> j) & 1u)) {
+                    const int t = push_dst(g, x0, y, z, j);
+                    if (d.flags[t] == 2) Stor<S>::st(dst + (long long)opp(j) * g.qs + t, s[j].x - wall_term<R>(d, j));
+                }
+                if (live1 && ((mm.y >> j) & 1u)) {
+                    const int t = push_dst(g, x0 + 1, y, z, j);
+                    if (d.flags[t] == 2) Stor<S>::st(dst + (long long)opp(j) * g.qs + t, s[j].y - wall_term<R>(d, j));
+                }
+            }
+        }
+    }
 }
 
 // Bounce-back links (separate-kernel form): for each fluid cell x and
-// direction j with x + e_j solid, slot opp(j) of the solid cell receives the
-// post-collision population j of x, copied bit for bit. Links are grouped by
+// direction j with x + e_j solid and at rest, slot opp(j) of the solid cell
+// receives the post-collision population j of x, copied bit for bit (links
+// into moving walls are written by the step kernel). Links are grouped by
 // direction (blockIdx.y + 1) and ordered by cell within a direction.
 // Each thread copies LINKS_PER_THREAD links (256 apart, so index loads stay
 // coalesced); all index loads are issued before the value loads, and all value
@@ -278,8 +370,20 @@ __global__ void __launch_bounds__(256)
                   threadIdx.y, x, y, z))
         return;
     const int c = cell_index(d.g, x, y, z);
-    if (FLAGS && d.flags[c]) return;
+    if (FLAGS && d.flags[c]) {
+        if (nan_marked<S>(d))
+#pragma unroll
+            for (int i = 0; i < Q; ++i) P[(long long)i * d.g.qs + c] = Stor<S>::enc(quiet_nan<R>());
+        return;
+    }
     const long long N = d.n_cells, cc = canon_index(d.g, x, y, z);
+    if (d.layout == LAYOUT_AA_NAT) {  // AA natural layout: f^0_i(x) at the cell itself
+        const R r1 = rho0 ? rho0[cc] - R(1) : R(0);
+#pragma unroll
+        for (int i = 0; i < Q; ++i)
+            P[(long long)i * d.g.qs + c] = Stor<S>::enc(feq_shifted<R>(i, r1, u0[cc], u0[N + cc], u0[2 * N + cc]));
+        return;
+    }
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const int t = push_dst(d.g, x, y, z, i);
@@ -292,9 +396,11 @@ __global__ void __launch_bounds__(256)
         }
         const R r1 = rho0 ? rho0[ct] - R(1) : R(0);
         const R v = feq_shifted<R>(k, r1, u0[ct], u0[N + ct], u0[2 * N + ct]);
-        P[(long long)i * d.g.qs + c] = Stor<S>::enc(v);
-        // the solid neighbour's slot that the step kernel pulls f_opp(i)(x) from
-        if (bounce) P[(long long)opp(i) * d.g.qs + t] = Stor<S>::enc(v);
+        // (the gather adds the moving-wall term to a value bounced off a moving wall)
+        const R wv = !LinkBounce<S>::value && bounce && d.flags[t] == 2 && d.moving_on ? wall_term<R>(d, i) : R(0);
+        P[(long long)i * d.g.qs + c] = Stor<S>::enc(v + wv);
+        // the solid neighbour's slot that the link form pulls f_opp(i)(x) from
+        if (bounce && Bounce<S>::mode == BB_LINKS) P[(long long)opp(i) * d.g.qs + t] = Stor<S>::enc(v);
     }
 }
 
@@ -330,8 +436,18 @@ __global__ void __launch_bounds__(256)
                   threadIdx.y, x, y, z))
         return;
     const int c = cell_index(d.g, x, y, z);
-    if (FLAGS && d.flags[c]) return;
+    if (FLAGS && d.flags[c]) {
+        if (nan_marked<S>(d))
+#pragma unroll
+            for (int i = 0; i < Q; ++i) IOFmt<S>::put(P + (long long)i * d.g.qs + c, (double)quiet_nan<float>());
+        return;
+    }
     const long long N = d.n_cells, cc = canon_index(d.g, x, y, z);
+    if (d.layout == LAYOUT_AA_NAT) {  // AA natural layout: s_i(x) at the cell itself
+#pragma unroll
+        for (int i = 0; i < Q; ++i) IOFmt<S>::put(P + (long long)i * d.g.qs + c, IOFmt<D>::get(in + i * N + cc));
+        return;
+    }
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const int t = push_dst(d.g, x, y, z, i);
@@ -339,9 +455,10 @@ __global__ void __launch_bounds__(256)
         const bool bounce = FLAGS && d.flags[t];
         if (bounce) off = (long long)opp(i) * N + cc;
         const double v = IOFmt<D>::get(in + off);
-        IOFmt<S>::put(P + (long long)i * d.g.qs + c, v);
-        // the solid neighbour's slot that the step kernel pulls f_opp(i)(x) from
-        if (bounce) IOFmt<S>::put(P + (long long)opp(i) * d.g.qs + t, v);
+        const double wv = !LinkBounce<S>::value && bounce && d.flags[t] == 2 && d.moving_on ? d.wc[i] : 0.0;
+        IOFmt<S>::put(P + (long long)i * d.g.qs + c, v + wv);
+        // the solid neighbour's slot that the link form pulls f_opp(i)(x) from
+        if (bounce && Bounce<S>::mode == BB_LINKS) IOFmt<S>::put(P + (long long)opp(i) * d.g.qs + t, v);
     }
 }
 
@@ -497,6 +614,25 @@ cudaError_t Ops<S>::step(const Dev &d, const void *src, void *dst, void *tape) {
     const int per_block = 256 * LINKS_PER_THREAD;
     k_bounce<S><<<dim3((d.link_max + per_block - 1) / per_block, Q - 1), 256, 0, d.stream>>>(
         d, static_cast<typename Stor<S>::T *>(dst));
+    return cudaGetLastError();
+}
+
+// NaN marks on every slot of every solid cell (NaN-mark form; no-op otherwise).
+template <int S>
+__global__ void __launch_bounds__(256) k_fill_solid(const Dev d, typename Stor<S>::T *__restrict__ P) {
+    int x, y, z;
+    if (!row_cell(d.g, d.L.nxb, blockDim.x, blockDim.y, blockIdx.x, blockIdx.y, threadIdx.x, threadIdx.y, x, y, z))
+        return;
+    const int c = cell_index(d.g, x, y, z);
+    if (!d.flags[c]) return;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) P[(long long)i * d.g.qs + c] = Stor<S>::enc(quiet_nan<typename Stor<S>::R>());
+}
+
+template <int S>
+cudaError_t Ops<S>::fill_solid(const Dev &d, void *lat) {
+    if (!d.flags || (Bounce<S>::mode != BB_NANS && d.layout == LAYOUT_PULL)) return cudaSuccess;
+    k_fill_solid<S><<<row_grid(d), row_block(d), 0, d.stream>>>(d, static_cast<typename Stor<S>::T *>(lat));
     return cudaGetLastError();
 }
 

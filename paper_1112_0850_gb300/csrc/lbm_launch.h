@@ -9,6 +9,13 @@
 
 namespace lbm {
 
+// How the state f^n sits in the lattice the readers and writers are given:
+//   LAYOUT_PULL     post-collision P^{n-1} at its cell; f^n = gather (two lattices)
+//   LAYOUT_AA_NAT   AA pattern before an even step: slot i of cell x holds f^n_i(x)
+//   LAYOUT_AA_SWAP  AA pattern before an odd step: slot opp(i) of x holds
+//                   P^{n-1}_i(x); f^n = the pull gather with mirrored slots
+enum { LAYOUT_PULL = 0, LAYOUT_AA_NAT = 1, LAYOUT_AA_SWAP = 2 };
+
 // Everything a launch needs to know about a context, by value.
 struct Dev {
     Geom g;
@@ -20,6 +27,10 @@ struct Dev {
     double F[3];           // uniform force (used when Ffield == nullptr)
     double gA[9], gC[9];   // Guo constants of the uniform force per opposite pair (see collide)
     float gAf[9], gCf[9];  // the same, rounded to float
+    bool has_moving;       // some cell is a moving wall (flag 2)
+    bool moving_on;        // has_moving and the wall velocity is nonzero
+    double wc[19];         // moving-wall term 6 w_i (e_i . u_w) added to a population bounced into direction i
+    float wcf[19];         // the same, rounded to float
     const uint32_t *links; // bounce-back links (cell, solid neighbour) grouped by direction, or null
     int link_off[20];      // links of direction j: [link_off[j], link_off[j + 1]), j = 1..18
     int link_max;          // largest per-direction count
@@ -28,7 +39,15 @@ struct Dev {
     unsigned *status;      // device status word
     cudaStream_t stream;
     long long n_cells;     // nx * ny * nz
+    int layout;            // LAYOUT_* of the lattice passed to readers and writers
 };
+
+// Bounce-back form per storage format (see k_step), the measured fastest on
+// the walled channel: FP64 load side, FP32 NaN marks, 16-bit link kernel.
+enum { BB_LOAD = 0, BB_LINKS = 1, BB_NANS = 2 };
+__host__ __device__ constexpr int bounce_mode(int s) {
+    return s == LBM_F64 ? BB_LOAD : (s == LBM_F32 ? BB_NANS : BB_LINKS);
+}
 
 constexpr int RED_BLOCKS = 152 * 8;  // fixed grid of the reduction: deterministic order
 constexpr int RED_THREADS = 256;
@@ -37,6 +56,9 @@ template <int S> struct Ops {
     // One fused stream-collide step: dst = C(G(src)); tape (nullable) gets
     // (rho, ux, uy, uz) of the pre-collision state, padded [4][qs] of R.
     static cudaError_t step(const Dev &d, const void *src, void *dst, void *tape);
+    // Mark the solid cells of lat for the NaN-mark form of bounce-back and the
+    // AA pattern (no-op otherwise).
+    static cudaError_t fill_solid(const Dev &d, void *lat);
     // lat = P^{-1} such that gathering it gives f_eq(rho0, u0); rho0 nullable.
     static cudaError_t init_eq(const Dev &d, void *lat, const void *rho0, const void *u0);
     // Canonical shifted state of format fmt <-> lattice (gather / inverse gather).
@@ -49,6 +71,17 @@ template <int S> struct Ops {
     static cudaError_t adj_seed(const Dev &d, const void *lat, const void *dL_du,
                                 const void *dL_drho, void *lam, void *grad_F);
 };
+
+// The AA-pattern update (one lattice, in place); every solid slot holds NaN.
+template <int S> struct AaOps {
+    // One step on lattice A: the local (even) step if odd == 0, which takes
+    // the natural layout to the swapped one, else the neighbour (odd) step,
+    // which takes it back. tape as in Ops<S>::step.
+    static cudaError_t step(const Dev &d, void *A, int odd, void *tape);
+};
+
+// Set-up: push masks of every padded cell from the padded flags (device).
+cudaError_t build_push_mask(const Geom &g, const uint8_t *flags, uint32_t *mask, cudaStream_t st);
 
 // Adjoint kernels that only depend on the arithmetic type R (double or float).
 template <class R> struct AdjOps {

@@ -28,19 +28,23 @@ def _storage_code(s):
 class Lattice:
     """A periodic nx * ny * nz D3Q19 lattice on the current CUDA device.
 
-    flags: optional uint8 array [nz][ny][nx] (0 fluid, nonzero solid);
+    flags: optional uint8 array [nz][ny][nx] (0 fluid, 2 moving wall, other nonzero solid);
     force: optional uniform body force (3,); storage: "f64" | "f32" | "f16s" |
     "bf16s". Work is enqueued on `stream` (default: torch's current stream at
     construction). row_align: bytes each padded row starts on (0 = 128).
+    pattern: "pull" (two lattices) or "aa" (one lattice updated in place).
     """
 
-    def __init__(self, nx, ny, nz, tau, flags=None, force=None, storage="f32", stream=None, row_align=0):
+    def __init__(self, nx, ny, nz, tau, flags=None, force=None, storage="f32", stream=None, row_align=0,
+                 pattern="pull"):
         L = capi.lib()
         self.storage = _storage_code(storage)
+        self.pattern = capi.PATTERN[pattern] if isinstance(pattern, str) else int(pattern)
         self.shape = (nz, ny, nx)
         self.real = _real_dtype(self.storage)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
-        opt = capi.lbm_options(self.storage, ctypes.c_void_p(self.stream.cuda_stream), int(row_align))
+        opt = capi.lbm_options(self.storage, ctypes.c_void_p(self.stream.cuda_stream), int(row_align),
+                               self.pattern)
         fl = None
         if flags is not None:
             fl = np.ascontiguousarray(np.asarray(flags.cpu() if torch.is_tensor(flags) else flags), dtype=np.uint8)
@@ -109,6 +113,10 @@ class Lattice:
     def set_uniform_force(self, force):
         F = None if force is None else (ctypes.c_double * 3)(*[float(v) for v in force])
         self._call("lbm_set_uniform_force", F)
+
+    def set_wall_velocity(self, u_w):
+        U = None if u_w is None else (ctypes.c_double * 3)(*[float(v) for v in u_w])
+        self._call("lbm_set_wall_velocity", U)
 
     def set_force_field(self, F):
         self._call("lbm_set_force_field", self._ptr(F, self.real, (3,) + self.shape))

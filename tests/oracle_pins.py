@@ -357,6 +357,52 @@ def check_shifted_storage_emulation(orc):
     assert np.abs(dev - dev.astype(np.float16).astype(np.float64)).max() < 1e-16
 
 
+def check_couette_moving_wall(orc):
+    """Plane Couette flow between a fixed wall (y = 0) and a wall moving with U
+    along x (y = ny - 1, flag 2): halfway bounce-back with the moving-wall term
+    gives the exact linear profile u_x = U (y - 1/2) / (ny - 2)."""
+    H, U, tau = 16, 0.01, 0.8
+    ny = H + 2
+    fl = np.zeros((1, ny, 1), np.uint8)
+    fl[:, 0, :] = 1
+    fl[:, ny - 1, :] = 2
+    f = orc.init_equilibrium(np.zeros((3, 1, ny, 1)), flags=fl)
+    f = orc.run(f, tau, 20000, flags=fl, u_wall=np.array([U, 0.0, 0.0]), threads=1)
+    _, u = orc.macros(f, flags=fl)
+    y = np.arange(1, ny - 1)
+    assert np.abs(u[0, 0, 1:ny - 1, 0] - U * (y - 0.5) / H).max() < 1e-9 * U
+    assert np.abs(u[1:, 0, 1:ny - 1, 0]).max() < 1e-13
+
+
+def check_moving_walls_keep_matching_flow(orc):
+    """Fluid moving uniformly with the walls is a fixed point: the moving-wall
+    term turns the reflected equilibrium population into the incoming one."""
+    ny, U = 8, np.array([0.02, 0.0, -0.01])
+    fl = np.zeros((5, ny, 6), np.uint8)
+    fl[:, 0, :] = 2
+    fl[:, ny - 1, :] = 2
+    u0 = np.zeros((3, 5, ny, 6))
+    u0[:] = U[:, None, None, None]
+    f0 = orc.init_equilibrium(u0, flags=fl)
+    f = orc.run(f0, 0.7, 50, flags=fl, u_wall=U)
+    assert np.abs(f - f0).max() < 1e-15
+
+
+def check_lid_cavity_mass(orc):
+    """A closed cavity whose lid slides tangentially conserves mass."""
+    n = 10
+    fl = np.ones((n, n, n), np.uint8)
+    fl[1:-1, 1:-1, 1:-1] = 0
+    fl[1:-1, n - 1, 1:-1] = 2  # lid at y = n - 1
+    f0 = orc.init_equilibrium(np.zeros((3, n, n, n)), flags=fl)
+    m0 = orc.sums(f0, flags=fl)[0]
+    f = orc.run(f0, 0.6, 60, flags=fl, u_wall=np.array([0.05, 0.0, 0.0]))
+    m = orc.sums(f, flags=fl)[0]
+    _, u = orc.macros(f, flags=fl)
+    assert abs(m - m0) <= 1e-13 * m0
+    assert u[0, 1:-1, n - 2, 1:-1].mean() > 0.01  # the lid drags the fluid below it
+
+
 ALL_ORACLE_CHECKS = [
     check_equilibrium_moments,
     check_collision_properties,
@@ -372,6 +418,9 @@ ALL_ORACLE_CHECKS = [
     check_init_moments,
     check_shifted_storage_emulation,
     check_poiseuille,
+    check_couette_moving_wall,
+    check_moving_walls_keep_matching_flow,
+    check_lid_cavity_mass,
     check_storage_rounding,
 ]
 

@@ -71,3 +71,17 @@ def test_reference_vjp_is_linear_in_cotangent():
     c = oadj.vjp_of_velocity(u0, F, 0.6, 4, 2.0 * g1 - g2, flags)
     for k in range(2):
         assert np.abs(c[k] - (2 * a[k] - b[k])).max() < 1e-12 * np.abs(c[k]).max()
+
+
+def test_torch_forward_matches_c_oracle_with_moving_lid():
+    n = 7
+    flags = np.ones((n, n, n), np.uint8)
+    flags[1:-1, 1:-1, 1:-1] = 0
+    flags[1:-1, n - 1, 1:-1] = 2
+    rng = np.random.default_rng(31)
+    u0 = 0.01 * rng.standard_normal((3, n, n, n)) * (flags == 0)
+    F = np.zeros((3, n, n, n))
+    uw = np.array([0.05, 0.0, 0.02])
+    _, u_t, f_t = oadj.forward(torch.tensor(u0), torch.tensor(F), 0.6, 12, flags, u_wall=uw)
+    f_c = oracle.run(oracle.init_equilibrium(u0, flags=flags), 0.6, 12, flags=flags, F=F, u_wall=uw)
+    assert np.abs(f_t.numpy() - f_c).max() < 4e-15

@@ -30,8 +30,8 @@ MUTANTS = [
     ("moment_wrong_axis", "j[a] += f[i] * E[i][a];", "j[a] += f[i] * E[i][(a + 1) % 3];"),
     ("stream_backwards", "int xd = wrap(x + E[i][0], nx)", "int xd = wrap(x - E[i][0], nx)"),
     ("stream_swap_yz", "yd = wrap(y + E[i][1], ny),", "yd = wrap(y + E[i][2], ny),"),
-    ("bounce_no_reverse", "nxt[opposite(i) * N + c] = fs[i];", "nxt[i * N + c] = fs[i];"),
-    ("bounce_dropped", "nxt[opposite(i) * N + c] = fs[i];", ";"),
+    ("bounce_no_reverse", "nxt[opposite(i) * N + c] = fs[i] - moving;", "nxt[i * N + c] = fs[i] - moving;"),
+    ("bounce_dropped", "nxt[opposite(i) * N + c] = fs[i] - moving;", ";"),
     ("weight_axis", "if (i <= 6) return 1.0 / 18.0;", "if (i <= 6) return 1.0 / 36.0;"),
     ("weight_split", "if (i <= 6)", "if (i <= 5)"),
     ("table_entry", "{1, -1, 0}, {-1, 1, 0}", "{-1, 1, 0}, {1, -1, 0}"),
@@ -40,6 +40,9 @@ MUTANTS = [
     ("round_fp16_mantissa", "round_format(v, 10, -14, 65504.0)", "round_format(v, 11, -14, 65504.0)"),
     ("round_unshifted", "w + oracle_round(f[i * N + c] - w, fmt)", "oracle_round(f[i * N + c], fmt)"),
     ("init_rho_ignored", "if (rho0) rho = rho0[c];", ";"),
+    ("moving_wall_sign", "nxt[opposite(i) * N + c] = fs[i] - moving;", "nxt[opposite(i) * N + c] = fs[i] + moving;"),
+    ("moving_wall_factor", "moving = 6.0 * weight(i) *", "moving = 2.0 * weight(i) *"),
+    ("moving_wall_cell", "if (u_wall && is_moving_wall(flags, d))", "if (u_wall && is_moving_wall(flags, c))"),
 ]
 
 
