@@ -79,6 +79,38 @@ def ncu_traffic(case, storage):
     return None if ent is None else float(ent["dram_bytes_per_launch"])
 
 
+def record_traffic(pairs):
+    """Write profiles/step_kernel_traffic.json from ncu reports: for each
+    KEY=REPORT (KEY as in ncu_traffic, e.g. channel/f32), the DRAM bytes read
+    and written by the one captured launch in REPORT, stamped with the hash of
+    the kernel sources they were taken on. Reads the reports with `ncu -i`;
+    needs no GPU."""
+    import csv
+    import io
+    import subprocess
+    entries = {}
+    for arg in pairs:
+        key, rep = arg.split("=", 1)
+        out = subprocess.run(["ncu", "-i", rep, "--page", "raw", "--csv"], capture_output=True, text=True,
+                             check=True).stdout
+        rows = list(csv.reader(io.StringIO(out)))
+        hdr, units, vals = rows[0], rows[1], rows[2]
+
+        def get(name):
+            i = hdr.index(name)
+            scale = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9}.get(units[i], 1)
+            return float(vals[i].replace(",", "")) * scale
+
+        r, w = get("dram__bytes_read.sum"), get("dram__bytes_write.sum")
+        entries[key] = {"dram_bytes_per_launch": r + w, "dram_read": r, "dram_write": w,
+                        "kernel": vals[hdr.index("Kernel Name")], "report": os.path.basename(rep)}
+    out = {"src_hash": kernel_source_hash(), "kernels": entries,
+           "note": "one cold-cache ncu launch of each kernel; writes still dirty in L2 at kernel end are not counted"}
+    with open(os.path.join(ROOT, "profiles", "step_kernel_traffic.json"), "w") as f:
+        json.dump(out, f, indent=1)
+    print(json.dumps(out, indent=1))
+
+
 def workload_flags():
     return lbm_inputs.channel_flags(NX, NY, NZ, SOLID, lbm_inputs.seed_for(1))
 
@@ -284,9 +316,15 @@ def main():
                     help="headline workload: the walled channel (default) or a periodic Taylor-Green box")
     ap.add_argument("--storage", default="f32", choices=["f64", "f32", "f16s", "bf16s"])
     ap.add_argument("--n", type=int, default=512, help="Taylor-Green box edge")
+    ap.add_argument("--pattern", default="pull", choices=["pull", "aa"],
+                    help="two lattices (pull) or one lattice updated in place (AA pattern)")
     ap.add_argument("--sweep", action="store_true",
                     help="domain-size sweep of periodic boxes and the row-padding ablation (one JSON line)")
+    ap.add_argument("--record-traffic", nargs="+", metavar="KEY=REPORT",
+                    help="write profiles/step_kernel_traffic.json from ncu reports and exit")
     args = ap.parse_args()
+    if args.record_traffic:
+        return record_traffic(args.record_traffic)
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
         return reference_arm(args)
@@ -314,14 +352,14 @@ def main():
     F = (GX, 0.0, 0.0)
     storage = args.storage
     if args.case == "channel":
-        lat = Lattice(NX, NY, NZ, TAU, flags=flags, force=F, storage=storage)
+        lat = Lattice(NX, NY, NZ, TAU, flags=flags, force=F, storage=storage, pattern=args.pattern)
         lat.init_equilibrium(lat.zeros(3))
         n_cells = NX * NY * NZ
         workload = WORKLOAD
         flag_bytes = FLAG_BYTES
     else:
         n = args.n
-        lat = Lattice(n, n, n, 0.52, storage=storage)
+        lat = Lattice(n, n, n, 0.52, storage=storage, pattern=args.pattern)
         rho_tg, u_tg = lbm_inputs.taylor_green(n, 0.02, dtype=np.float32)
         real = torch.float64 if storage == "f64" else torch.float32
         lat.init_equilibrium(torch.from_numpy(u_tg).to("cuda", real), torch.from_numpy(rho_tg).to("cuda", real))
@@ -386,6 +424,23 @@ def main():
             tg[s] = {"mlups": n ** 3 / t / 1e6, "gbs": gbs, "frac": gbs / peak, "ms_per_step": t * 1e3}
             l2.close()
         extras["taylor_green_512"] = tg
+        # ---- the AA pattern (one lattice, in place) on both workloads ------------------
+        aa = {}
+        for s in ("f32", "f16s", "bf16s"):
+            l2 = Lattice(n, n, n, 0.52, storage=s, pattern="aa")
+            l2.init_equilibrium(u_tg, rho_tg)
+            t = time_steps(torch, l2, 40, 4) / 40
+            gbs = n ** 3 * PDF_BYTES[s] / t / 1e9
+            aa["taylor_green_512_" + s] = {"mlups": n ** 3 / t / 1e6, "gbs": gbs, "frac": gbs / peak}
+            l2.close()
+        for s in ("f32", "f16s"):
+            l2 = Lattice(NX, NY, NZ, TAU, flags=flags, force=F, storage=s, pattern="aa")
+            l2.init_equilibrium(l2.zeros(3))
+            t = time_steps(torch, l2, ks, args.warmup) / ks
+            gbs = (n_fluid * PDF_BYTES[s] + n_cells * FLAG_BYTES) / t / 1e9
+            aa["channel_" + s] = {"mflups": n_fluid / t / 1e6, "gbs": gbs, "frac": gbs / peak}
+            l2.close()
+        extras["aa_pattern"] = aa
         del rho_tg, u_tg
         # ---- adjoint / forward step-time ratio (FP32, per-cell force gradient) -------------
         K = 50
@@ -445,12 +500,15 @@ def main():
             "data": "synthetic",
             "config": {"workload": workload, "n_cells": n_cells, "n_fluid": n_fluid,
                        "storage": storage + " (shifted f - w)",
-                       "l2": "no flush: the two lattices (%.0f MB each) exceed the 129 MB L2" % (
-                           lat_bytes / 1e6),
+                       "pattern": args.pattern,
+                       "l2": "no flush: the %s (%.0f MB each) exceed%s the 129 MB L2" % (
+                           "lattice" if args.pattern == "aa" else "two lattices", lat_bytes / 1e6,
+                           "s" if args.pattern == "aa" else ""),
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "kernel": "%s<%s%s>" % (STEP_KERNEL, storage,
+                         "kernel": "%s<%s%s>" % (STEP_KERNEL if args.pattern == "pull" else "k_aa_even+k_aa_odd",
+                                                 storage,
                                                  ",flags,uniform force" if args.case == "channel" else ""),
                          "peak_source": peak_kind + " hbm_gbs (MEASURED_PEAKS.json)",
                          "alg_bytes_per_launch": alg_bytes},

@@ -263,7 +263,8 @@ int lbm_lattice_table(int *e, double *w, int *opp);
  * makes for an nx * ny * nz lattice in format fmt with rows aligned to
  * row_align bytes (as in lbm_options; 0 = 128): walks every thread of each
  * launch configuration on the CPU and verifies that every address it forms
- * lies inside its buffer. Returns the number of violations (0 = all in
+ * lies inside its buffer (two-grid and AA step kernels, reverse step,
+ * per-cell kernels, reduction). Returns the number of violations (0 = all in
  * bounds), or -1 for invalid sizes or alignment. Needs no GPU. */
 int64_t lbm_check_launch_indices(int nx, int ny, int nz, lbm_storage fmt, int row_align);
 

@@ -18,11 +18,14 @@
 // thread, so the in-place update has no races (and the read-only load path is
 // safe: nothing is written before it is read within a launch).
 //
-// Solid cells hold NaN in every slot and are never written. A NaN read in the
-// odd step therefore marks a solid neighbour x - e_j, which is also the target
-// x + e_opp(j) of the outgoing population opp(j): one test finds both the
-// bounced reads and the bounced writes. As in the two-grid kernel, a NaN makes
-// rho NaN, so only cells next to a solid test their populations one by one.
+// Solid cells hold NaN in every slot; nothing but NaN is ever written there
+// (a solid cell stores its own NaN marks again, so that 32-byte sectors are
+// written complete, and no other thread writes into a solid cell). A NaN
+// read in the odd step therefore marks a solid neighbour x - e_j, which is
+// also the target x + e_opp(j) of the outgoing population opp(j): one test
+// finds both the bounced reads and the bounced writes. As in the two-grid
+// kernel, a NaN makes rho NaN, so only cells next to a solid test their
+// populations one by one.
 #pragma once
 
 #include "lbm_kernels.cuh"
@@ -88,7 +91,9 @@ __global__ void __launch_bounds__(256, StepBlocks<S>::value)
     const int c = cell_index(d.g, x0, y, z);
     bool live0, live1;
     pair_live<FLAGS>(d, c, x0 + 1 < d.g.nx, live0, live1);
-    if (FLAGS && !live0 && !live1) return;
+    // (solid cells load, collide and store their NaN marks like the others:
+    // an early exit on the flags would put a dependent load before the gather)
+    const R nan = quiet_nan<R>();
     V s[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) Stor<S>::ld2(A + (long long)i * qs + c, s[i].x, s[i].y);
@@ -99,15 +104,19 @@ __global__ void __launch_bounds__(256, StepBlocks<S>::value)
     pair_check_record<R, RECORD>(d, c, live0, live1, m, tape);
     collide2<R, FORCE != 0>(s, m, R(d.omega), Fx, Fy, Fz, G);
     // a solid lane writes its NaN back (its slots stay marked)
-    const R nan = quiet_nan<R>();
 #pragma unroll
     for (int i = 0; i < Q; ++i)
         Stor<S>::st2(A + (long long)opp(i) * qs + c, !FLAGS || live0 ? s[i].x : nan, !FLAGS || live1 ? s[i].y : nan);
 }
 
+// Resident 256-thread blocks per SM the odd step is compiled for.
+template <int S> struct AaOddBlocks {
+    static constexpr int value = StepBlocks<S>::value;
+};
+
 // Odd step (swapped -> natural): gather from the neighbours, scatter to them.
 template <int S, bool FLAGS, int FORCE, bool RECORD>
-__global__ void __launch_bounds__(256, StepBlocks<S>::value)
+__global__ void __launch_bounds__(256, AaOddBlocks<S>::value)
     k_aa_odd(const Dev d, typename Stor<S>::T *__restrict__ A, typename Stor<S>::R *__restrict__ tape) {
     typedef typename Stor<S>::T T;
     typedef typename Stor<S>::R R;
@@ -122,7 +131,7 @@ __global__ void __launch_bounds__(256, StepBlocks<S>::value)
     const int c = cell_index(g, x0, y, z);
     bool live0, live1;
     pair_live<FLAGS>(d, c, has1, live0, live1);
-    if (FLAGS && !live0 && !live1) return;
+    const R nan = quiet_nan<R>();
     // neighbour columns: x0 - 1, x0 + 1, x0 + 2 (the last only for a full pair)
     const int xa = wrap1(x0 - 1, g.nx);
     const int xb = wrap1(x0 + 1, g.nx);
@@ -165,8 +174,11 @@ __global__ void __launch_bounds__(256, StepBlocks<S>::value)
     }
     pair_check_record<R, RECORD>(d, c, live0, live1, m, tape);
     collide2<R, FORCE != 0>(s, m, R(d.omega), Fx, Fy, Fz, G);
-    if (live0 && live1 && !(n0 | n1)) {
+    if (!FLAGS || (live0 && live1 && !(n0 | n1))) {
         // both cells fluid, no solid neighbour: P_i(x) to slot i of x + e_i
+        // (without flags the second cell may be missing at the end of an odd
+        // row: its pair store then fills the padding, its shifted store is
+        // skipped)
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             const int row = (wrap1(z + ez(i), g.nz) * g.ny + wrap1(y + ey(i), g.ny)) * g.pitch;
@@ -175,19 +187,26 @@ __global__ void __launch_bounds__(256, StepBlocks<S>::value)
                 Stor<S>::st2(Pi + x0, s[i].x, s[i].y);
             } else {
                 Stor<S>::st(Pi + (ex(i) > 0 ? xb : xa), s[i].x);
-                Stor<S>::st(Pi + (ex(i) > 0 ? xc : x0), s[i].y);
+                if (FLAGS || has1) Stor<S>::st(Pi + (ex(i) > 0 ? xc : x0), s[i].y);
             }
         }
         return;
     }
     // cells next to a solid, or a pair with one solid or missing cell: per
     // cell, a population headed into a solid goes back to slot opp(i) of x
-    // (minus the moving-wall term of the direction it arrives from there)
+    // (minus the moving-wall term of the direction it arrives from there); a
+    // solid (or padding) cell stores its own NaN marks again
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const int row = (wrap1(z + ez(i), g.nz) * g.ny + wrap1(y + ey(i), g.ny)) * g.pitch;
         T *Pi = A + (long long)i * qs + row;
         T *Po = A + (long long)opp(i) * qs + c;
+        if (FLAGS && !live0 && !live1) {
+            Stor<S>::st2(A + (long long)i * qs + c, nan, nan);
+            continue;
+        }
+        if (FLAGS && !live0) Stor<S>::st(A + (long long)i * qs + c, nan);
+        if (FLAGS && !live1) Stor<S>::st(A + (long long)i * qs + c + 1, nan);
         if (live0) {
             if ((n0 >> opp(i)) & 1u) {
                 R v = s[i].x;

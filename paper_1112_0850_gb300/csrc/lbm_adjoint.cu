@@ -251,6 +251,7 @@ static cudaError_t launch_adj_step(const Dev &d, const void *li, void *lo, const
 
 template <class R>
 cudaError_t AdjOps<R>::step(const Dev &d, const void *lam_in, void *lam_out, const void *tape_k, void *grad_F) {
+    if (d.flags && !d.mask) return cudaErrorInvalidValue;  // the reverse gather reads the push masks
     return d.flags ? launch_adj_step<R, true>(d, lam_in, lam_out, tape_k, grad_F)
                    : launch_adj_step<R, false>(d, lam_in, lam_out, tape_k, grad_F);
 }

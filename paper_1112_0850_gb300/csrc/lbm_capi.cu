@@ -646,6 +646,18 @@ lbm_status lbm_set_state(lbm_ctx *ctx, const void *src, lbm_storage fmt) {
 }
 
 static lbm_status ensure_lambda(lbm_ctx *ctx) {
+    // the reverse step gathers with the push masks, which an AA-pattern
+    // context (whose forward kernels do not need them) builds on first use
+    if (ctx->flags_d && !ctx->mask_d) {
+        cudaError_t e = cudaMalloc((void **)&ctx->mask_d, (size_t)ctx->g.qs * sizeof(uint32_t));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            ctx->mask_d = nullptr;
+            return fail(ctx, LBM_ERR_OOM, "cannot allocate the push masks");
+        }
+        e = build_push_mask(ctx->g, ctx->flags_d, ctx->mask_d, ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "push mask build");
+    }
     const size_t bytes = (size_t)Q * (size_t)ctx->g.qs * real_size(ctx->storage);
     for (int k = 0; k < 2; ++k) {
         if (ctx->lam[k]) continue;
@@ -795,7 +807,9 @@ int64_t lbm_check_launch_indices(int nx, int ny, int nz, lbm_storage fmt, int ro
                     }
                 }
     if (visited != N) ++bad;  // every cell owned by exactly one thread
-    // paired launch of the step kernels: every address k_step forms
+    // paired launch of the step kernels: every address k_step forms, which
+    // covers the AA kernels too (the odd step loads at the pull sources and
+    // stores at the reverse step's rows and columns; both touch the pair at c)
     const RowLaunch P = pair_launch(g);
     long long visited2 = 0;
     auto in_row = [&](int rowbase, int x) { return x >= 0 && x < g.pitch && rowbase + x < g.qs && rowbase >= 0; };

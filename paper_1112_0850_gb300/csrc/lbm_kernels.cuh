@@ -75,7 +75,7 @@ __device__ __forceinline__ void gather(const Dev &d, const typename Stor<S>::T *
         return;
     }
     const bool mirror = d.layout == LAYOUT_AA_SWAP;
-    const bool flag_free = bounce_mode(S) == BB_LINKS && !mirror;
+    const bool flag_free = bounce_in_solid(S) && !mirror;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         int src = pull_src(d.g, x, y, z, i);
@@ -100,8 +100,9 @@ template <int S> __device__ __forceinline__ bool nan_marked(const Dev &d) {
 // populations with e_x = 0 (rest, +-y, +-z and the yz diagonals) move as one
 // aligned pair per load and every population is stored as one aligned pair;
 // populations with e_x = +-1 come from sources shifted by one cell and are
-// loaded per cell. Every pair is stored whole, solid cells included, so
-// 32-byte sectors are written complete. Halfway bounce-back takes one of three
+// loaded per cell. Every pair with a fluid cell is stored whole, its solid
+// cell included, so 32-byte sectors are written complete; pairs of two solid
+// cells do nothing. Halfway bounce-back takes one of three
 // forms, chosen per storage format by measurement (Bounce<S>):
 //
 //  - load side (FP64): a 32-bit push mask per cell (bit j: x + e_j is solid)
@@ -189,6 +190,9 @@ __global__ void __launch_bounds__(256, StepBlocks<S>::value)
         if (!live0 && !live1) return;
     } else if (FLAGS) {
         const uchar2 fl = __ldg(reinterpret_cast<const uchar2 *>(d.flags + c));
+        // (no early exit for two solid cells: branching on this load would put
+        // a dependent round trip in front of the gather, which measured ~12%
+        // slower on the walled channel than loading and storing their pairs)
         live0 = !fl.x;
         live1 = has1 && !fl.y;
     }
@@ -276,15 +280,23 @@ __global__ void __launch_bounds__(256, StepBlocks<S>::value)
         st2_real(tape + 3 * qs + c, m.uz.x, m.uz.y);
     }
     collide2<R, FORCE != 0>(s, m, R(d.omega), Fx, Fy, Fz, G);
-    // Every pair is stored whole, solid cells included, so 32-byte sectors are
-    // written complete; a solid cell's values are never read (load side), its
-    // bounce-back slots are overwritten by k_bounce right after (links), or
-    // it stores the NaN that marks it (NaN marks).
+    // The pair is stored whole, a solid cell included, so 32-byte sectors are
+    // written complete: a solid cell's values are never read (load side), it
+    // stores the NaN that marks it (NaN marks), or its slots are link targets
+    // that k_bounce rewrites (links). When moving-wall links are written into
+    // solid slots by other threads of this launch, a pair with a solid cell
+    // stores its fluid cell alone.
     if (FLAGS && NANS) {
         const R nan = quiet_nan<R>();
 #pragma unroll
         for (int i = 0; i < Q; ++i)
             Stor<S>::st2(dst + (long long)i * g.qs + c, live0 ? s[i].x : nan, live1 ? s[i].y : nan);
+    } else if (FLAGS && LinkBounce<S>::value && d.has_moving && !(live0 && live1)) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            if (live0) Stor<S>::st(dst + (long long)i * g.qs + c, s[i].x);
+            if (live1) Stor<S>::st(dst + (long long)i * g.qs + c + 1, s[i].y);
+        }
     } else {
 #pragma unroll
         for (int i = 0; i < Q; ++i) Stor<S>::st2(dst + (long long)i * g.qs + c, s[i].x, s[i].y);
@@ -397,10 +409,10 @@ __global__ void __launch_bounds__(256)
         const R r1 = rho0 ? rho0[ct] - R(1) : R(0);
         const R v = feq_shifted<R>(k, r1, u0[ct], u0[N + ct], u0[2 * N + ct]);
         // (the gather adds the moving-wall term to a value bounced off a moving wall)
-        const R wv = !LinkBounce<S>::value && bounce && d.flags[t] == 2 && d.moving_on ? wall_term<R>(d, i) : R(0);
+        const R wv = !bounce_in_solid(S) && bounce && d.flags[t] == 2 && d.moving_on ? wall_term<R>(d, i) : R(0);
         P[(long long)i * d.g.qs + c] = Stor<S>::enc(v + wv);
         // the solid neighbour's slot that the link form pulls f_opp(i)(x) from
-        if (bounce && Bounce<S>::mode == BB_LINKS) P[(long long)opp(i) * d.g.qs + t] = Stor<S>::enc(v);
+        if (bounce && bounce_in_solid(S)) P[(long long)opp(i) * d.g.qs + t] = Stor<S>::enc(v);
     }
 }
 
@@ -455,10 +467,10 @@ __global__ void __launch_bounds__(256)
         const bool bounce = FLAGS && d.flags[t];
         if (bounce) off = (long long)opp(i) * N + cc;
         const double v = IOFmt<D>::get(in + off);
-        const double wv = !LinkBounce<S>::value && bounce && d.flags[t] == 2 && d.moving_on ? d.wc[i] : 0.0;
+        const double wv = !bounce_in_solid(S) && bounce && d.flags[t] == 2 && d.moving_on ? d.wc[i] : 0.0;
         IOFmt<S>::put(P + (long long)i * d.g.qs + c, v + wv);
         // the solid neighbour's slot that the link form pulls f_opp(i)(x) from
-        if (bounce && Bounce<S>::mode == BB_LINKS) IOFmt<S>::put(P + (long long)opp(i) * d.g.qs + t, v);
+        if (bounce && bounce_in_solid(S)) IOFmt<S>::put(P + (long long)opp(i) * d.g.qs + t, v);
     }
 }
 
@@ -609,6 +621,7 @@ static cudaError_t launch_step2(const Dev &d, const void *src, void *dst, void *
 template <int S>
 cudaError_t Ops<S>::step(const Dev &d, const void *src, void *dst, void *tape) {
     if (!d.flags) return launch_step2<S, false>(d, src, dst, tape);
+    if (!d.mask) return cudaErrorInvalidValue;  // every two-grid form with flags may read the push masks
     cudaError_t e = launch_step2<S, true>(d, src, dst, tape);
     if (e != cudaSuccess || !LinkBounce<S>::value || d.link_max == 0) return e;
     const int per_block = 256 * LINKS_PER_THREAD;

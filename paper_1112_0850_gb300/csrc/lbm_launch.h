@@ -48,6 +48,9 @@ enum { BB_LOAD = 0, BB_LINKS = 1, BB_NANS = 2 };
 __host__ __device__ constexpr int bounce_mode(int s) {
     return s == LBM_F64 ? BB_LOAD : (s == LBM_F32 ? BB_NANS : BB_LINKS);
 }
+// The form in which a solid cell's slot holds the value bounced into it, so
+// the gather needs no flags (links).
+__host__ __device__ constexpr bool bounce_in_solid(int s) { return bounce_mode(s) == BB_LINKS; }
 
 constexpr int RED_BLOCKS = 152 * 8;  // fixed grid of the reduction: deterministic order
 constexpr int RED_THREADS = 256;

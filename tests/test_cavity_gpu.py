@@ -134,3 +134,30 @@ def test_wall_velocity_change_rebuilds_step_graphs(storage):
     assert torch.equal(a.get_state(), b.get_state())
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("pattern", ["pull", "aa"])
+@pytest.mark.parametrize("storage", STORAGES)
+def test_moving_wall_sharing_a_pair_with_fluid(storage, pattern):
+    """A moving wall plane at odd x (each wall cell is paired with a fluid
+    cell in the step kernels' two-cell threads) and a resting plane, walls
+    sliding tangentially; against the oracle."""
+    nx, ny, nz, tau, T = 9, 6, 5, 0.7, 40
+    flags = np.zeros((nz, ny, nx), np.uint8)
+    flags[:, :, 3] = 2
+    flags[:, :, 7] = 1
+    uw = np.array([0.0, 0.03, 0.01])
+    rng = np.random.default_rng(44)
+    u0 = 0.01 * rng.standard_normal((3, nz, ny, nx)) * (flags == 0)
+    lat = _lattice(nx, ny, nz, tau, flags=flags, storage=storage, pattern=pattern)
+    lat.set_wall_velocity(uw)
+    lat.init_equilibrium(torch.tensor(u0, dtype=REAL[storage]).cuda())
+    lat.step(T)
+    _, u = lat.macros()
+    lat.close()
+    f = oracle.run(oracle.init_equilibrium(as_input(u0, storage), flags=flags), tau, T, flags=flags,
+                   u_wall=uw if storage == "f64" else np.float32(uw).astype(np.float64))
+    _, u_o = oracle.macros(f, flags=flags)
+    m = fluid_mask(flags, (nz, ny, nx))
+    assert rel_l2(u.double().cpu().numpy(), u_o, m) <= TOL_U[storage]
+    assert np.abs(u_o[1][m]).max() > 1e-3  # the wall drives the flow
