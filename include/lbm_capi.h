@@ -86,6 +86,14 @@ typedef enum {
                              same bytes per update, half the population memory */
 } lbm_pattern;
 
+/* Equilibrium of the collision (Sec. 2 cites Qian et al.; the paper calls its
+ * solver incompressible and leaves the 1/rho out of its velocity moment). */
+typedef enum {
+    LBM_MODEL_QIAN = 0,           /* f_eq = w rho [1 + 3 e.u + 9/2 (e.u)^2 - 3/2 u.u], u = (j + F/2)/rho */
+    LBM_MODEL_INCOMPRESSIBLE = 1  /* He & Luo (1997): f_eq = w [rho + 3 e.u + 9/2 (e.u)^2 - 3/2 u.u],
+                                     u = j + F/2 (the momentum of the reference density 1) */
+} lbm_model;
+
 typedef struct {
     lbm_storage storage; /* default LBM_F32 */
     void *cuda_stream;   /* cudaStream_t used for every launch and copy; NULL = default stream */
@@ -93,6 +101,8 @@ typedef struct {
                             otherwise a power of two >= 2 elements of the storage format (the
                             kernels move pairs of cells); 2 elements = no padding beyond pairs */
     lbm_pattern pattern; /* default LBM_PATTERN_PULL */
+    lbm_model model;     /* default LBM_MODEL_QIAN; applies to every call (step, macros,
+                            totals, init, adjoint) */
 } lbm_options;
 
 typedef struct {
@@ -107,9 +117,11 @@ typedef struct {
     size_t tape_bytes_per_step; /* bytes lbm_step_record writes per step */
     int64_t steps_done;         /* time steps since the last init or set_state */
     lbm_pattern pattern;        /* streaming pattern (one lattice for LBM_PATTERN_AA, else two) */
+    lbm_model model;            /* equilibrium */
 } lbm_info;
 
-/* Fill *opt with defaults (LBM_F32, default stream, 128-byte rows, LBM_PATTERN_PULL). */
+/* Fill *opt with defaults (LBM_F32, default stream, 128-byte rows, LBM_PATTERN_PULL,
+ * LBM_MODEL_QIAN). */
 lbm_status lbm_options_default(lbm_options *opt);
 
 /* Create a context for an nx * ny * nz periodic lattice (Sec. 2: the uniform

@@ -11,6 +11,8 @@ velocity u[3][nz][ny][nx], x fastest; flags uint8 [nz][ny][nx] with 0 = fluid,
 Every function follows Sec. 2 of the paper (moments, equilibrium after Qian et
 al., BGK relaxation of Eq. 1, streaming, bounce-back after Ziegler), with the
 Guo body force and halfway bounce-back as the readings stated in the C source.
+`model` selects the equilibrium: "qian" (default) or "incompressible" (He &
+Luo: velocity terms with the reference density 1, u = j + F/2).
 """
 import ctypes
 
@@ -20,6 +22,7 @@ from . import build as _build
 
 Q = 19
 FMT = {None: 0, "f64": 0, "f32": 1, "f16": 2, "bf16": 3}
+MODEL = {None: 0, "qian": 0, "incompressible": 1}
 
 class Oracle:
     """The oracle's functions bound to one build of lbm_oracle.c (ctypes)."""
@@ -32,15 +35,18 @@ class Oracle:
         ci = ctypes.c_int
         L.oracle_lattice.argtypes = [ip, dp, ip]
         L.oracle_equilibrium.argtypes = [ctypes.c_double, dp, dp]
+        L.oracle_equilibrium_incompressible.argtypes = [ctypes.c_double, dp, dp]
         L.oracle_moments.argtypes = [dp, dp, dp, dp]
+        L.oracle_moments_incompressible.argtypes = [dp, dp, dp, dp]
         L.oracle_collide_cell.argtypes = [dp, ctypes.c_double, dp, dp]
+        L.oracle_collide_cell_model.argtypes = [ci, dp, ctypes.c_double, dp, dp]
         L.oracle_round.argtypes = [ctypes.c_double, ci]
         L.oracle_round.restype = ctypes.c_double
-        L.oracle_init.argtypes = [ci] * 3 + [vp, vp, vp, vp, ci]
-        L.oracle_run.argtypes = [ci] * 3 + [ctypes.c_double, vp, vp, ci, vp, vp, ci, ci, ci]
+        L.oracle_init.argtypes = [ci] * 3 + [vp, vp, vp, vp, ci, ci]
+        L.oracle_run.argtypes = [ci] * 3 + [ctypes.c_double, vp, vp, ci, vp, vp, ci, ci, ci, ci]
         L.oracle_run.restype = ci
-        L.oracle_macros.argtypes = [ci] * 3 + [vp, vp, ci, vp, vp, vp]
-        L.oracle_sums.argtypes = [ci] * 3 + [vp, vp, ci, vp, vp]
+        L.oracle_macros.argtypes = [ci] * 3 + [vp, vp, ci, vp, vp, vp, ci]
+        L.oracle_sums.argtypes = [ci] * 3 + [vp, vp, ci, vp, vp, ci]
         L.oracle_max_threads.restype = ci
         self.lib = L
         self.path = path
@@ -54,33 +60,36 @@ class Oracle:
         self.lib.oracle_lattice(e.ctypes.data_as(ip), _dp(w), opp.ctypes.data_as(ip))
         return e, w, opp
 
-    def equilibrium(self, rho, u):
-        """f_eq(rho, u) for one cell (Qian et al., cited in Sec. 2)."""
+    def equilibrium(self, rho, u, model=None):
+        """f_eq(rho, u) for one cell (Qian et al., cited in Sec. 2; or He & Luo)."""
         u = _f64(u)
         out = np.zeros(Q)
-        self.lib.oracle_equilibrium(float(rho), _dp(u), _dp(out))
+        fn = self.lib.oracle_equilibrium_incompressible if MODEL[model] else self.lib.oracle_equilibrium
+        fn(float(rho), _dp(u), _dp(out))
         return out
 
-    def moments(self, f, F=(0.0, 0.0, 0.0)):
-        """(rho, u) of one cell, u = (j + F/2)/rho (Sec. 2 step 1 with the Guo shift)."""
+    def moments(self, f, F=(0.0, 0.0, 0.0), model=None):
+        """(rho, u) of one cell, u = (j + F/2)/rho (Sec. 2 step 1 with the Guo
+        shift), or u = j + F/2 for the incompressible model."""
         f, F = _f64(f), _f64(F)
         rho = np.zeros(1)
         u = np.zeros(3)
-        self.lib.oracle_moments(_dp(f), _dp(F), _dp(rho), _dp(u))
+        fn = self.lib.oracle_moments_incompressible if MODEL[model] else self.lib.oracle_moments
+        fn(_dp(f), _dp(F), _dp(rho), _dp(u))
         return rho[0], u
 
-    def collide_cell(self, f, tau, F=(0.0, 0.0, 0.0)):
+    def collide_cell(self, f, tau, F=(0.0, 0.0, 0.0), model=None):
         """Post-collision populations of one cell (Eq. 1 plus the Guo source)."""
         f, F = _f64(f), _f64(F)
         out = np.zeros(Q)
-        self.lib.oracle_collide_cell(_dp(f), float(tau), _dp(F), _dp(out))
+        self.lib.oracle_collide_cell_model(MODEL[model], _dp(f), float(tau), _dp(F), _dp(out))
         return out
 
     def round_storage_value(self, v, fmt):
         """Round one FP64 value to 'f32' | 'f16' | 'bf16' (ties to even)."""
         return self.lib.oracle_round(float(v), FMT[fmt])
 
-    def init_equilibrium(self, u0, rho0=None, flags=None, fmt=None):
+    def init_equilibrium(self, u0, rho0=None, flags=None, fmt=None, model=None):
         """f^0 = f_eq(rho0, u0) per fluid cell; u0 [3][nz][ny][nx]; returns f [19][nz][ny][nx]."""
         u0 = _f64(u0)
         shape = u0.shape[1:]
@@ -88,10 +97,10 @@ class Oracle:
         fl = _flags(flags, shape)
         r0 = None if rho0 is None else _f64(rho0)
         f = np.zeros((Q,) + shape)
-        self.lib.oracle_init(nx, ny, nz, _vp(fl), _vp(r0), _vp(u0), _vp(f), FMT[fmt])
+        self.lib.oracle_init(nx, ny, nz, _vp(fl), _vp(r0), _vp(u0), _vp(f), FMT[fmt], MODEL[model])
         return f
 
-    def run(self, f, tau, steps, flags=None, F=None, fmt=None, threads=None, u_wall=None):
+    def run(self, f, tau, steps, flags=None, F=None, fmt=None, threads=None, u_wall=None, model=None):
         """Advance state f by `steps` collide-and-stream steps; returns a new array.
 
         Cells flagged 2 are walls moving with velocity u_wall (3,)."""
@@ -103,12 +112,12 @@ class Oracle:
         uw = None if u_wall is None else _f64(u_wall)
         nt = threads if threads else self.lib.oracle_max_threads()
         rc = self.lib.oracle_run(nx, ny, nz, float(tau), _vp(fl), _vp(Fa), per_cell, _vp(uw), _vp(f),
-                                 int(steps), FMT[fmt], int(nt))
+                                 int(steps), FMT[fmt], int(nt), MODEL[model])
         if rc != 0:
             raise MemoryError("oracle_run could not allocate its second lattice")
         return f
 
-    def macros(self, f, flags=None, F=None):
+    def macros(self, f, flags=None, F=None, model=None):
         """(rho [nz][ny][nx], u [3][nz][ny][nx]) of state f; zeros at solid cells."""
         f = _f64(f)
         shape = f.shape[1:]
@@ -117,18 +126,18 @@ class Oracle:
         Fa, per_cell = _force(F, shape)
         rho = np.zeros(shape)
         u = np.zeros((3,) + shape)
-        self.lib.oracle_macros(nx, ny, nz, _vp(fl), _vp(Fa), per_cell, _vp(f), _vp(rho), _vp(u))
+        self.lib.oracle_macros(nx, ny, nz, _vp(fl), _vp(Fa), per_cell, _vp(f), _vp(rho), _vp(u), MODEL[model])
         return rho, u
 
-    def sums(self, f, flags=None, F=None):
-        """[sum rho, sum rho u_x, sum rho u_y, sum rho u_z] over fluid cells."""
+    def sums(self, f, flags=None, F=None, model=None):
+        """[sum rho, and the sum of the momentum j + F/2] over fluid cells."""
         f = _f64(f)
         shape = f.shape[1:]
         nz, ny, nx = shape
         fl = _flags(flags, shape)
         Fa, per_cell = _force(F, shape)
         out = np.zeros(4)
-        self.lib.oracle_sums(nx, ny, nz, _vp(fl), _vp(Fa), per_cell, _vp(f), _vp(out))
+        self.lib.oracle_sums(nx, ny, nz, _vp(fl), _vp(Fa), per_cell, _vp(f), _vp(out), MODEL[model])
         return out
 
     def max_threads(self):
@@ -155,36 +164,36 @@ def lattice():
     return default().lattice()
 
 
-def equilibrium(rho, u):
-    return default().equilibrium(rho, u)
+def equilibrium(rho, u, model=None):
+    return default().equilibrium(rho, u, model)
 
 
-def moments(f, F=(0.0, 0.0, 0.0)):
-    return default().moments(f, F)
+def moments(f, F=(0.0, 0.0, 0.0), model=None):
+    return default().moments(f, F, model)
 
 
-def collide_cell(f, tau, F=(0.0, 0.0, 0.0)):
-    return default().collide_cell(f, tau, F)
+def collide_cell(f, tau, F=(0.0, 0.0, 0.0), model=None):
+    return default().collide_cell(f, tau, F, model)
 
 
 def round_storage_value(v, fmt):
     return default().round_storage_value(v, fmt)
 
 
-def init_equilibrium(u0, rho0=None, flags=None, fmt=None):
-    return default().init_equilibrium(u0, rho0, flags, fmt)
+def init_equilibrium(u0, rho0=None, flags=None, fmt=None, model=None):
+    return default().init_equilibrium(u0, rho0, flags, fmt, model)
 
 
-def run(f, tau, steps, flags=None, F=None, fmt=None, threads=None, u_wall=None):
-    return default().run(f, tau, steps, flags, F, fmt, threads, u_wall)
+def run(f, tau, steps, flags=None, F=None, fmt=None, threads=None, u_wall=None, model=None):
+    return default().run(f, tau, steps, flags, F, fmt, threads, u_wall, model)
 
 
-def macros(f, flags=None, F=None):
-    return default().macros(f, flags, F)
+def macros(f, flags=None, F=None, model=None):
+    return default().macros(f, flags, F, model)
 
 
-def sums(f, flags=None, F=None):
-    return default().sums(f, flags, F)
+def sums(f, flags=None, F=None, model=None):
+    return default().sums(f, flags, F, model)
 
 
 def max_threads():

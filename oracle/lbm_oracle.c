@@ -27,6 +27,11 @@
  *     2 w_i rho_w (e_i . u_w) / c_s^2 = 6 w_i (e_i . u_w), with the wall
  *     density rho_w taken as the reference density 1 (Ladd's rule).
  *   - all three axes are periodic; walls are solid flag layers.
+ *   - model 1 is the incompressible equilibrium of He & Luo (1997), the
+ *     reading of the paper's "incompressible flow solver" wording with the
+ *     1/rho of its velocity moment left out (Sec. 1, Sec. 2 step 1): the
+ *     velocity terms carry the reference density rho0 = 1 instead of rho and
+ *     u = j + F/2. Model 0 is the Qian equilibrium above.
  * The state is the pre-collision populations f^n (push form), canonical layout
  * f[i][z][y][x], x fastest. Solid cells hold zeros.
  *
@@ -105,6 +110,31 @@ void oracle_equilibrium(double rho, const double *u, double *feq)
     }
 }
 
+/* He & Luo incompressible equilibrium (model 1): the density enters only the
+ * zeroth-order term, the velocity terms are those of the reference density 1:
+ *   f_eq_i(rho, u) = w_i [rho + 3 e.u + 9/2 (e.u)^2 - 3/2 u.u]. */
+void oracle_equilibrium_incompressible(double rho, const double *u, double *feq)
+{
+    double usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    for (int i = 0; i < Q; ++i) {
+        double cu = E[i][0] * u[0] + E[i][1] * u[1] + E[i][2] * u[2];
+        feq[i] = weight(i) * (rho + 3.0 * cu + 4.5 * cu * cu - 1.5 * usq);
+    }
+}
+
+/* Moments of one cell for the incompressible model: rho = sum f_i, and the
+ * velocity is the momentum over the reference density 1, u = sum f_i e_i + F/2. */
+void oracle_moments_incompressible(const double *f, const double *F, double *rho_out, double *u_out)
+{
+    double r = 0.0, mom[3] = {0.0, 0.0, 0.0};
+    for (int i = 0; i < Q; ++i) {
+        r += f[i];
+        for (int a = 0; a < 3; ++a) mom[a] += E[i][a] * f[i];
+    }
+    *rho_out = r;
+    for (int a = 0; a < 3; ++a) u_out[a] = mom[a] + F[a] / 2.0;
+}
+
 /* Moments of one cell: rho = sum f_i, u = (sum f_i e_i + F/2) / rho. */
 void oracle_moments(const double *f, const double *F, double *rho_out, double *u_out)
 {
@@ -117,12 +147,18 @@ void oracle_moments(const double *f, const double *F, double *rho_out, double *u
     for (int a = 0; a < 3; ++a) u_out[a] = (j[a] + 0.5 * F[a]) / rho;
 }
 
-/* Collide one cell (Eq. 1 with the Guo source term): fout = f - (f - feq)/tau + S. */
-void oracle_collide_cell(const double *f, double tau, const double *F, double *fout)
+/* Collide one cell (Eq. 1 with the Guo source term): fout = f - (f - feq)/tau + S,
+ * with the moments and equilibrium of `model` (0 Qian, 1 incompressible). */
+void oracle_collide_cell_model(int model, const double *f, double tau, const double *F, double *fout)
 {
     double rho, u[3], feq[Q];
-    oracle_moments(f, F, &rho, u);
-    oracle_equilibrium(rho, u, feq);
+    if (model == 1) {
+        oracle_moments_incompressible(f, F, &rho, u);
+        oracle_equilibrium_incompressible(rho, u, feq);
+    } else {
+        oracle_moments(f, F, &rho, u);
+        oracle_equilibrium(rho, u, feq);
+    }
     double uF = u[0] * F[0] + u[1] * F[1] + u[2] * F[2];
     for (int i = 0; i < Q; ++i) {
         double eu = E[i][0] * u[0] + E[i][1] * u[1] + E[i][2] * u[2];
@@ -130,6 +166,11 @@ void oracle_collide_cell(const double *f, double tau, const double *F, double *f
         double S = (1.0 - 1.0 / (2.0 * tau)) * weight(i) * (3.0 * (eF - uF) + 9.0 * eu * eF);
         fout[i] = f[i] - (f[i] - feq[i]) / tau + S;
     }
+}
+
+void oracle_collide_cell(const double *f, double tau, const double *F, double *fout)
+{
+    oracle_collide_cell_model(0, f, tau, F, fout);
 }
 
 /* Force at cell c: uniform (F_per_cell == 0, F = [3]) or a field F[3][N]. */
@@ -191,10 +232,11 @@ static void round_storage(double *f, const uint8_t *flags, int64_t N, int fmt)
     }
 }
 
-/* f[i][c] = f_eq_i(rho0(c), u0(c)) at fluid cells, 0 at solid cells. rho0 may
- * be NULL (rho0 = 1). Optional storage rounding as in oracle_run. */
+/* f[i][c] = f_eq_i(rho0(c), u0(c)) at fluid cells, 0 at solid cells, with the
+ * equilibrium of `model`. rho0 may be NULL (rho0 = 1). Optional storage
+ * rounding as in oracle_run. */
 void oracle_init(int nx, int ny, int nz, const uint8_t *flags, const double *rho0,
-                 const double *u0 /* [3][N] */, double *f /* [19][N] */, int fmt)
+                 const double *u0 /* [3][N] */, double *f /* [19][N] */, int fmt, int model)
 {
     int64_t N = (int64_t)nx * ny * nz;
     for (int64_t c = 0; c < N; ++c) {
@@ -202,7 +244,10 @@ void oracle_init(int nx, int ny, int nz, const uint8_t *flags, const double *rho
         if (is_fluid(flags, c)) {
             if (rho0) rho = rho0[c];
             for (int a = 0; a < 3; ++a) u[a] = u0[a * N + c];
-            oracle_equilibrium(rho, u, feq);
+            if (model == 1)
+                oracle_equilibrium_incompressible(rho, u, feq);
+            else
+                oracle_equilibrium(rho, u, feq);
         } else {
             for (int i = 0; i < Q; ++i) feq[i] = 0.0;
         }
@@ -215,7 +260,7 @@ void oracle_init(int nx, int ny, int nz, const uint8_t *flags, const double *rho
  * bounce-back rule). Every fluid entry of nxt is written exactly once. */
 static void step_once(int nx, int ny, int nz, double tau, const uint8_t *flags,
                       const double *F, int F_per_cell, const double *u_wall, const double *cur,
-                      double *nxt, int nthreads)
+                      double *nxt, int nthreads, int model)
 {
     int64_t N = (int64_t)nx * ny * nz;
     memset(nxt, 0, sizeof(double) * Q * N);
@@ -230,7 +275,7 @@ static void step_once(int nx, int ny, int nz, double tau, const uint8_t *flags,
                 double f[Q], fs[Q], Fc[3];
                 for (int i = 0; i < Q; ++i) f[i] = cur[i * N + c];
                 force_at(F, F_per_cell, c, N, Fc);
-                oracle_collide_cell(f, tau, Fc, fs);
+                oracle_collide_cell_model(model, f, tau, Fc, fs);
                 for (int i = 0; i < Q; ++i) {
                     int xd = wrap(x + E[i][0], nx), yd = wrap(y + E[i][1], ny),
                         zd = wrap(z + E[i][2], nz);
@@ -251,10 +296,11 @@ static void step_once(int nx, int ny, int nz, double tau, const uint8_t *flags,
     (void)nthreads;
 }
 
-/* Advance f (in place) by nsteps; u_wall (nullable) is the velocity of the
- * cells flagged 2. Returns 0, or -1 if scratch allocation failed. */
+/* Advance f (in place) by nsteps with the collision of `model`; u_wall
+ * (nullable) is the velocity of the cells flagged 2. Returns 0, or -1 if
+ * scratch allocation failed. */
 int oracle_run(int nx, int ny, int nz, double tau, const uint8_t *flags, const double *F,
-               int F_per_cell, const double *u_wall, double *f, int nsteps, int fmt, int nthreads)
+               int F_per_cell, const double *u_wall, double *f, int nsteps, int fmt, int nthreads, int model)
 {
     int64_t N = (int64_t)nx * ny * nz;
     double *tmp = (double *)malloc(sizeof(double) * Q * N);
@@ -262,7 +308,7 @@ int oracle_run(int nx, int ny, int nz, double tau, const uint8_t *flags, const d
     if (nthreads < 1) nthreads = 1;
     double *a = f, *b = tmp;
     for (int s = 0; s < nsteps; ++s) {
-        step_once(nx, ny, nz, tau, flags, F, F_per_cell, u_wall, a, b, nthreads);
+        step_once(nx, ny, nz, tau, flags, F, F_per_cell, u_wall, a, b, nthreads, model);
         round_storage(b, flags, N, fmt);
         double *t = a; a = b; b = t;
     }
@@ -271,9 +317,18 @@ int oracle_run(int nx, int ny, int nz, double tau, const uint8_t *flags, const d
     return 0;
 }
 
+/* Moments of one cell under `model`. */
+static void moments_of(int model, const double *f, const double *F, double *rho, double *u)
+{
+    if (model == 1)
+        oracle_moments_incompressible(f, F, rho, u);
+    else
+        oracle_moments(f, F, rho, u);
+}
+
 /* Macroscopic fields at state f: rho [N] and u [3][N]; 0 at solid cells. */
 void oracle_macros(int nx, int ny, int nz, const uint8_t *flags, const double *F,
-                   int F_per_cell, const double *f, double *rho, double *u)
+                   int F_per_cell, const double *f, double *rho, double *u, int model)
 {
     int64_t N = (int64_t)nx * ny * nz;
     for (int64_t c = 0; c < N; ++c) {
@@ -281,17 +336,18 @@ void oracle_macros(int nx, int ny, int nz, const uint8_t *flags, const double *F
         if (is_fluid(flags, c)) {
             for (int i = 0; i < Q; ++i) fc[i] = f[i * N + c];
             force_at(F, F_per_cell, c, N, Fc);
-            oracle_moments(fc, Fc, &r, uc);
+            moments_of(model, fc, Fc, &r, uc);
         }
         if (rho) rho[c] = r;
         for (int a = 0; a < 3; ++a) u[a * N + c] = uc[a];
     }
 }
 
-/* Totals over fluid cells: out = {sum rho, sum rho u_x, sum rho u_y, sum rho u_z},
- * with rho u = j + F/2. Accumulated in cell order. */
+/* Totals over fluid cells: out = {sum rho, and the three components of the
+ * sum of the momentum j + F/2} (rho u for model 0, u for model 1).
+ * Accumulated in cell order. */
 void oracle_sums(int nx, int ny, int nz, const uint8_t *flags, const double *F, int F_per_cell,
-                 const double *f, double *out)
+                 const double *f, double *out, int model)
 {
     int64_t N = (int64_t)nx * ny * nz;
     for (int k = 0; k < 4; ++k) out[k] = 0.0;
@@ -300,9 +356,9 @@ void oracle_sums(int nx, int ny, int nz, const uint8_t *flags, const double *F, 
         double fc[Q], Fc[3], r, uc[3];
         for (int i = 0; i < Q; ++i) fc[i] = f[i * N + c];
         force_at(F, F_per_cell, c, N, Fc);
-        oracle_moments(fc, Fc, &r, uc);
+        moments_of(model, fc, Fc, &r, uc);
         out[0] += r;
-        for (int a = 0; a < 3; ++a) out[1 + a] += r * uc[a];
+        for (int a = 0; a < 3; ++a) out[1 + a] += model == 1 ? uc[a] : r * uc[a];
     }
 }
 

@@ -23,18 +23,21 @@ Q = 19
 
 LBM_PATTERN_PULL, LBM_PATTERN_AA = 0, 1
 PATTERN = {"pull": LBM_PATTERN_PULL, "aa": LBM_PATTERN_AA}
+LBM_MODEL_QIAN, LBM_MODEL_INCOMPRESSIBLE = 0, 1
+MODEL = {"qian": LBM_MODEL_QIAN, "incompressible": LBM_MODEL_INCOMPRESSIBLE}
 
 
 class lbm_options(ctypes.Structure):
     _fields_ = [("storage", ctypes.c_int), ("cuda_stream", ctypes.c_void_p), ("row_align", ctypes.c_int),
-                ("pattern", ctypes.c_int)]
+                ("pattern", ctypes.c_int), ("model", ctypes.c_int)]
 
 
 class lbm_info(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int), ("pitch", ctypes.c_int),
                 ("storage", ctypes.c_int), ("real_size", ctypes.c_int), ("tau", ctypes.c_double),
                 ("n_cells", ctypes.c_int64), ("n_fluid", ctypes.c_int64), ("lattice_bytes", ctypes.c_size_t),
-                ("tape_bytes_per_step", ctypes.c_size_t), ("steps_done", ctypes.c_int64), ("pattern", ctypes.c_int)]
+                ("tape_bytes_per_step", ctypes.c_size_t), ("steps_done", ctypes.c_int64), ("pattern", ctypes.c_int),
+                ("model", ctypes.c_int)]
 
 
 _vp = ctypes.c_void_p

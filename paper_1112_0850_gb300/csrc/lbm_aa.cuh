@@ -18,14 +18,11 @@
 // thread, so the in-place update has no races (and the read-only load path is
 // safe: nothing is written before it is read within a launch).
 //
-// Solid cells hold NaN in every slot; nothing but NaN is ever written there
-// (a solid cell stores its own NaN marks again, so that 32-byte sectors are
-// written complete, and no other thread writes into a solid cell). A NaN
-// read in the odd step therefore marks a solid neighbour x - e_j, which is
-// also the target x + e_opp(j) of the outgoing population opp(j): one test
-// finds both the bounced reads and the bounced writes. As in the two-grid
-// kernel, a NaN makes rho NaN, so only cells next to a solid test their
-// populations one by one.
+// Halfway bounce-back needs only the odd step: where x - e_j is solid (bit
+// opp(j) of the push mask, i.e. x + e_opp(j) is solid too) population j is
+// read from slot j of x itself, and population opp(j) is written back there.
+// Solid cells are never read; the even step stores their lanes with the rest
+// of the pair (whole 32-byte sectors), the odd step leaves them alone.
 #pragma once
 
 #include "lbm_kernels.cuh"
@@ -91,8 +88,8 @@ __global__ void __launch_bounds__(256, StepBlocks<S>::value)
     const int c = cell_index(d.g, x0, y, z);
     bool live0, live1;
     pair_live<FLAGS>(d, c, x0 + 1 < d.g.nx, live0, live1);
-    // (solid cells load, collide and store their NaN marks like the others:
-    // an early exit on the flags would put a dependent load before the gather)
+    // (solid cells load, collide and store like the others: an early exit on
+    // the flags would put a dependent load before the gather)
     const R nan = quiet_nan<R>();
     V s[Q];
 #pragma unroll
@@ -100,23 +97,32 @@ __global__ void __launch_bounds__(256, StepBlocks<S>::value)
     V Fx, Fy, Fz;
     Guo2<R> G;
     pair_force<R, FORCE>(d, c, Fx, Fy, Fz, G);
-    const Mom2<R> m = moments2<R, FORCE != 0>(s, Fx, Fy, Fz);
+    const Mom2<R> m = moments2<R, FORCE != 0>(s, Fx, Fy, Fz, d.incomp);
     pair_check_record<R, RECORD>(d, c, live0, live1, m, tape);
-    collide2<R, FORCE != 0>(s, m, R(d.omega), Fx, Fy, Fz, G);
+    collide2<R, FORCE != 0>(s, m, R(d.omega), Fx, Fy, Fz, G, d.incomp);
     // a solid lane writes its NaN back (its slots stay marked)
 #pragma unroll
     for (int i = 0; i < Q; ++i)
         Stor<S>::st2(A + (long long)opp(i) * qs + c, !FLAGS || live0 ? s[i].x : nan, !FLAGS || live1 ? s[i].y : nan);
 }
 
-// Resident 256-thread blocks per SM the odd step is compiled for.
-template <int S> struct AaOddBlocks {
-    static constexpr int value = StepBlocks<S>::value;
+// Resident 256-thread blocks per SM the odd step is compiled for. With flags
+// its selected addresses need more registers: 2 blocks (128 registers) ran
+// the walled channel at 30.4 vs 22.8 GFLUPS (FP32, 3 blocks) and 33.2 vs 26.7
+// (FP16, 3 blocks).
+template <int S, bool FLAGS> struct AaOddBlocks {
+    static constexpr int value = S == LBM_F64 ? 1 : (FLAGS ? 2 : StepBlocks<S>::value);
 };
 
 // Odd step (swapped -> natural): gather from the neighbours, scatter to them.
+// Bounce-back reads and writes are both selected by the push mask (bit j: x +
+// e_j is solid): population i comes from slot i of x itself when bit opp(i)
+// is set, and goes to slot opp(i) of x itself when bit i is set. Every
+// address is a select, so the whole step is one branch-free sequence (a
+// NaN-driven fix-up with separate store paths measured twice as slow here:
+// its code size and divergence made it instruction-bound).
 template <int S, bool FLAGS, int FORCE, bool RECORD>
-__global__ void __launch_bounds__(256, AaOddBlocks<S>::value)
+__global__ void __launch_bounds__(256, AaOddBlocks<S, FLAGS>::value)
     k_aa_odd(const Dev d, typename Stor<S>::T *__restrict__ A, typename Stor<S>::R *__restrict__ tape) {
     typedef typename Stor<S>::T T;
     typedef typename Stor<S>::R R;
@@ -129,9 +135,14 @@ __global__ void __launch_bounds__(256, AaOddBlocks<S>::value)
     const long long qs = g.qs;
     const bool has1 = x0 + 1 < g.nx;
     const int c = cell_index(g, x0, y, z);
-    bool live0, live1;
-    pair_live<FLAGS>(d, c, has1, live0, live1);
-    const R nan = quiet_nan<R>();
+    uint32_t m0 = 0u, m1 = has1 ? 0u : SOLID_BIT;
+    if (FLAGS) {
+        const uint2 mm = __ldg(reinterpret_cast<const uint2 *>(d.mask + c));
+        m0 = mm.x;
+        m1 |= mm.y;
+    }
+    const bool live0 = !(m0 & SOLID_BIT), live1 = !(m1 & SOLID_BIT);
+    if (!live0 && !live1) return;  // (the gather waits for the mask anyway)
     // neighbour columns: x0 - 1, x0 + 1, x0 + 2 (the last only for a full pair)
     const int xa = wrap1(x0 - 1, g.nx);
     const int xb = wrap1(x0 + 1, g.nx);
@@ -139,91 +150,63 @@ __global__ void __launch_bounds__(256, AaOddBlocks<S>::value)
     V s[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        // f_i(x) = slot opp(i) of x - e_i
+        // f_i(x) = slot opp(i) of x - e_i, or slot i of x if x - e_i is solid
         const int row = (wrap1(z - ez(i), g.nz) * g.ny + wrap1(y - ey(i), g.ny)) * g.pitch;
-        const T *Pi = A + (long long)opp(i) * qs + row;
+        const T *Pn = A + (long long)opp(i) * qs + row;
+        const T *Po = A + (long long)i * qs + c;
+        const bool b0 = FLAGS && i > 0 && ((m0 >> opp(i)) & 1u), b1 = FLAGS && i > 0 && ((m1 >> opp(i)) & 1u);
         if (ex(i) == 0) {
-            Stor<S>::ld2(Pi + x0, s[i].x, s[i].y);
+            if (b0 == b1) {
+                Stor<S>::ld2(b0 ? Po : Pn + x0, s[i].x, s[i].y);
+            } else {
+                s[i].x = Stor<S>::ld(b0 ? Po : Pn + x0);
+                s[i].y = Stor<S>::ld(b1 ? Po + 1 : Pn + x0 + 1);
+            }
         } else {
-            s[i].x = Stor<S>::ld(Pi + (ex(i) > 0 ? xa : xb));
-            s[i].y = Stor<S>::ld(Pi + (ex(i) > 0 ? x0 : xc));
+            s[i].x = Stor<S>::ld(b0 ? Po : Pn + (ex(i) > 0 ? xa : xb));
+            s[i].y = Stor<S>::ld(b1 ? Po + 1 : Pn + (ex(i) > 0 ? x0 : xc));
+        }
+    }
+    const bool mv = FLAGS && d.moving_on && ((m0 | m1) & MOVING_BIT);
+    if (mv) {
+        // bounced off a moving wall: plus 6 w_i (e_i . u_w)
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+            if (((m0 >> opp(i)) & 1u) && d.flags[pull_src(g, x0, y, z, i)] == 2) s[i].x += wall_term<R>(d, i);
+            if (((m1 >> opp(i)) & 1u) && d.flags[pull_src(g, x0 + 1, y, z, i)] == 2) s[i].y += wall_term<R>(d, i);
         }
     }
     V Fx, Fy, Fz;
     Guo2<R> G;
     pair_force<R, FORCE>(d, c, Fx, Fy, Fz, G);
-    Mom2<R> m = moments2<R, FORCE != 0>(s, Fx, Fy, Fz);
-    // bit i of n0 / n1: x - e_i is solid (so x + e_opp(i) is too)
-    uint32_t n0 = 0u, n1 = 0u;
-    if (FLAGS && ((live0 && m.rho.x != m.rho.x) || (live1 && m.rho.y != m.rho.y))) {
-#pragma unroll
-        for (int i = 1; i < Q; ++i) {
-            const T *Po = A + (long long)i * qs + c;  // slot i of x: P_opp(i)(x)
-            if (live0 && s[i].x != s[i].x) {
-                n0 |= 1u << i;
-                s[i].x = Stor<S>::ld(Po);
-                if (d.moving_on && d.flags[pull_src(g, x0, y, z, i)] == 2) s[i].x += wall_term<R>(d, i);
-            }
-            if (live1 && s[i].y != s[i].y) {
-                n1 |= 1u << i;
-                s[i].y = Stor<S>::ld(Po + 1);
-                if (d.moving_on && d.flags[pull_src(g, x0 + 1, y, z, i)] == 2) s[i].y += wall_term<R>(d, i);
-            }
-        }
-        m = moments2<R, FORCE != 0>(s, Fx, Fy, Fz);
-    }
+    const Mom2<R> m = moments2<R, FORCE != 0>(s, Fx, Fy, Fz, d.incomp);
     pair_check_record<R, RECORD>(d, c, live0, live1, m, tape);
-    collide2<R, FORCE != 0>(s, m, R(d.omega), Fx, Fy, Fz, G);
-    if (!FLAGS || (live0 && live1 && !(n0 | n1))) {
-        // both cells fluid, no solid neighbour: P_i(x) to slot i of x + e_i
-        // (without flags the second cell may be missing at the end of an odd
-        // row: its pair store then fills the padding, its shifted store is
-        // skipped)
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            const int row = (wrap1(z + ez(i), g.nz) * g.ny + wrap1(y + ey(i), g.ny)) * g.pitch;
-            T *Pi = A + (long long)i * qs + row;
-            if (ex(i) == 0) {
-                Stor<S>::st2(Pi + x0, s[i].x, s[i].y);
-            } else {
-                Stor<S>::st(Pi + (ex(i) > 0 ? xb : xa), s[i].x);
-                if (FLAGS || has1) Stor<S>::st(Pi + (ex(i) > 0 ? xc : x0), s[i].y);
-            }
-        }
-        return;
-    }
-    // cells next to a solid, or a pair with one solid or missing cell: per
-    // cell, a population headed into a solid goes back to slot opp(i) of x
-    // (minus the moving-wall term of the direction it arrives from there); a
-    // solid (or padding) cell stores its own NaN marks again
+    collide2<R, FORCE != 0>(s, m, R(d.omega), Fx, Fy, Fz, G, d.incomp);
+    // P_i(x) to slot i of x + e_i, or to slot opp(i) of x if x + e_i is solid
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const int row = (wrap1(z + ez(i), g.nz) * g.ny + wrap1(y + ey(i), g.ny)) * g.pitch;
-        T *Pi = A + (long long)i * qs + row;
+        T *Pn = A + (long long)i * qs + row;
         T *Po = A + (long long)opp(i) * qs + c;
-        if (FLAGS && !live0 && !live1) {
-            Stor<S>::st2(A + (long long)i * qs + c, nan, nan);
-            continue;
+        const bool b0 = FLAGS && i > 0 && ((m0 >> i) & 1u), b1 = FLAGS && i > 0 && ((m1 >> i) & 1u);
+        if (ex(i) == 0 && b0 == b1 && live0 && live1) {
+            Stor<S>::st2(b0 ? Po : Pn + x0, s[i].x, s[i].y);
+        } else {
+            if (live0) Stor<S>::st(b0 ? Po : Pn + (ex(i) > 0 ? xb : (ex(i) < 0 ? xa : x0)), s[i].x);
+            if (live1) Stor<S>::st(b1 ? Po + 1 : Pn + (ex(i) > 0 ? xc : (ex(i) < 0 ? x0 : x0 + 1)), s[i].y);
         }
-        if (FLAGS && !live0) Stor<S>::st(A + (long long)i * qs + c, nan);
-        if (FLAGS && !live1) Stor<S>::st(A + (long long)i * qs + c + 1, nan);
-        if (live0) {
-            if ((n0 >> opp(i)) & 1u) {
-                R v = s[i].x;
-                if (d.moving_on && d.flags[push_dst(g, x0, y, z, i)] == 2) v -= wall_term<R>(d, i);
-                Stor<S>::st(Po, v);
-            } else {
-                Stor<S>::st(Pi + (ex(i) > 0 ? xb : (ex(i) < 0 ? xa : x0)), s[i].x);
-            }
-        }
-        if (live1) {
-            if ((n1 >> opp(i)) & 1u) {
-                R v = s[i].y;
-                if (d.moving_on && d.flags[push_dst(g, x0 + 1, y, z, i)] == 2) v -= wall_term<R>(d, i);
-                Stor<S>::st(Po + 1, v);
-            } else {
-                Stor<S>::st(Pi + (ex(i) > 0 ? xc : (ex(i) < 0 ? x0 : x0 + 1)), s[i].y);
-            }
+    }
+    if (mv) {
+        // a population bounced back from a moving wall arrives as opp(i) and
+        // carries 6 w_opp(i) (e_opp(i) . u_w) = -6 w_i (e_i . u_w): rewrite
+        // the own slots just stored (same thread, so this store is the last)
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+            T *Po = A + (long long)opp(i) * qs + c;
+            if (live0 && ((m0 >> i) & 1u) && d.flags[push_dst(g, x0, y, z, i)] == 2)
+                Stor<S>::st(Po, s[i].x - wall_term<R>(d, i));
+            if (live1 && ((m1 >> i) & 1u) && d.flags[push_dst(g, x0 + 1, y, z, i)] == 2)
+                Stor<S>::st(Po + 1, s[i].y - wall_term<R>(d, i));
         }
     }
 }
@@ -257,6 +240,7 @@ static cudaError_t launch_aa2(const Dev &d, void *A, int odd, void *tape) {
 
 template <int S>
 cudaError_t AaOps<S>::step(const Dev &d, void *A, int odd, void *tape) {
+    if (d.flags && !d.mask) return cudaErrorInvalidValue;  // the odd step selects with the push masks
     return d.flags ? launch_aa2<S, true>(d, A, odd, tape) : launch_aa2<S, false>(d, A, odd, tape);
 }
 

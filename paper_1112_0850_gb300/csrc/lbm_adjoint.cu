@@ -16,6 +16,10 @@
 //   b = sum mu_k B_k,  B_k = w_k [3 e_k + 9 (e_k.u) e_k - 3 u]
 //   d = sum mu_k D_k,  D_k = (1 - w/2) w_k [-3 F + 9 (e_k.F) e_k]
 // and the force gradient of that step is dL/dF(x) += b + d / (2 rho).
+// In the incompressible model (He & Luo: u = j', f_eq with the reference
+// density 1 in its velocity terms) A_k = w_k, u does not depend on rho, so
+//   lambda^n_m = (1 - w) mu_m + w sum_k mu_k w_k + [w b + d] . e_m,
+// and dL/dF(x) += b + d / 2 (B_k and D_k are unchanged).
 // Only (rho, u) of f^n enter, so the forward pass records just those.
 #include "lbm_launch.h"
 
@@ -53,7 +57,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_reduce_final(const double *__re
 // the force (see the header comment); adds this step's dL/dF to g.
 template <class R, bool FORCE>
 __device__ __forceinline__ void adj_collide(R mu[Q], R rho, R ux, R uy, R uz, R Fx, R Fy, R Fz, R om, R &gx, R &gy,
-                                            R &gz) {
+                                            R &gz, bool incomp) {
     const R usq = ux * ux + uy * uy + uz * uz;
     // P = sum_k w_k mu_k; A4 = sum over pairs w p (e.u)^2; b = sum w (3 q + 9 (e.u) p) e;
     // d = sum w p (e.F) e; with p = mu_i + mu_opp(i), q = mu_i - mu_opp(i)
@@ -79,7 +83,7 @@ __device__ __forceinline__ void adj_collide(R mu[Q], R rho, R ux, R uy, R uz, R 
             dz += td * R(ez(i));
         }
     }
-    const R a = P * (R(1) + R(1.5) * usq) - R(4.5) * A4;
+    const R a = incomp ? P : P * (R(1) + R(1.5) * usq) - R(4.5) * A4;
     bx -= R(3) * ux * P;
     by -= R(3) * uy * P;
     bz -= R(3) * uz * P;
@@ -89,8 +93,8 @@ __device__ __forceinline__ void adj_collide(R mu[Q], R rho, R ux, R uy, R uz, R 
         dy = cF * (R(9) * dy - R(3) * Fy * P);
         dz = cF * (R(9) * dz - R(3) * Fz * P);
     }
-    const R inv = R(1) / rho;
-    const R alpha = om * a - (dx * ux + dy * uy + dz * uz) * inv;
+    const R inv = incomp ? R(1) : R(1) / rho;
+    const R alpha = incomp ? om * a : om * a - (dx * ux + dy * uy + dz * uz) * inv;
     const R betx = om * bx + dx * inv, bety = om * by + dy * inv, betz = om * bz + dz * inv;
     const R keep = R(1) - om;
 #pragma unroll
@@ -173,8 +177,8 @@ __global__ void __launch_bounds__(256, AdjBlocks<R>::value)
     }
     const R om = R(d.omega);
     R g0x, g0y, g0z, g1x, g1y, g1z;
-    adj_collide<R, FORCE>(mu0, rho0, ux0, uy0, uz0, F0x, F0y, F0z, om, g0x, g0y, g0z);
-    adj_collide<R, FORCE>(mu1, rho1, ux1, uy1, uz1, F1x, F1y, F1z, om, g1x, g1y, g1z);
+    adj_collide<R, FORCE>(mu0, rho0, ux0, uy0, uz0, F0x, F0y, F0z, om, g0x, g0y, g0z, d.incomp);
+    adj_collide<R, FORCE>(mu1, rho1, ux1, uy1, uz1, F1x, F1y, F1z, om, g1x, g1y, g1z, d.incomp);
     // (a solid cell of a mixed pair gets a value nobody reads)
 #pragma unroll
     for (int i = 0; i < Q; ++i) st2_real(lam_out + (long long)i * qs + c, mu0[i], mu1[i]);
@@ -196,6 +200,7 @@ __global__ void __launch_bounds__(256, AdjBlocks<R>::value)
 // dL/du0 and dL/drho0 through f^0 = f_eq(rho0, u0):
 //   dL/du0 = rho0 sum_i lambda_i w_i [3 e_i + 9 (e_i.u0) e_i - 3 u0]
 //   dL/drho0 = sum_i lambda_i w_i [1 + 3 e_i.u0 + 9/2 (e_i.u0)^2 - 3/2 u0.u0]
+// (incompressible model: no rho0 factor in dL/du0, dL/drho0 = sum lambda_i w_i)
 template <class R, bool FLAGS>
 __global__ void __launch_bounds__(256)
     k_adj_init_grad(const Dev d, const R *__restrict__ lam, const R *__restrict__ rho0, const R *__restrict__ u0,
@@ -226,10 +231,13 @@ __global__ void __launch_bounds__(256)
         P += l;
         gr += l * (R(3) * eu + R(4.5) * eu * eu);
     }
-    grad_u0[cc] = r0 * (gx - R(3) * ux * P);
-    grad_u0[N + cc] = r0 * (gy - R(3) * uy * P);
-    grad_u0[2 * N + cc] = r0 * (gz - R(3) * uz * P);
-    if (grad_rho0) grad_rho0[cc] = P * (R(1) - R(1.5) * usq) + gr;
+    // d f_eq / d u carries rho0 in the Qian equilibrium, the reference
+    // density 1 in the incompressible one, where d f_eq / d rho0 = w
+    const R ru = d.incomp ? R(1) : r0;
+    grad_u0[cc] = ru * (gx - R(3) * ux * P);
+    grad_u0[N + cc] = ru * (gy - R(3) * uy * P);
+    grad_u0[2 * N + cc] = ru * (gz - R(3) * uz * P);
+    if (grad_rho0) grad_rho0[cc] = d.incomp ? P : P * (R(1) - R(1.5) * usq) + gr;
 }
 
 static dim3 grid_of(const Dev &d) { return dim3(d.L.nxb * d.L.nyb, d.g.nz); }

@@ -21,6 +21,7 @@ struct lbm_ctx {
     cudaStream_t stream;
     int device;
     lbm_pattern pattern;
+    lbm_model model;
     void *lat[2];       // pull: lat[cur] holds the latest post-collision populations;
                         // AA: lat[0] is the one lattice, lat[1] is null
     int cur;            // pull: current lattice; AA: 0 = natural layout, 1 = swapped
@@ -119,6 +120,7 @@ Dev make_dev(const lbm_ctx *ctx) {
     d.stream = ctx->stream;
     d.n_cells = (long long)ctx->g.nx * ctx->g.ny * ctx->g.nz;
     d.layout = ctx->pattern == LBM_PATTERN_AA ? (ctx->cur ? LAYOUT_AA_SWAP : LAYOUT_AA_NAT) : LAYOUT_PULL;
+    d.incomp = ctx->model == LBM_MODEL_INCOMPRESSIBLE;
     return d;
 }
 
@@ -255,6 +257,7 @@ lbm_status lbm_options_default(lbm_options *opt) {
     opt->cuda_stream = nullptr;
     opt->row_align = 0;
     opt->pattern = LBM_PATTERN_PULL;
+    opt->model = LBM_MODEL_QIAN;
     return LBM_OK;
 }
 
@@ -266,7 +269,8 @@ lbm_status lbm_create(lbm_ctx **out, int nx, int ny, int nz, double tau, const u
     lbm_options_default(&o);
     if (opt) o = *opt;
     if (nx < 1 || ny < 1 || nz < 1 || nz > 65535 || !(tau > 0.5) || !valid_storage(o.storage) ||
-        (o.pattern != LBM_PATTERN_PULL && o.pattern != LBM_PATTERN_AA))
+        (o.pattern != LBM_PATTERN_PULL && o.pattern != LBM_PATTERN_AA) ||
+        (o.model != LBM_MODEL_QIAN && o.model != LBM_MODEL_INCOMPRESSIBLE))
         return LBM_ERR_ARG;
     const bool aa = o.pattern == LBM_PATTERN_AA;
     const int pitch = pitch_for(nx, o.storage, o.row_align);
@@ -285,6 +289,7 @@ lbm_status lbm_create(lbm_ctx **out, int nx, int ny, int nz, double tau, const u
     ctx->L = row_launch(ctx->g);
     ctx->storage = o.storage;
     ctx->pattern = o.pattern;
+    ctx->model = o.model;
     ctx->tau = tau;
     for (int a = 0; a < 3; ++a) ctx->F[a] = force ? force[a] : 0.0;
     for (int a = 0; a < 3; ++a) ctx->u_wall[a] = 0.0;
@@ -321,8 +326,8 @@ lbm_status lbm_create(lbm_ctx **out, int nx, int ny, int nz, double tau, const u
         delete ctx;
         return LBM_ERR_CUDA;
     }
-    // lattices, flags (+ push masks for the two-grid kernels), reduction scratch
-    const size_t need = (aa ? 1 : 2) * lat_bytes + (flags ? (aa ? 1 : 5) * (size_t)qs : 0) +
+    // lattices, flags and push masks, reduction scratch
+    const size_t need = (aa ? 1 : 2) * lat_bytes + (flags ? 5 * (size_t)qs : 0) +
                         ((size_t)RED_BLOCKS * 4 + 8) * sizeof(double);
     if (need > free_b) {
         delete ctx;
@@ -362,7 +367,7 @@ lbm_status lbm_create(lbm_ctx **out, int nx, int ny, int nz, double tau, const u
               cudaMalloc((void **)&ctx->red_out, 4 * sizeof(double)) == cudaSuccess &&
               cudaMalloc((void **)&ctx->status_d, sizeof(unsigned)) == cudaSuccess;
     if (ok && flags) ok = cudaMalloc((void **)&ctx->flags_d, (size_t)qs) == cudaSuccess;
-    if (ok && flags && !aa) ok = cudaMalloc((void **)&ctx->mask_d, (size_t)qs * sizeof(uint32_t)) == cudaSuccess;
+    if (ok && flags) ok = cudaMalloc((void **)&ctx->mask_d, (size_t)qs * sizeof(uint32_t)) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         free_ctx(ctx);
@@ -375,8 +380,8 @@ lbm_status lbm_create(lbm_ctx **out, int nx, int ny, int nz, double tau, const u
     if (ok && flags)
         ok = cudaMemcpyAsync(ctx->flags_d, hflags.data(), (size_t)qs, cudaMemcpyHostToDevice, ctx->stream) ==
              cudaSuccess;
-    // push masks of the two-grid kernels, built on the device from the padded flags
-    if (ok && flags && !aa) ok = build_push_mask(ctx->g, ctx->flags_d, ctx->mask_d, ctx->stream) == cudaSuccess;
+    // push masks, built on the device from the padded flags
+    if (ok && flags) ok = build_push_mask(ctx->g, ctx->flags_d, ctx->mask_d, ctx->stream) == cudaSuccess;
     if (ok && flags) {
         Dev d = make_dev(ctx);
         ok = LBM_DISPATCH(ctx, fill_solid(d, ctx->lat[0])) == cudaSuccess &&
@@ -445,6 +450,7 @@ lbm_status lbm_get_info(const lbm_ctx *ctx, lbm_info *info) {
     info->tape_bytes_per_step = 4 * (size_t)ctx->g.qs * real_size(ctx->storage);
     info->steps_done = ctx->steps_done;
     info->pattern = ctx->pattern;
+    info->model = ctx->model;
     return LBM_OK;
 }
 
@@ -646,8 +652,8 @@ lbm_status lbm_set_state(lbm_ctx *ctx, const void *src, lbm_storage fmt) {
 }
 
 static lbm_status ensure_lambda(lbm_ctx *ctx) {
-    // the reverse step gathers with the push masks, which an AA-pattern
-    // context (whose forward kernels do not need them) builds on first use
+    // the reverse step gathers with the push masks (built at create; kept
+    // here for a context whose masks are missing)
     if (ctx->flags_d && !ctx->mask_d) {
         cudaError_t e = cudaMalloc((void **)&ctx->mask_d, (size_t)ctx->g.qs * sizeof(uint32_t));
         if (e != cudaSuccess) {

@@ -269,8 +269,10 @@ template <class R> struct Mom {
     R rho1, rho, ux, uy, uz;
 };
 
+// incomp: the incompressible model of He & Luo, u = j + F/2 (the momentum of
+// the reference density 1); otherwise u = (j + F/2)/rho.
 template <class R>
-__device__ __forceinline__ Mom<R> moments(const R s[Q], R Fx, R Fy, R Fz) {
+__device__ __forceinline__ Mom<R> moments(const R s[Q], R Fx, R Fy, R Fz, bool incomp = false) {
     Mom<R> m;
     // rho - 1 summed over opposite pairs first: the odd (velocity) parts of
     // s_i and s_opp(i) cancel exactly before any rounding of the total
@@ -283,6 +285,12 @@ __device__ __forceinline__ Mom<R> moments(const R s[Q], R Fx, R Fy, R Fz) {
     R jz = (((s[5] - s[6]) + (s[11] - s[14])) + ((s[13] - s[12]) + (s[15] - s[18]))) + (s[17] - s[16]);
     m.rho1 = r;
     m.rho = R(1) + r;
+    if (incomp) {
+        m.ux = jx + R(0.5) * Fx;
+        m.uy = jy + R(0.5) * Fy;
+        m.uz = jz + R(0.5) * Fz;
+        return m;
+    }
     R inv = rcp_rn(m.rho);
     m.ux = (jx + R(0.5) * Fx) * inv;
     m.uy = (jy + R(0.5) * Fy) * inv;
@@ -348,10 +356,10 @@ template <class R> struct Mom2 {
 
 // Moments of both cells: rho - 1 summed over opposite pairs first (the odd
 // parts of s_i and s_opp(i) cancel exactly before the total is rounded),
-// u = (j + F/2) / rho.
+// u = (j + F/2) / rho, or u = j + F/2 for the incompressible model.
 template <class R, bool FORCE>
 __device__ __forceinline__ Mom2<R> moments2(const typename Pair2<R>::V s[Q], typename Pair2<R>::V Fx,
-                                            typename Pair2<R>::V Fy, typename Pair2<R>::V Fz) {
+                                            typename Pair2<R>::V Fy, typename Pair2<R>::V Fz, bool incomp) {
     typedef typename Pair2<R>::V V;
     Mom2<R> m;
     V r = s[0];
@@ -371,6 +379,12 @@ __device__ __forceinline__ Mom2<R> moments2(const typename Pair2<R>::V s[Q], typ
     }
     m.rho1 = r;
     m.rho = vadd(vsplat(R(1)), r);
+    if (incomp) {
+        m.ux = jx;
+        m.uy = jy;
+        m.uz = jz;
+        return m;
+    }
     const V inv = vrcp(m.rho);
     m.ux = vmul(jx, inv);
     m.uy = vmul(jy, inv);
@@ -414,12 +428,14 @@ __device__ __forceinline__ Guo2<R> guo2(R omega, typename Pair2<R>::V Fx, typena
 // even and odd parts of the source (bracketed terms only with a force).
 // Without a force E +- P = a + b (t +- 3 e). a and b are formed per weight
 // class, the diagonal ones (w = 1/36) by halving the axis ones (w = 1/18),
-// so only one class's factors are held at a time.
+// so only one class's factors are held at a time. The incompressible model
+// (He & Luo) has the reference density 1 in place of rho in b.
 template <class R, bool FORCE>
 __device__ __forceinline__ void collide2(typename Pair2<R>::V s[Q], const Mom2<R> &m, R omega,
                                          typename Pair2<R>::V Fx, typename Pair2<R>::V Fy,
-                                         typename Pair2<R>::V Fz, const Guo2<R> &G) {
+                                         typename Pair2<R>::V Fz, const Guo2<R> &G, bool incomp) {
     typedef typename Pair2<R>::V V;
+    const V rho_e = incomp ? vsplat(R(1)) : m.rho;
     const V omc = vsplat(R(1) - omega);
     const V nusq15 = vmul(vsplat(R(-1.5)), vfma(m.uz, m.uz, vfma(m.uy, m.uy, vmul(m.ux, m.ux))));
     const R cF = R(1) - R(0.5) * omega;
@@ -428,12 +444,12 @@ __device__ __forceinline__ void collide2(typename Pair2<R>::V s[Q], const Mom2<R
     {  // rest population, w = 1/3 (3 w c = c)
         V a0 = vmul(vsplat(omega * R(1.0 / 3.0)), m.rho1);
         if (FORCE) a0 = vfma(vsplat(-cF), uF, a0);
-        const V b0 = vmul(vsplat(omega * R(1.0 / 3.0)), m.rho);
+        const V b0 = vmul(vsplat(omega * R(1.0 / 3.0)), rho_e);
         s[0] = vfma(omc, s[0], vfma(b0, nusq15, a0));
     }
     V a = vmul(vsplat(omega * R(1.0 / 18.0)), m.rho1);
     if (FORCE) a = vfma(vsplat(R(-1.0 / 6.0) * cF), uF, a);
-    V b = vmul(vsplat(omega * R(1.0 / 18.0)), m.rho);
+    V b = vmul(vsplat(omega * R(1.0 / 18.0)), rho_e);
 #pragma unroll
     for (int p = 0; p < NPAIR; ++p) {
         const int i = pair_first(p), io = opp(i);

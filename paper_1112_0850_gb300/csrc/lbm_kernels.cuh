@@ -248,7 +248,7 @@ __global__ void __launch_bounds__(256, StepBlocks<S>::value)
         ld2_real(F + 2 * g.qs + c, Fz.x, Fz.y);
         G = guo2<R>(R(d.omega), Fx, Fy, Fz);
     }
-    Mom2<R> m = moments2<R, FORCE != 0>(s, Fx, Fy, Fz);
+    Mom2<R> m = moments2<R, FORCE != 0>(s, Fx, Fy, Fz, d.incomp);
     if (FLAGS && NANS && ((live0 && m.rho.x != m.rho.x) || (live1 && m.rho.y != m.rho.y))) {
         // A solid source slot holds NaN, and a NaN anywhere makes rho NaN, so
         // one test per cell finds the cells next to a solid. Only those reload
@@ -267,7 +267,7 @@ __global__ void __launch_bounds__(256, StepBlocks<S>::value)
                 if (d.moving_on && d.flags[pull_src(g, x0 + 1, y, z, i)] == 2) s[i].y += wall_term<R>(d, i);
             }
         }
-        m = moments2<R, FORCE != 0>(s, Fx, Fy, Fz);
+        m = moments2<R, FORCE != 0>(s, Fx, Fy, Fz, d.incomp);
     }
     const bool bad0 = live0 && !(m.rho.x > R(0) && m.rho.x < R(1e30));
     const bool bad1 = live1 && !(m.rho.y > R(0) && m.rho.y < R(1e30));
@@ -279,7 +279,7 @@ __global__ void __launch_bounds__(256, StepBlocks<S>::value)
         st2_real(tape + 2 * qs + c, m.uy.x, m.uy.y);
         st2_real(tape + 3 * qs + c, m.uz.x, m.uz.y);
     }
-    collide2<R, FORCE != 0>(s, m, R(d.omega), Fx, Fy, Fz, G);
+    collide2<R, FORCE != 0>(s, m, R(d.omega), Fx, Fy, Fz, G, d.incomp);
     // The pair is stored whole, a solid cell included, so 32-byte sectors are
     // written complete: a solid cell's values are never read (load side), it
     // stores the NaN that marks it (NaN marks), or its slots are link targets
@@ -361,10 +361,10 @@ __global__ void __launch_bounds__(256) k_bounce(const Dev d, typename Stor<S>::T
 // f_eq_{opp(i)}(y) (so that the gather yields f^0 = f_eq(rho0, u0)), stored
 // shifted by -w_i.
 template <class R>
-__device__ __forceinline__ R feq_shifted(int i, R rho1, R ux, R uy, R uz) {
+__device__ __forceinline__ R feq_shifted(int i, R rho1, R ux, R uy, R uz, bool incomp) {
     const R eu = R(ex(i)) * ux + R(ey(i)) * uy + R(ez(i)) * uz;
     const R usq = ux * ux + uy * uy + uz * uz;
-    const R rho = R(1) + rho1;
+    const R rho = incomp ? R(1) : R(1) + rho1;  // (He & Luo: velocity terms of the reference density)
     return R(weight(i)) * (rho1 + rho * (R(3) * eu + R(4.5) * eu * eu - R(1.5) * usq));
 }
 
@@ -393,7 +393,8 @@ __global__ void __launch_bounds__(256)
         const R r1 = rho0 ? rho0[cc] - R(1) : R(0);
 #pragma unroll
         for (int i = 0; i < Q; ++i)
-            P[(long long)i * d.g.qs + c] = Stor<S>::enc(feq_shifted<R>(i, r1, u0[cc], u0[N + cc], u0[2 * N + cc]));
+            P[(long long)i * d.g.qs + c] =
+                Stor<S>::enc(feq_shifted<R>(i, r1, u0[cc], u0[N + cc], u0[2 * N + cc], d.incomp));
         return;
     }
 #pragma unroll
@@ -407,7 +408,7 @@ __global__ void __launch_bounds__(256)
             ct = cc;
         }
         const R r1 = rho0 ? rho0[ct] - R(1) : R(0);
-        const R v = feq_shifted<R>(k, r1, u0[ct], u0[N + ct], u0[2 * N + ct]);
+        const R v = feq_shifted<R>(k, r1, u0[ct], u0[N + ct], u0[2 * N + ct], d.incomp);
         // (the gather adds the moving-wall term to a value bounced off a moving wall)
         const R wv = !bounce_in_solid(S) && bounce && d.flags[t] == 2 && d.moving_on ? wall_term<R>(d, i) : R(0);
         P[(long long)i * d.g.qs + c] = Stor<S>::enc(v + wv);
@@ -496,7 +497,7 @@ __global__ void __launch_bounds__(256)
     gather<S, FLAGS>(d, P, x, y, z, c, s);
     R Fx = R(0), Fy = R(0), Fz = R(0);
     if (FORCE) force_at<R>(d, c, Fx, Fy, Fz);
-    const Mom<R> m = moments<R>(s, Fx, Fy, Fz);
+    const Mom<R> m = moments<R>(s, Fx, Fy, Fz, d.incomp);
     if (rho) rho[cc] = m.rho;
     u[cc] = m.ux;
     u[N + cc] = m.uy;
@@ -531,11 +532,13 @@ __global__ void __launch_bounds__(RED_THREADS)
         gather<S, FLAGS>(d, P, x, y, z, c, s);
         R Fx = R(0), Fy = R(0), Fz = R(0);
         if (FORCE) force_at<R>(d, c, Fx, Fy, Fz);
-        const Mom<R> m = moments<R>(s, Fx, Fy, Fz);
+        const Mom<R> m = moments<R>(s, Fx, Fy, Fz, d.incomp);
+        // momentum j + F/2: rho u, or u itself in the incompressible model
+        const double mr = d.incomp ? 1.0 : (double)m.rho;
         acc[0] += (double)m.rho;
-        acc[1] += (double)m.rho * (double)m.ux;
-        acc[2] += (double)m.rho * (double)m.uy;
-        acc[3] += (double)m.rho * (double)m.uz;
+        acc[1] += mr * (double)m.ux;
+        acc[2] += mr * (double)m.uy;
+        acc[3] += mr * (double)m.uz;
     }
     __shared__ double sm[RED_THREADS / 32][4];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -558,6 +561,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_reduce_final(const double *__re
 // ---------------------------------------------------------------------------
 // Adjoint seed (not in the paper): lambda^T_m = dL/drho + g.(e_m - u)/rho,
 // g = dL/du, at the gathered state; grad_F += g / (2 rho) (u contains F/2).
+// Incompressible model (u = j + F/2): lambda^T_m = dL/drho + g.e_m, grad_F += g/2.
 template <int S, bool FLAGS, bool FORCE>
 __global__ void __launch_bounds__(256)
     k_adj_seed(const Dev d, const typename Stor<S>::T *__restrict__ P, const typename Stor<S>::R *__restrict__ dL_du,
@@ -575,11 +579,11 @@ __global__ void __launch_bounds__(256)
     gather<S, FLAGS>(d, P, x, y, z, c, s);
     R Fx = R(0), Fy = R(0), Fz = R(0);
     if (FORCE) force_at<R>(d, c, Fx, Fy, Fz);
-    const Mom<R> m = moments<R>(s, Fx, Fy, Fz);
+    const Mom<R> m = moments<R>(s, Fx, Fy, Fz, d.incomp);
     const R gx = dL_du[cc], gy = dL_du[N + cc], gz = dL_du[2 * N + cc];
     const R dr = dL_drho ? dL_drho[cc] : R(0);
-    const R inv = R(1) / m.rho;
-    const R base = dr - (gx * m.ux + gy * m.uy + gz * m.uz) * inv;
+    const R inv = d.incomp ? R(1) : R(1) / m.rho;
+    const R base = d.incomp ? dr : dr - (gx * m.ux + gy * m.uy + gz * m.uz) * inv;
 #pragma unroll
     for (int i = 0; i < Q; ++i) lam[i * qs + c] = base + (R(ex(i)) * gx + R(ey(i)) * gy + R(ez(i)) * gz) * inv;
     if (grad_F) {

@@ -40,6 +40,7 @@ struct Dev {
     cudaStream_t stream;
     long long n_cells;     // nx * ny * nz
     int layout;            // LAYOUT_* of the lattice passed to readers and writers
+    bool incomp;           // incompressible equilibrium (He & Luo) instead of Qian's
 };
 
 // Bounce-back form per storage format (see k_step), the measured fastest on

@@ -33,18 +33,20 @@ class Lattice:
     "bf16s". Work is enqueued on `stream` (default: torch's current stream at
     construction). row_align: bytes each padded row starts on (0 = 128).
     pattern: "pull" (two lattices) or "aa" (one lattice updated in place).
+    model: "qian" (default) or "incompressible" (He & Luo equilibrium).
     """
 
     def __init__(self, nx, ny, nz, tau, flags=None, force=None, storage="f32", stream=None, row_align=0,
-                 pattern="pull"):
+                 pattern="pull", model="qian"):
         L = capi.lib()
         self.storage = _storage_code(storage)
         self.pattern = capi.PATTERN[pattern] if isinstance(pattern, str) else int(pattern)
         self.shape = (nz, ny, nx)
         self.real = _real_dtype(self.storage)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.model = capi.MODEL[model] if isinstance(model, str) else int(model)
         opt = capi.lbm_options(self.storage, ctypes.c_void_p(self.stream.cuda_stream), int(row_align),
-                               self.pattern)
+                               self.pattern, self.model)
         fl = None
         if flags is not None:
             fl = np.ascontiguousarray(np.asarray(flags.cpu() if torch.is_tensor(flags) else flags), dtype=np.uint8)

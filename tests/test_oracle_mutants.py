@@ -43,6 +43,16 @@ MUTANTS = [
     ("moving_wall_sign", "nxt[opposite(i) * N + c] = fs[i] - moving;", "nxt[opposite(i) * N + c] = fs[i] + moving;"),
     ("moving_wall_factor", "moving = 6.0 * weight(i) *", "moving = 2.0 * weight(i) *"),
     ("moving_wall_cell", "if (u_wall && is_moving_wall(flags, d))", "if (u_wall && is_moving_wall(flags, c))"),
+    ("inc_feq_rho_scaled", "weight(i) * (rho + 3.0 * cu", "weight(i) * rho * (1.0 + 3.0 * cu"),
+    ("inc_feq_quadratic", "4.5 * cu * cu", "4.0 * cu * cu"),
+    ("inc_velocity_over_rho", "u_out[a] = mom[a] + F[a] / 2.0;", "u_out[a] = (mom[a] + F[a] / 2.0) / r;"),
+    ("inc_velocity_full_force", "u_out[a] = mom[a] + F[a] / 2.0;", "u_out[a] = mom[a] + F[a];"),
+    ("inc_collide_ignores_model", "    if (model == 1) {\n        oracle_moments_incompressible(f, F, &rho, u);",
+     "    if (model == 7) {\n        oracle_moments_incompressible(f, F, &rho, u);"),
+    ("inc_init_ignores_model", "            if (model == 1)\n                oracle_equilibrium_incompressible",
+     "            if (model == 7)\n                oracle_equilibrium_incompressible"),
+    ("inc_step_ignores_model", "oracle_collide_cell_model(model, f, tau, Fc, fs);", "oracle_collide_cell_model(0, f, tau, Fc, fs);"),
+    ("inc_sums_rho_weighted", "model == 1 ? uc[a] : r * uc[a]", "r * uc[a]"),
 ]
 
 
