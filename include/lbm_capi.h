@@ -76,6 +76,7 @@ typedef enum {
 /* Bits of the device status word. */
 #define LBM_STATUS_DIVERGED 0x1u /* some fluid cell had rho <= 0 or non-finite rho */
 #define LBM_STATUS_INDEX    0x2u /* a checked build caught an out-of-range index */
+#define LBM_STATUS_TIMEOUT  0x4u /* a kernel gave up waiting (about 1 s) for its asynchronous copies */
 
 /* Streaming pattern: how the fused update moves populations through memory. */
 typedef enum {
@@ -103,6 +104,10 @@ typedef struct {
     lbm_pattern pattern; /* default LBM_PATTERN_PULL */
     lbm_model model;     /* default LBM_MODEL_QIAN; applies to every call (step, macros,
                             totals, init, adjoint) */
+    int stage_rows;      /* 1: the two-grid step stages its source rows in shared memory with
+                            TMA bulk copies where the rows allow it (FP32 and 16-bit storage,
+                            rows a multiple of 16 bytes); 0 (default): it loads them directly,
+                            which measured faster on walled lattices. Same bits either way. */
 } lbm_options;
 
 typedef struct {

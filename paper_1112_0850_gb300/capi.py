@@ -17,6 +17,7 @@ STORAGE_NAME = {v: k for k, v in STORAGE.items()}
 STORAGE_BYTES = {LBM_F64: 8, LBM_F32: 4, LBM_F16S: 2, LBM_BF16S: 2}
 STATUS_DIVERGED = 0x1
 STATUS_INDEX = 0x2
+STATUS_TIMEOUT = 0x4
 NOALLOC_MAX_CELLS = 268435456
 Q = 19
 
@@ -29,7 +30,7 @@ MODEL = {"qian": LBM_MODEL_QIAN, "incompressible": LBM_MODEL_INCOMPRESSIBLE}
 
 class lbm_options(ctypes.Structure):
     _fields_ = [("storage", ctypes.c_int), ("cuda_stream", ctypes.c_void_p), ("row_align", ctypes.c_int),
-                ("pattern", ctypes.c_int), ("model", ctypes.c_int)]
+                ("pattern", ctypes.c_int), ("model", ctypes.c_int), ("stage_rows", ctypes.c_int)]
 
 
 class lbm_info(ctypes.Structure):

@@ -22,6 +22,8 @@ struct lbm_ctx {
     int device;
     lbm_pattern pattern;
     lbm_model model;
+    bool stage_rows;
+    int num_sms;
     void *lat[2];       // pull: lat[cur] holds the latest post-collision populations;
                         // AA: lat[0] is the one lattice, lat[1] is null
     int cur;            // pull: current lattice; AA: 0 = natural layout, 1 = swapped
@@ -121,6 +123,8 @@ Dev make_dev(const lbm_ctx *ctx) {
     d.n_cells = (long long)ctx->g.nx * ctx->g.ny * ctx->g.nz;
     d.layout = ctx->pattern == LBM_PATTERN_AA ? (ctx->cur ? LAYOUT_AA_SWAP : LAYOUT_AA_NAT) : LAYOUT_PULL;
     d.incomp = ctx->model == LBM_MODEL_INCOMPRESSIBLE;
+    d.row_staging = ctx->stage_rows;
+    d.num_sms = ctx->num_sms;
     return d;
 }
 
@@ -258,6 +262,7 @@ lbm_status lbm_options_default(lbm_options *opt) {
     opt->row_align = 0;
     opt->pattern = LBM_PATTERN_PULL;
     opt->model = LBM_MODEL_QIAN;
+    opt->stage_rows = 0;
     return LBM_OK;
 }
 
@@ -290,6 +295,8 @@ lbm_status lbm_create(lbm_ctx **out, int nx, int ny, int nz, double tau, const u
     ctx->storage = o.storage;
     ctx->pattern = o.pattern;
     ctx->model = o.model;
+    ctx->stage_rows = o.stage_rows != 0;
+    ctx->num_sms = 1;
     ctx->tau = tau;
     for (int a = 0; a < 3; ++a) ctx->F[a] = force ? force[a] : 0.0;
     for (int a = 0; a < 3; ++a) ctx->u_wall[a] = 0.0;
@@ -314,6 +321,7 @@ lbm_status lbm_create(lbm_ctx **out, int nx, int ny, int nz, double tau, const u
     ctx->graph[0] = ctx->graph[1] = nullptr;
     ctx->graph_failed = false;
     cudaError_t e = cudaGetDevice(&ctx->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device);
     if (e != cudaSuccess) {
         delete ctx;
         return LBM_ERR_CUDA;

@@ -58,6 +58,13 @@ template <> struct Stor<LBM_F64> {
     static __device__ __forceinline__ void st2(T *p, R a, R b) {
         __stcs(reinterpret_cast<double2 *>(p), make_double2(a, b));
     }
+    // plain loads (shared memory)
+    static __device__ __forceinline__ R ls(const T *p) { return *p; }
+    static __device__ __forceinline__ void ls2(const T *p, R &a, R &b) {
+        const double2 v = *reinterpret_cast<const double2 *>(p);
+        a = v.x;
+        b = v.y;
+    }
 };
 
 template <> struct Stor<LBM_F32> {
@@ -73,6 +80,12 @@ template <> struct Stor<LBM_F32> {
     }
     static __device__ __forceinline__ void st2(T *p, R a, R b) {
         __stcs(reinterpret_cast<float2 *>(p), make_float2(a, b));
+    }
+    static __device__ __forceinline__ R ls(const T *p) { return *p; }
+    static __device__ __forceinline__ void ls2(const T *p, R &a, R &b) {
+        const float2 v = *reinterpret_cast<const float2 *>(p);
+        a = v.x;
+        b = v.y;
     }
 };
 
@@ -105,6 +118,12 @@ template <> struct Stor<LBM_F16S> {
         v.h = __floats2half2_rn(a, b);
         __stcs(reinterpret_cast<unsigned *>(p), v.u);
     }
+    static __device__ __forceinline__ R ls(const T *p) { return __half2float(*p); }
+    static __device__ __forceinline__ void ls2(const T *p, R &a, R &b) {
+        const float2 f = __half22float2(*reinterpret_cast<const __half2 *>(p));
+        a = f.x;
+        b = f.y;
+    }
 };
 
 template <> struct Stor<LBM_BF16S> {
@@ -135,6 +154,12 @@ template <> struct Stor<LBM_BF16S> {
         } v;
         v.h = __floats2bfloat162_rn(a, b);
         __stcs(reinterpret_cast<unsigned *>(p), v.u);
+    }
+    static __device__ __forceinline__ R ls(const T *p) { return __bfloat162float(*p); }
+    static __device__ __forceinline__ void ls2(const T *p, R &a, R &b) {
+        const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(p));
+        a = f.x;
+        b = f.y;
     }
 };
 

@@ -163,19 +163,40 @@ template <> __device__ __forceinline__ Guo2<double> uniform_guo<double>(const De
     return t;
 }
 
-template <int S, bool FLAGS, int FORCE, bool RECORD>
-__global__ void __launch_bounds__(256, StepBlocks<S>::value)
-    k_step(const Dev d, const typename Stor<S>::T *__restrict__ src, typename Stor<S>::T *__restrict__ dst,
-           typename Stor<S>::R *__restrict__ tape) {
+// Where the gather finds the row of population i that cell row (y, z) pulls
+// from, (y - e_iy, z - e_iz): in the source lattice in global memory, or in
+// a shared-memory copy of those 19 rows (see k_step_tma).
+template <int S> struct GlobalRows {
+    typedef typename Stor<S>::T T;
+    typedef typename Stor<S>::R R;
+    const T *src;
+    __device__ __forceinline__ const T *row(const Geom &g, int i, int y, int z) const {
+        return src + (long long)i * g.qs + (wrap1(z - ez(i), g.nz) * g.ny + wrap1(y - ey(i), g.ny)) * g.pitch;
+    }
+    static __device__ __forceinline__ R ld(const T *p) { return Stor<S>::ld(p); }
+    static __device__ __forceinline__ void ld2(const T *p, R &a, R &b) { Stor<S>::ld2(p, a, b); }
+};
+template <int S> struct SharedRows {
+    typedef typename Stor<S>::T T;
+    typedef typename Stor<S>::R R;
+    const T *buf;  // [Q][pitch]
+    __device__ __forceinline__ const T *row(const Geom &g, int i, int, int) const { return buf + i * g.pitch; }
+    static __device__ __forceinline__ R ld(const T *p) { return Stor<S>::ls(p); }
+    static __device__ __forceinline__ void ld2(const T *p, R &a, R &b) { Stor<S>::ls2(p, a, b); }
+};
+
+// One fused step for the cell pair (x0, x0 + 1) of row (y, z): gather through
+// `rows` (the cell's own opposite populations, for bounce-back, from src),
+// collide, store to dst.
+template <int S, bool FLAGS, int FORCE, bool RECORD, class Rows>
+__device__ __forceinline__ void step_pair(const Dev &d, const Rows &rows, const typename Stor<S>::T *__restrict__ src,
+                                          typename Stor<S>::T *__restrict__ dst, typename Stor<S>::R *__restrict__ tape,
+                                          int x0, int y, int z) {
     typedef typename Stor<S>::T T;
     typedef typename Stor<S>::R R;
     typedef typename Pair2<R>::V V;  // lane x: cell x0, lane y: cell x0 + 1
     constexpr bool LINKS = Bounce<S>::mode != BB_LOAD;  // flag-free gather (links or NaN marks)
     constexpr bool NANS = Bounce<S>::mode == BB_NANS;
-    int x0, y, z;
-    if (!pair_cell(d.g, d.P.nxb, blockDim.x, blockDim.y, blockIdx.x, blockIdx.y, threadIdx.x, threadIdx.y, x0,
-                   y, z))
-        return;
     const Geom &g = d.g;
     const bool has1 = x0 + 1 < g.nx;
     const int c = cell_index(g, x0, y, z);
@@ -203,8 +224,7 @@ __global__ void __launch_bounds__(256, StepBlocks<S>::value)
     V s[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        const int row = (wrap1(z - ez(i), g.nz) * g.ny + wrap1(y - ey(i), g.ny)) * g.pitch;
-        const T *Pi = src + (long long)i * g.qs + row;
+        const T *Pi = rows.row(g, i, y, z);
         if (FLAGS && !LINKS && i > 0) {
             const T *Po = src + (long long)opp(i) * g.qs + c;  // own cell, opposite population
             const bool b0 = (m0 >> opp(i)) & 1u, b1 = (m1 >> opp(i)) & 1u;
@@ -220,10 +240,10 @@ __global__ void __launch_bounds__(256, StepBlocks<S>::value)
                 s[i].y = Stor<S>::ld(b1 ? Po + 1 : Pi + (ex(i) > 0 ? x0 : xc));
             }
         } else if (ex(i) == 0) {
-            Stor<S>::ld2(Pi + x0, s[i].x, s[i].y);
+            Rows::ld2(Pi + x0, s[i].x, s[i].y);
         } else {
-            s[i].x = Stor<S>::ld(Pi + (ex(i) > 0 ? xa : xb));
-            s[i].y = Stor<S>::ld(Pi + (ex(i) > 0 ? x0 : xc));
+            s[i].x = Rows::ld(Pi + (ex(i) > 0 ? xa : xb));
+            s[i].y = Rows::ld(Pi + (ex(i) > 0 ? x0 : xc));
         }
     }
     if (FLAGS && !LINKS && d.moving_on && ((m0 | m1) & MOVING_BIT)) {
@@ -318,6 +338,128 @@ __global__ void __launch_bounds__(256, StepBlocks<S>::value)
                     if (d.flags[t] == 2) Stor<S>::st(dst + (long long)opp(j) * g.qs + t, s[j].y - wall_term<R>(d, j));
                 }
             }
+        }
+    }
+}
+
+template <int S, bool FLAGS, int FORCE, bool RECORD>
+__global__ void __launch_bounds__(256, StepBlocks<S>::value)
+    k_step(const Dev d, const typename Stor<S>::T *__restrict__ src, typename Stor<S>::T *__restrict__ dst,
+           typename Stor<S>::R *__restrict__ tape) {
+    int x0, y, z;
+    if (!pair_cell(d.g, d.P.nxb, blockDim.x, blockDim.y, blockIdx.x, blockIdx.y, threadIdx.x, threadIdx.y, x0,
+                   y, z))
+        return;
+    step_pair<S, FLAGS, FORCE, RECORD>(d, GlobalRows<S>{src}, src, dst, tape, x0, y, z);
+}
+
+// ---------------------------------------------------------------------------
+// The step with its source rows staged in shared memory by the Tensor Memory
+// Accelerator (FP32 and 16-bit storage). A cell row (y, z) pulls population
+// i from the one row (y - e_iy, z - e_iz) of array i, shifted by e_ix, so a
+// block that updates whole cell rows needs exactly 19 source rows per row.
+// One thread issues them as 1-D bulk asynchronous copies (cp.async.bulk,
+// whole padded rows: 16-byte aligned, sizes a multiple of 16 bytes) that
+// signal an mbarrier with their byte count; the block computes row k from one
+// buffer while the copies of row k + 1 land in the other. The loads are thus
+// in flight without holding registers. The gathered values, the arithmetic
+// (step_pair) and the stores are the same as in k_step, so both give the
+// same bits. Opt-in (lbm_options.stage_rows): measured against the direct
+// kernel it gains 1-4% on 16-bit lattices without obstacles, and loses on
+// walled ones, where the block barrier per row exposes the latency of the
+// bounce-back reloads that the direct kernel hides behind other warps.
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+// Wait for the phase with the given parity to complete, for at most ~1 s.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - t0 > (1LL << 31)) return false;
+    return true;
+}
+__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+// Order this thread's earlier shared-memory accesses (and the block's, after
+// a barrier) before later asynchronous-proxy writes to the same memory.
+__device__ __forceinline__ void fence_async_shared() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+// The 19 source rows of cell row r into buf [Q][pitch], counted on bar.
+template <int S>
+__device__ __forceinline__ void issue_source_rows(const Geom &g, const typename Stor<S>::T *src,
+                                                  typename Stor<S>::T *buf, uint64_t *bar, int r, uint32_t rowbytes) {
+    const int y = r % g.ny, z = r / g.ny;
+    mbar_arrive_expect_tx(bar, (uint32_t)Q * rowbytes);
+#pragma unroll 1
+    for (int i = 0; i < Q; ++i) {
+        const long long row = (long long)(wrap1(z - ez(i), g.nz) * g.ny + wrap1(y - ey(i), g.ny)) * g.pitch;
+        bulk_copy_g2s(buf + i * g.pitch, src + (long long)i * g.qs + row, rowbytes, bar);
+    }
+}
+
+template <int S, bool FLAGS, int FORCE, bool RECORD>
+__global__ void __launch_bounds__(512)
+    k_step_tma(const Dev d, const typename Stor<S>::T *__restrict__ src, typename Stor<S>::T *__restrict__ dst,
+               typename Stor<S>::R *__restrict__ tape) {
+    typedef typename Stor<S>::T T;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const Geom &g = d.g;
+    const uint32_t rowbytes = (uint32_t)g.pitch * (uint32_t)sizeof(T);
+    T *buf = reinterpret_cast<T *>(smem_raw);  // [2][Q][pitch]
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw + 2 * Q * rowbytes);
+    const int nrows = g.ny * g.nz;
+    const int t = threadIdx.x, stride = gridDim.x;
+    if (t == 0) {
+        mbar_init(bar, 1);
+        mbar_init(bar + 1, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    int r = blockIdx.x;
+    if (t == 0) {
+        if (r < nrows) issue_source_rows<S>(g, src, buf, bar, r, rowbytes);
+        if (r + stride < nrows) issue_source_rows<S>(g, src, buf + Q * g.pitch, bar + 1, r + stride, rowbytes);
+    }
+    const int pairs = (g.nx + 1) >> 1;
+    for (int k = 0; r < nrows; ++k, r += stride) {
+        const int b = k & 1;
+        const bool ok = mbar_wait_bounded(bar + b, (k >> 1) & 1);
+        if (__syncthreads_or(!ok)) {
+            // copies that never completed: report, give the other buffer's
+            // copies a bounded chance to land, and leave
+            if (t == 0) {
+                atomicOr(d.status, LBM_STATUS_TIMEOUT);
+                mbar_wait_bounded(bar + (b ^ 1), ((k + 1) >> 1) & 1);
+            }
+            return;
+        }
+        const int y = r % g.ny, z = r / g.ny;
+        const SharedRows<S> rows{buf + b * Q * g.pitch};
+        for (int p = t; p < pairs; p += blockDim.x) step_pair<S, FLAGS, FORCE, RECORD>(d, rows, src, dst, tape, 2 * p, y, z);
+        __syncthreads();  // every read of buffer b is done
+        if (t == 0 && r + 2 * stride < nrows) {
+            fence_async_shared();
+            issue_source_rows<S>(g, src, buf + b * Q * g.pitch, bar + b, r + 2 * stride, rowbytes);
         }
     }
 }
@@ -615,11 +757,57 @@ static cudaError_t launch_step3(const Dev &d, const void *src, void *dst, void *
     return cudaGetLastError();
 }
 
+// Shared memory of the row-staged step: two buffers of 19 padded rows.
+constexpr int TMA_SMEM_MAX = 200 * 1024;
+template <int S> inline int tma_smem_bytes(const Dev &d) {
+    return 2 * Q * d.g.pitch * (int)sizeof(typename Stor<S>::T) + 16;
+}
+// The row-staged step serves the flag-free gathers (NaN marks, links) of
+// FP32 and 16-bit storage when rows are whole 16-byte multiples and two
+// buffers fit.
+template <int S> inline bool tma_eligible(const Dev &d) {
+    const long long rowbytes = (long long)d.g.pitch * sizeof(typename Stor<S>::T);
+    return d.row_staging && Bounce<S>::mode != BB_LOAD && rowbytes % 16 == 0 && tma_smem_bytes<S>(d) <= TMA_SMEM_MAX;
+}
+
+template <int S, bool FLAGS, int FORCE, bool RECORD>
+static cudaError_t launch_step_tma4(const Dev &d, const void *src, void *dst, void *tape) {
+    typedef typename Stor<S>::T T;
+    typedef typename Stor<S>::R R;
+    auto kern = k_step_tma<S, FLAGS, FORCE, RECORD>;
+    static bool configured = false;  // (idempotent: racing first calls set the same value)
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, TMA_SMEM_MAX);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    const int smem = tma_smem_bytes<S>(d);
+    const int pairs = (d.g.nx + 1) / 2;
+    const int threads = pairs >= 512 ? 512 : (pairs + 31) / 32 * 32;
+    int occ = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem);
+    if (e != cudaSuccess) return e;
+    const long long nrows = (long long)d.g.ny * d.g.nz;
+    const long long want = (long long)(occ > 0 ? occ : 1) * d.num_sms;
+    const int grid = (int)(nrows < want ? nrows : want);
+    kern<<<grid, threads, smem, d.stream>>>(d, static_cast<const T *>(src), static_cast<T *>(dst),
+                                           static_cast<R *>(tape));
+    return cudaGetLastError();
+}
+
+template <int S, bool FLAGS, int FORCE>
+static cudaError_t launch_step3_any(const Dev &d, const void *src, void *dst, void *tape) {
+    if (tma_eligible<S>(d))
+        return tape ? launch_step_tma4<S, FLAGS, FORCE, true>(d, src, dst, tape)
+                    : launch_step_tma4<S, FLAGS, FORCE, false>(d, src, dst, tape);
+    return launch_step3<S, FLAGS, FORCE>(d, src, dst, tape);
+}
+
 template <int S, bool FLAGS>
 static cudaError_t launch_step2(const Dev &d, const void *src, void *dst, void *tape) {
-    if (d.Ffield) return launch_step3<S, FLAGS, 2>(d, src, dst, tape);
-    if (d.force_on) return launch_step3<S, FLAGS, 1>(d, src, dst, tape);
-    return launch_step3<S, FLAGS, 0>(d, src, dst, tape);
+    if (d.Ffield) return launch_step3_any<S, FLAGS, 2>(d, src, dst, tape);
+    if (d.force_on) return launch_step3_any<S, FLAGS, 1>(d, src, dst, tape);
+    return launch_step3_any<S, FLAGS, 0>(d, src, dst, tape);
 }
 
 template <int S>

@@ -41,6 +41,8 @@ struct Dev {
     long long n_cells;     // nx * ny * nz
     int layout;            // LAYOUT_* of the lattice passed to readers and writers
     bool incomp;           // incompressible equilibrium (He & Luo) instead of Qian's
+    bool row_staging;      // use the TMA row-staged step kernel where it applies
+    int num_sms;           // multiprocessors of the device (grid of persistent kernels)
 };
 
 // Bounce-back form per storage format (see k_step), the measured fastest on

@@ -34,10 +34,12 @@ class Lattice:
     construction). row_align: bytes each padded row starts on (0 = 128).
     pattern: "pull" (two lattices) or "aa" (one lattice updated in place).
     model: "qian" (default) or "incompressible" (He & Luo equilibrium).
+    stage_rows: True makes the two-grid step stage its source rows in shared
+    memory with TMA bulk copies where possible (same results; off by default).
     """
 
     def __init__(self, nx, ny, nz, tau, flags=None, force=None, storage="f32", stream=None, row_align=0,
-                 pattern="pull", model="qian"):
+                 pattern="pull", model="qian", stage_rows=False):
         L = capi.lib()
         self.storage = _storage_code(storage)
         self.pattern = capi.PATTERN[pattern] if isinstance(pattern, str) else int(pattern)
@@ -46,7 +48,7 @@ class Lattice:
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.model = capi.MODEL[model] if isinstance(model, str) else int(model)
         opt = capi.lbm_options(self.storage, ctypes.c_void_p(self.stream.cuda_stream), int(row_align),
-                               self.pattern, self.model)
+                               self.pattern, self.model, 1 if stage_rows else 0)
         fl = None
         if flags is not None:
             fl = np.ascontiguousarray(np.asarray(flags.cpu() if torch.is_tensor(flags) else flags), dtype=np.uint8)
