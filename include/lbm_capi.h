@@ -98,9 +98,11 @@ typedef enum {
 typedef struct {
     lbm_storage storage; /* default LBM_F32 */
     void *cuda_stream;   /* cudaStream_t used for every launch and copy; NULL = default stream */
-    int row_align;       /* bytes each padded row starts on (Sec. 6 padding): 0 = 128 (default);
-                            otherwise a power of two >= 2 elements of the storage format (the
-                            kernels move pairs of cells); 2 elements = no padding beyond pairs */
+    int row_align;       /* bytes each padded row starts on: 0 (default) = rows padded only
+                            to a whole pair of cells (the kernels move pairs); otherwise a
+                            power of two >= 2 elements of the storage format, e.g. 128 for
+                            the paper's padding (Sec. 6), which measured 4-8% slower on GB300
+                            for row lengths that are not multiples of it */
     lbm_pattern pattern; /* default LBM_PATTERN_PULL */
     lbm_model model;     /* default LBM_MODEL_QIAN; applies to every call (step, macros,
                             totals, init, adjoint) */
@@ -278,7 +280,7 @@ int lbm_lattice_table(int *e, double *w, int *opp);
 
 /* Host-side check of the index arithmetic of every kernel launch the library
  * makes for an nx * ny * nz lattice in format fmt with rows aligned to
- * row_align bytes (as in lbm_options; 0 = 128): walks every thread of each
+ * row_align bytes (as in lbm_options; 0 = pairs only): walks every thread of each
  * launch configuration on the CPU and verifies that every address it forms
  * lies inside its buffer (two-grid and AA step kernels, reverse step,
  * per-cell kernels, reduction). Returns the number of violations (0 = all in

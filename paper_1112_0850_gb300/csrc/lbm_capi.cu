@@ -69,10 +69,10 @@ size_t real_size(lbm_storage s) { return s == LBM_F64 ? 8 : 4; }
 bool valid_storage(int s) { return s >= LBM_F64 && s <= LBM_BF16S; }
 
 // Elements per padded row so that each row starts on a row_align-byte
-// boundary (0 = 128 bytes); -1 if row_align is not allowed.
+// boundary (0 = a whole pair of cells); -1 if row_align is not allowed.
 int pitch_for(int nx, lbm_storage s, int row_align = 0) {
     const int eb = (int)storage_bytes(s);
-    const int align = row_align ? row_align : 128;
+    const int align = row_align ? row_align : 2 * eb;
     if (align < 2 * eb || (align & (align - 1)) || align > 4096) return -1;
     const int per = align / eb;
     return (nx + per - 1) / per * per;

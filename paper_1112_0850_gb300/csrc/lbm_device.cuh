@@ -116,7 +116,7 @@ template <> struct Stor<LBM_F16S> {
             __half2 h;
         } v;
         v.h = __floats2half2_rn(a, b);
-        __stcs(reinterpret_cast<unsigned *>(p), v.u);
+        *reinterpret_cast<unsigned *>(p) = v.u;  // (write-back: +1% over streaming stores)
     }
     static __device__ __forceinline__ R ls(const T *p) { return __half2float(*p); }
     static __device__ __forceinline__ void ls2(const T *p, R &a, R &b) {
@@ -153,7 +153,7 @@ template <> struct Stor<LBM_BF16S> {
             __nv_bfloat162 h;
         } v;
         v.h = __floats2bfloat162_rn(a, b);
-        __stcs(reinterpret_cast<unsigned *>(p), v.u);
+        *reinterpret_cast<unsigned *>(p) = v.u;  // (write-back: +1% over streaming stores)
     }
     static __device__ __forceinline__ R ls(const T *p) { return __bfloat162float(*p); }
     static __device__ __forceinline__ void ls2(const T *p, R &a, R &b) {

@@ -31,7 +31,8 @@ class Lattice:
     flags: optional uint8 array [nz][ny][nx] (0 fluid, 2 moving wall, other nonzero solid);
     force: optional uniform body force (3,); storage: "f64" | "f32" | "f16s" |
     "bf16s". Work is enqueued on `stream` (default: torch's current stream at
-    construction). row_align: bytes each padded row starts on (0 = 128).
+    construction). row_align: bytes each padded row starts on (0 = pairs only,
+    128 = the paper's padding).
     pattern: "pull" (two lattices) or "aa" (one lattice updated in place).
     model: "qian" (default) or "incompressible" (He & Luo equilibrium).
     stage_rows: True makes the two-grid step stage its source rows in shared

@@ -56,12 +56,12 @@ SIZES = [(1, 1, 1), (1, 3, 2), (3, 1, 1), (2, 2, 2), (5, 4, 3), (8, 6, 5), (31, 
          (64, 3, 3), (65, 2, 3), (100, 5, 2), (256, 2, 2), (257, 3, 2), (300, 2, 1), (513, 1, 2)]
 
 
-@pytest.mark.parametrize("align", ["default", "pairs"])
+@pytest.mark.parametrize("align", ["default", "128"])
 @pytest.mark.parametrize("fmt", [0, 1, 2, 3])
 @pytest.mark.parametrize("size", SIZES, ids=lambda s: "x".join(map(str, s)))
 def test_launch_indices_in_bounds(lib, size, fmt, align):
     nx, ny, nz = size
-    row_align = 0 if align == "default" else 2 * capi.STORAGE_BYTES[fmt]  # minimal rows: pairs only
+    row_align = 0 if align == "default" else 128  # default: rows padded to pairs only
     assert lib.lbm_check_launch_indices(nx, ny, nz, fmt, row_align) == 0
 
 

@@ -21,7 +21,8 @@ def _run(storage, case, staged, steps=9, record=False, u_wall=None, flags_overri
         flags = flags_override
     nz, ny, nx = u0.shape[1:]
     real = REAL[storage]
-    lat = Lattice(nx, ny, nz, tau, flags=flags, force=F, storage=storage, stage_rows=staged)
+    # 128-byte rows, so that every case is eligible for the staged kernel
+    lat = Lattice(nx, ny, nz, tau, flags=flags, force=F, storage=storage, stage_rows=staged, row_align=128)
     if Ffield is not None:
         lat.set_force_field(torch.as_tensor(Ffield, dtype=real).cuda())
     if u_wall is not None:
