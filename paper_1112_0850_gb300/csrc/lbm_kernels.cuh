@@ -346,6 +346,10 @@ template <int S, bool FLAGS, int FORCE, bool RECORD>
 __global__ void __launch_bounds__(256, StepBlocks<S>::value)
     k_step(const Dev d, const typename Stor<S>::T *__restrict__ src, typename Stor<S>::T *__restrict__ dst,
            typename Stor<S>::R *__restrict__ tape) {
+    // let the bounce kernel (a programmatic dependent) be scheduled once every
+    // block of this grid is running; it still waits for this grid to complete
+    // before it reads what this grid writes
+    if (FLAGS && LinkBounce<S>::value) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     int x0, y, z;
     if (!pair_cell(d.g, d.P.nxb, blockDim.x, blockDim.y, blockIdx.x, blockIdx.y, threadIdx.x, threadIdx.y, x0,
                    y, z))
@@ -473,6 +477,8 @@ __global__ void __launch_bounds__(512)
 // coalesced); all index loads are issued before the value loads, and all value
 // loads before the stores, so the two dependent round trips are shared.
 constexpr int LINKS_PER_THREAD = 4;
+// Launch k_bounce as a programmatic dependent of the step kernel.
+constexpr int BOUNCE_PDL = 1;
 
 template <int S>
 __global__ void __launch_bounds__(256) k_bounce(const Dev d, typename Stor<S>::T *__restrict__ P) {
@@ -490,6 +496,10 @@ __global__ void __launch_bounds__(256) k_bounce(const Dev d, typename Stor<S>::T
         const int k = k0 + r * blockDim.x;
         l[r] = k < n ? __ldg(L + k) : make_uint2(0u, 0u);  // (fluid cell, solid cell)
     }
+    // Launched as a programmatic dependent of the step kernel: the links above
+    // do not depend on it, the values below do. Wait here for the step's grid
+    // to complete (a no-op when launched normally).
+    asm volatile("griddepcontrol.wait;" ::: "memory");
 #pragma unroll
     for (int r = 0; r < LINKS_PER_THREAD; ++r)
         if (k0 + r * blockDim.x < n) v[r] = from[l[r].x];
@@ -817,8 +827,21 @@ cudaError_t Ops<S>::step(const Dev &d, const void *src, void *dst, void *tape) {
     cudaError_t e = launch_step2<S, true>(d, src, dst, tape);
     if (e != cudaSuccess || !LinkBounce<S>::value || d.link_max == 0) return e;
     const int per_block = 256 * LINKS_PER_THREAD;
-    k_bounce<S><<<dim3((d.link_max + per_block - 1) / per_block, Q - 1), 256, 0, d.stream>>>(
-        d, static_cast<typename Stor<S>::T *>(dst));
+    // programmatic dependent launch: the bounce kernel's blocks may start (and
+    // load their links) while the step kernel drains; they wait for its grid
+    // before reading the values (griddepcontrol.wait in k_bounce)
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((d.link_max + per_block - 1) / per_block, Q - 1);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = d.stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = BOUNCE_PDL;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, k_bounce<S>, d, static_cast<typename Stor<S>::T *>(dst));
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
