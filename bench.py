@@ -328,6 +328,8 @@ def main():
                     help="two lattices (pull) or one lattice updated in place (AA pattern)")
     ap.add_argument("--sweep", action="store_true",
                     help="domain-size sweep of periodic boxes and the row-padding ablation (one JSON line)")
+    ap.add_argument("--adjoint-only", type=int, default=0, metavar="K",
+                    help="run K recorded steps, the seed and K reverse steps on the channel (for profilers) and exit")
     ap.add_argument("--record-traffic", nargs="+", metavar="KEY=REPORT",
                     help="write profiles/step_kernel_traffic.json from ncu reports and exit")
     args = ap.parse_args()
@@ -359,6 +361,22 @@ def main():
     flags = workload_flags()
     F = (GX, 0.0, 0.0)
     storage = args.storage
+    if args.adjoint_only:
+        # the reverse step alone, for profilers: K recorded steps, seed, K reverse steps
+        K = args.adjoint_only
+        lat = Lattice(NX, NY, NZ, TAU, flags=flags, force=F, storage=storage)
+        lat.init_equilibrium(lat.zeros(3))
+        tape = lat.new_tape(K)
+        gF = lat.zeros(3)
+        lat.step(args.warmup)
+        lat.step_record(K, tape)
+        lat.adjoint_seed(lat.zeros(3).add_(1e-3), None, gF)
+        lat.adjoint_step(K, tape, gF)
+        torch.cuda.synchronize()
+        status = lat.status_word()
+        lat.close()
+        print(json.dumps({"adjoint_only": K, "storage": storage, "status_word": status}), flush=True)
+        return 0 if status == 0 else 1
     if args.case == "channel":
         lat = Lattice(NX, NY, NZ, TAU, flags=flags, force=F, storage=storage, pattern=args.pattern)
         lat.init_equilibrium(lat.zeros(3))

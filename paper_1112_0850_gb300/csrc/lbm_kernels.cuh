@@ -785,17 +785,14 @@ static cudaError_t launch_step_tma4(const Dev &d, const void *src, void *dst, vo
     typedef typename Stor<S>::T T;
     typedef typename Stor<S>::R R;
     auto kern = k_step_tma<S, FLAGS, FORCE, RECORD>;
-    static bool configured = false;  // (idempotent: racing first calls set the same value)
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, TMA_SMEM_MAX);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
+    // (set on every launch: the attribute belongs to the current device's context)
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, TMA_SMEM_MAX);
+    if (e != cudaSuccess) return e;
     const int smem = tma_smem_bytes<S>(d);
     const int pairs = (d.g.nx + 1) / 2;
     const int threads = pairs >= 512 ? 512 : (pairs + 31) / 32 * 32;
     int occ = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem);
     if (e != cudaSuccess) return e;
     const long long nrows = (long long)d.g.ny * d.g.nz;
     const long long want = (long long)(occ > 0 ? occ : 1) * d.num_sms;
