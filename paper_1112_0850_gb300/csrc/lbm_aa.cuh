@@ -81,7 +81,7 @@ __global__ void __launch_bounds__(256, StepBlocks<S>::value)
     typedef typename Stor<S>::R R;
     typedef typename Pair2<R>::V V;
     int x0, y, z;
-    if (!pair_cell(d.g, d.P.nxb, blockDim.x, blockDim.y, blockIdx.x, blockIdx.y, threadIdx.x, threadIdx.y, x0,
+    if (!pair_cell(d.g, d.P, blockDim.x, blockDim.y, blockIdx.x, blockIdx.y, threadIdx.x, threadIdx.y, x0,
                    y, z))
         return;
     const long long qs = d.g.qs;
@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(256, AaOddBlocks<S, FLAGS>::value)
     typedef typename Stor<S>::R R;
     typedef typename Pair2<R>::V V;
     int x0, y, z;
-    if (!pair_cell(d.g, d.P.nxb, blockDim.x, blockDim.y, blockIdx.x, blockIdx.y, threadIdx.x, threadIdx.y, x0,
+    if (!pair_cell(d.g, d.P, blockDim.x, blockDim.y, blockIdx.x, blockIdx.y, threadIdx.x, threadIdx.y, x0,
                    y, z))
         return;
     const Geom &g = d.g;

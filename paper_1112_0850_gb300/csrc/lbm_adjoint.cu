@@ -122,7 +122,7 @@ __global__ void __launch_bounds__(256, AdjBlocks<R>::value)
     k_adj_step(const Dev d, const R *__restrict__ lam_in, R *__restrict__ lam_out, const R *__restrict__ tape,
                R *__restrict__ grad_F) {
     int x0, y, z;
-    if (!pair_cell(d.g, d.P.nxb, blockDim.x, blockDim.y, blockIdx.x, blockIdx.y, threadIdx.x, threadIdx.y, x0,
+    if (!pair_cell(d.g, d.P, blockDim.x, blockDim.y, blockIdx.x, blockIdx.y, threadIdx.x, threadIdx.y, x0,
                    y, z))
         return;
     const Geom &g = d.g;
@@ -262,7 +262,7 @@ __global__ void __launch_bounds__(256)
 static dim3 grid_of(const Dev &d) { return dim3(d.L.nxb * d.L.nyb, d.g.nz); }
 static dim3 block_of(const Dev &d) { return dim3(d.L.bx_threads, d.L.by_threads); }
 // the reverse step runs on the paired launch of the forward step kernels
-static dim3 pair_grid_of(const Dev &d) { return dim3(d.P.nxb * d.P.nyb, d.g.nz); }
+static dim3 pair_grid_of(const Dev &d) { return dim3(d.P.nxb * d.P.nyb, d.P.nzr); }
 static dim3 pair_block_of(const Dev &d) { return dim3(d.P.bx_threads, d.P.by_threads); }
 
 template <class R, bool FLAGS>

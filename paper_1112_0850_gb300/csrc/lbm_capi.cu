@@ -27,6 +27,7 @@ struct lbm_ctx {
     void *lat[2];       // pull: lat[cur] holds the latest post-collision populations;
                         // AA: lat[0] is the one lattice, lat[1] is null
     int cur;            // pull: current lattice; AA: 0 = natural layout, 1 = swapped
+    int box[4];         // y0, rows, z0, planes: the smallest y/z box holding every fluid cell
     uint8_t *flags_d;   // padded [qs], 1 = solid (padding included), or null
     uint32_t *mask_d;   // padded [qs] push masks for the step kernels, or null
     uint32_t *links_d;  // bounce-back links (fluid cell, solid cell), grouped by direction
@@ -91,7 +92,7 @@ Dev make_dev(const lbm_ctx *ctx) {
     Dev d;
     d.g = ctx->g;
     d.L = ctx->L;
-    d.P = pair_launch(ctx->g);
+    d.P = pair_launch(ctx->g, ctx->box[0], ctx->box[1], ctx->box[2], ctx->box[3]);
     d.flags = ctx->flags_d;
     d.mask = ctx->mask_d;
     d.Ffield = ctx->Ffield_d;
@@ -301,6 +302,10 @@ lbm_status lbm_create(lbm_ctx **out, int nx, int ny, int nz, double tau, const u
     for (int a = 0; a < 3; ++a) ctx->F[a] = force ? force[a] : 0.0;
     for (int a = 0; a < 3; ++a) ctx->u_wall[a] = 0.0;
     ctx->has_moving = false;
+    ctx->box[0] = 0;
+    ctx->box[1] = ny;
+    ctx->box[2] = 0;
+    ctx->box[3] = nz;
     ctx->stream = static_cast<cudaStream_t>(o.cuda_stream);
     ctx->lat[0] = ctx->lat[1] = nullptr;
     ctx->cur = 0;
@@ -358,15 +363,27 @@ lbm_status lbm_create(lbm_ctx **out, int nx, int ny, int nz, double tau, const u
         }
         hflags.assign((size_t)qs, 1);
         n_fluid = 0;
+        long long ylo = ny, yhi = -1, zlo = nz, zhi = -1;  // box of the fluid cells
         for (long long z = 0; z < nz; ++z)
             for (long long y = 0; y < ny; ++y)
                 for (long long x = 0; x < nx; ++x) {
                     const uint8_t v = canon[(size_t)(x + nx * (y + ny * z))];
                     const uint8_t f = v == 0 ? 0 : (v == 2 ? 2 : 1);  // fluid, moving wall, solid
                     hflags[(size_t)((z * ny + y) * pitch + x)] = f;
-                    n_fluid += f ? 0 : 1;
                     if (f == 2) ctx->has_moving = true;
+                    if (f) continue;
+                    ++n_fluid;
+                    if (y < ylo) ylo = y;
+                    if (y > yhi) yhi = y;
+                    if (z < zlo) zlo = z;
+                    if (z > zhi) zhi = z;
                 }
+        if (n_fluid > 0) {  // the step kernels update rows of this box only
+            ctx->box[0] = (int)ylo;
+            ctx->box[1] = (int)(yhi - ylo + 1);
+            ctx->box[2] = (int)zlo;
+            ctx->box[3] = (int)(zhi - zlo + 1);
+        }
     }
     ctx->n_fluid = n_fluid;
     bool ok = cudaMalloc(&ctx->lat[0], lat_bytes) == cudaSuccess &&
@@ -832,7 +849,7 @@ int64_t lbm_check_launch_indices(int nx, int ny, int nz, lbm_storage fmt, int ro
             for (int ty = 0; ty < P.by_threads; ++ty)
                 for (int tx = 0; tx < P.bx_threads; ++tx) {
                     int x0, y, z;
-                    if (!pair_cell(g, P.nxb, P.bx_threads, P.by_threads, bx, bz, tx, ty, x0, y, z)) continue;
+                    if (!pair_cell(g, P, P.bx_threads, P.by_threads, bx, bz, tx, ty, x0, y, z)) continue;
                     const bool has1 = x0 + 1 < nx;
                     visited2 += has1 ? 2 : 1;
                     const int c = cell_index(g, x0, y, z);

@@ -202,6 +202,7 @@ LBM_HD int cell_index(const Geom &g, int x, int y, int z) { return (z * g.ny + y
 struct RowLaunch {
     int bx_threads, by_threads;  // block shape
     int nxb, nyb;                // x blocks per row, y groups
+    int y0, z0, nyr, nzr;        // paired launch: the rows y0 .. y0 + nyr - 1 of planes z0 .. z0 + nzr - 1
 };
 
 inline RowLaunch row_launch(const Geom &g) {
@@ -212,6 +213,9 @@ inline RowLaunch row_launch(const Geom &g) {
     L.by_threads = 256 / w;
     L.nxb = (g.nx + w - 1) / w;
     L.nyb = (g.ny + L.by_threads - 1) / L.by_threads;
+    L.y0 = L.z0 = 0;
+    L.nyr = g.ny;
+    L.nzr = g.nz;
     return L;
 }
 
@@ -220,25 +224,33 @@ inline RowLaunch row_launch(const Geom &g) {
 // split into the fewest blocks of at most 256 threads, each a multiple of 32
 // wide, so few lanes idle when nx is not a power of two; rows stack in y up to
 // 256 threads per block.
-inline RowLaunch pair_launch(const Geom &g) {
+// The paired launch covers whole rows of the box y0 <= y < y0 + nyr,
+// z0 <= z < z0 + nzr (the whole lattice by default; the step kernels get the
+// smallest box holding every fluid cell, since rows of solid cells need no
+// update).
+inline RowLaunch pair_launch(const Geom &g, int y0 = 0, int nyr = -1, int z0 = 0, int nzr = -1) {
     RowLaunch L;
     const int half = (g.nx + 1) / 2;
     L.nxb = (half + 255) / 256;
     const int per = (half + L.nxb - 1) / L.nxb;
     L.bx_threads = (per + 31) / 32 * 32;
     L.by_threads = 256 / L.bx_threads;
-    L.nyb = (g.ny + L.by_threads - 1) / L.by_threads;
+    L.y0 = y0;
+    L.z0 = z0;
+    L.nyr = nyr < 0 ? g.ny : nyr;
+    L.nzr = nzr < 0 ? g.nz : nzr;
+    L.nyb = (L.nyr + L.by_threads - 1) / L.by_threads;
     return L;
 }
 
-LBM_HD bool pair_cell(const Geom &g, int nxb, int bdx, int bdy, int bx, int bz, int tx, int ty, int &x0, int &y,
-                      int &z) {
-    const int xb = bx % nxb;
-    const int yg = bx / nxb;
+LBM_HD bool pair_cell(const Geom &g, const RowLaunch &P, int bdx, int bdy, int bx, int bz, int tx, int ty, int &x0,
+                      int &y, int &z) {
+    const int xb = bx % P.nxb;
+    const int yg = bx / P.nxb;
     x0 = 2 * (xb * bdx + tx);
-    y = yg * bdy + ty;
-    z = bz;
-    return x0 < g.nx && y < g.ny && z < g.nz;
+    y = P.y0 + yg * bdy + ty;
+    z = P.z0 + bz;
+    return x0 < g.nx && y < P.y0 + P.nyr && z < P.z0 + P.nzr;
 }
 
 // Push mask of a cell (precomputed on the host from the flags): bit j,

@@ -351,7 +351,7 @@ __global__ void __launch_bounds__(256, StepBlocks<S>::value)
     // before it reads what this grid writes
     if (FLAGS && LinkBounce<S>::value) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     int x0, y, z;
-    if (!pair_cell(d.g, d.P.nxb, blockDim.x, blockDim.y, blockIdx.x, blockIdx.y, threadIdx.x, threadIdx.y, x0,
+    if (!pair_cell(d.g, d.P, blockDim.x, blockDim.y, blockIdx.x, blockIdx.y, threadIdx.x, threadIdx.y, x0,
                    y, z))
         return;
     step_pair<S, FLAGS, FORCE, RECORD>(d, GlobalRows<S>{src}, src, dst, tape, x0, y, z);
@@ -409,10 +409,17 @@ __device__ __forceinline__ void fence_async_shared() { asm volatile("fence.proxy
 __device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
 
 // The 19 source rows of cell row r into buf [Q][pitch], counted on bar.
+// Row r of the fluid box (see pair_launch) as (y, z).
+__device__ __forceinline__ void box_row(const RowLaunch &P, int r, int &y, int &z) {
+    y = P.y0 + r % P.nyr;
+    z = P.z0 + r / P.nyr;
+}
+
 template <int S>
-__device__ __forceinline__ void issue_source_rows(const Geom &g, const typename Stor<S>::T *src,
+__device__ __forceinline__ void issue_source_rows(const Geom &g, const RowLaunch &P, const typename Stor<S>::T *src,
                                                   typename Stor<S>::T *buf, uint64_t *bar, int r, uint32_t rowbytes) {
-    const int y = r % g.ny, z = r / g.ny;
+    int y, z;
+    box_row(P, r, y, z);
     mbar_arrive_expect_tx(bar, (uint32_t)Q * rowbytes);
 #pragma unroll 1
     for (int i = 0; i < Q; ++i) {
@@ -431,7 +438,7 @@ __global__ void __launch_bounds__(512)
     const uint32_t rowbytes = (uint32_t)g.pitch * (uint32_t)sizeof(T);
     T *buf = reinterpret_cast<T *>(smem_raw);  // [2][Q][pitch]
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw + 2 * Q * rowbytes);
-    const int nrows = g.ny * g.nz;
+    const int nrows = d.P.nyr * d.P.nzr;  // the rows of the fluid box
     const int t = threadIdx.x, stride = gridDim.x;
     if (t == 0) {
         mbar_init(bar, 1);
@@ -441,8 +448,8 @@ __global__ void __launch_bounds__(512)
     __syncthreads();
     int r = blockIdx.x;
     if (t == 0) {
-        if (r < nrows) issue_source_rows<S>(g, src, buf, bar, r, rowbytes);
-        if (r + stride < nrows) issue_source_rows<S>(g, src, buf + Q * g.pitch, bar + 1, r + stride, rowbytes);
+        if (r < nrows) issue_source_rows<S>(g, d.P, src, buf, bar, r, rowbytes);
+        if (r + stride < nrows) issue_source_rows<S>(g, d.P, src, buf + Q * g.pitch, bar + 1, r + stride, rowbytes);
     }
     const int pairs = (g.nx + 1) >> 1;
     for (int k = 0; r < nrows; ++k, r += stride) {
@@ -457,13 +464,14 @@ __global__ void __launch_bounds__(512)
             }
             return;
         }
-        const int y = r % g.ny, z = r / g.ny;
+        int y, z;
+        box_row(d.P, r, y, z);
         const SharedRows<S> rows{buf + b * Q * g.pitch};
         for (int p = t; p < pairs; p += blockDim.x) step_pair<S, FLAGS, FORCE, RECORD>(d, rows, src, dst, tape, 2 * p, y, z);
         __syncthreads();  // every read of buffer b is done
         if (t == 0 && r + 2 * stride < nrows) {
             fence_async_shared();
-            issue_source_rows<S>(g, src, buf + b * Q * g.pitch, bar + b, r + 2 * stride, rowbytes);
+            issue_source_rows<S>(g, d.P, src, buf + b * Q * g.pitch, bar + b, r + 2 * stride, rowbytes);
         }
     }
 }
@@ -751,7 +759,7 @@ inline dim3 row_grid(const Dev &d) { return dim3(d.L.nxb * d.L.nyb, d.g.nz); }
 inline dim3 row_block(const Dev &d) { return dim3(d.L.bx_threads, d.L.by_threads); }
 
 // The step kernels run on the paired launch (two cells per thread).
-inline dim3 step_grid(const Dev &d) { return dim3(d.P.nxb * d.P.nyb, d.g.nz); }
+inline dim3 step_grid(const Dev &d) { return dim3(d.P.nxb * d.P.nyb, d.P.nzr); }
 inline dim3 step_block(const Dev &d) { return dim3(d.P.bx_threads, d.P.by_threads); }
 
 template <int S, bool FLAGS, int FORCE>
@@ -794,7 +802,7 @@ static cudaError_t launch_step_tma4(const Dev &d, const void *src, void *dst, vo
     int occ = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem);
     if (e != cudaSuccess) return e;
-    const long long nrows = (long long)d.g.ny * d.g.nz;
+    const long long nrows = (long long)d.P.nyr * d.P.nzr;
     const long long want = (long long)(occ > 0 ? occ : 1) * d.num_sms;
     const int grid = (int)(nrows < want ? nrows : want);
     kern<<<grid, threads, smem, d.stream>>>(d, static_cast<const T *>(src), static_cast<T *>(dst),
