@@ -297,6 +297,9 @@ def test_create_rejects_bad_arguments():
             Lattice(*args)
     with pytest.raises(LBMError):
         Lattice(4, 4, 4, 0.6, storage=7)
+    for kw in [{"pattern": 2}, {"model": 5}, {"row_align": 3}, {"row_align": 8192}, {"row_align": 4, "storage": "f64"}]:
+        with pytest.raises(LBMError):
+            Lattice(4, 4, 4, 0.6, **kw)
 
 
 @pytest.mark.parametrize("storage", STORAGES)
