@@ -54,6 +54,20 @@ def test_fp64_adjoint_matches_reference(with_flags):
     assert rel_l2(gF, gFr, m) <= 1e-10
 
 
+@pytest.mark.parametrize("T", [1, 2])
+@pytest.mark.parametrize("with_flags", [False, True])
+def test_fp64_single_step_transpose_matches_reference(T, with_flags):
+    """One or two steps: the GPU's J^T applied to the seed (the transpose of the
+    step Jacobian, without accumulation over many steps) against autograd."""
+    flags, u0, F, ut, _ = _problem(frac=0.2 if with_flags else 0.0, seed=33)
+    L, gu, gF = _gpu_grad("f64", flags, u0, F, ut, T, 0.7, 1)
+    Lr, gur, gFr = oadj.gradients(u0, F, 0.7, T, ut, flags)
+    m = fluid_mask(flags, u0.shape[1:])
+    assert abs(L - Lr) <= 1e-13 * Lr
+    assert rel_l2(gu, gur, m) <= 1e-12
+    assert rel_l2(gF, gFr, m) <= 1e-12
+
+
 @pytest.mark.parametrize("storage", ["f32", "f16s"])
 def test_fp32_adjoint_matches_reference(storage):
     flags, u0, F, ut, T = _problem()
