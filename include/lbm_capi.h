@@ -224,6 +224,15 @@ lbm_status lbm_reduce_state_noalloc(const void *state, lbm_storage fmt, int nx, 
                                     const uint8_t *flags, const double force[3], double *out,
                                     void *cuda_stream);
 
+/* The totals of lbm_reduce for the current state, then n >= 1 steps, with
+ * the totals summed inside the first step from the moments it forms anyway
+ * (no pass over the lattice of their own: the reduction fused into the step
+ * as an epilogue). out: 4 doubles, host (the call synchronizes) or device
+ * (asynchronous). The same totals as lbm_reduce up to the order of the FP64
+ * sums; deterministic. With LBM_PATTERN_AA the totals are taken by a
+ * reduction pass before the steps. */
+lbm_status lbm_step_reduce(lbm_ctx *ctx, int n, double *out);
+
 /* Copy the current state out as shifted populations s_i = f_i - w_i in format
  * fmt, canonical [19][nz][ny][nx] (element type double / float / binary16 /
  * bfloat16). Solid cells read 0. Host or device destination. */

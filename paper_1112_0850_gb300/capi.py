@@ -58,6 +58,7 @@ PROTOTYPES = {
     "lbm_step": (_st, [_vp, _i]),
     "lbm_macros": (_st, [_vp, _vp, _vp]),
     "lbm_reduce": (_st, [_vp, _vp]),
+    "lbm_step_reduce": (_st, [_vp, _i, _vp]),
     "lbm_reduce_state_noalloc": (_st, [_vp, _i, _i, _i, _i, _vp, _vp, _vp, _vp]),
     "lbm_get_state": (_st, [_vp, _vp, _i]),
     "lbm_set_state": (_st, [_vp, _vp, _i]),

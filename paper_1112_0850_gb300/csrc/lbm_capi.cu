@@ -39,6 +39,8 @@ struct lbm_ctx {
     bool lam_valid;
     double *red_partials;  // RED_BLOCKS * 4 doubles
     double *red_out;       // 4 doubles
+    double *step_partials; // 4 doubles per block of the step grid (fused reduction), on first use
+    size_t step_partials_n;
     unsigned *status_d;
     void *staging;         // device buffer for host-side arrays
     size_t staging_bytes;
@@ -245,8 +247,9 @@ void free_ctx(lbm_ctx *ctx) {
     cudaSetDevice(ctx->device);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     drop_graphs(ctx);
-    void *ptrs[] = {ctx->lat[0], ctx->lat[1],  ctx->flags_d,     ctx->mask_d,   ctx->links_d, ctx->Ffield_d,
-                    ctx->lam[0], ctx->lam[1], ctx->red_partials, ctx->red_out, ctx->status_d, ctx->staging};
+    void *ptrs[] = {ctx->lat[0], ctx->lat[1],  ctx->flags_d,     ctx->mask_d,   ctx->links_d,        ctx->Ffield_d,
+                    ctx->lam[0], ctx->lam[1], ctx->red_partials, ctx->red_out, ctx->step_partials, ctx->status_d,
+                    ctx->staging};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete ctx;
@@ -319,6 +322,8 @@ lbm_status lbm_create(lbm_ctx **out, int nx, int ny, int nz, double tau, const u
     ctx->lcur = 0;
     ctx->lam_valid = false;
     ctx->red_partials = ctx->red_out = nullptr;
+    ctx->step_partials = nullptr;
+    ctx->step_partials_n = 0;
     ctx->status_d = nullptr;
     ctx->staging = nullptr;
     ctx->staging_bytes = 0;
@@ -643,6 +648,51 @@ lbm_status lbm_reduce(lbm_ctx *ctx, double out[4]) {
     e = cudaMemcpyAsync(out, ctx->red_out, 4 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "reduce result copy");
+    return LBM_OK;
+}
+
+lbm_status lbm_step_reduce(lbm_ctx *ctx, int n, double *out) {
+    if (check_ctx(ctx)) return LBM_ERR_ARG;
+    if (n < 1 || !out) return fail(ctx, LBM_ERR_ARG, "n must be >= 1 and out is required");
+    cudaError_t e;
+    if (ctx->pattern == LBM_PATTERN_AA) {
+        // (the AA kernels have no fused form: the totals, then the steps)
+        Dev d = make_dev(ctx);
+        e = LBM_DISPATCH(ctx, reduce(d, state_lat(ctx), ctx->red_partials, ctx->red_out));
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "reduce launch");
+        lbm_status s = lbm_step(ctx, n);
+        if (s) return s;
+    } else {
+        Dev d = make_dev(ctx);
+        const size_t nb = (size_t)d.P.nxb * d.P.nyb * d.P.nzr;
+        if (ctx->step_partials_n < nb) {
+            if (ctx->step_partials) {
+                cudaStreamSynchronize(ctx->stream);
+                cudaFree(ctx->step_partials);
+            }
+            ctx->step_partials = nullptr;
+            ctx->step_partials_n = 0;
+            e = cudaMalloc((void **)&ctx->step_partials, nb * 4 * sizeof(double));
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                ctx->step_partials = nullptr;
+                return fail(ctx, LBM_ERR_OOM, "cannot allocate the fused-reduction partials");
+            }
+            ctx->step_partials_n = nb;
+        }
+        e = LBM_DISPATCH(ctx, step_reduce(d, ctx->lat[ctx->cur], ctx->lat[ctx->cur ^ 1], ctx->step_partials,
+                                          ctx->red_out));
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "fused step-reduce launch");
+        ctx->cur ^= 1;
+        ctx->steps_done++;
+        lbm_status s = lbm_step(ctx, n - 1);
+        if (s) return s;
+    }
+    const bool dev = is_device_ptr(out);
+    e = cudaMemcpyAsync(out, ctx->red_out, 4 * sizeof(double), dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                        ctx->stream);
+    if (e == cudaSuccess && !dev) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "totals copy");
     return LBM_OK;
 }
 

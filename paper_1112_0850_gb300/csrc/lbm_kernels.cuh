@@ -187,11 +187,13 @@ template <int S> struct SharedRows {
 
 // One fused step for the cell pair (x0, x0 + 1) of row (y, z): gather through
 // `rows` (the cell's own opposite populations, for bounce-back, from src),
-// collide, store to dst.
-template <int S, bool FLAGS, int FORCE, bool RECORD, class Rows>
+// collide, store to dst. RED: also add the pair's mass and momentum j + F/2
+// (of the pre-collision state, in FP64) to red[4]; the pair then never
+// returns early, so that its block can reduce.
+template <int S, bool FLAGS, int FORCE, bool RECORD, class Rows, bool RED = false>
 __device__ __forceinline__ void step_pair(const Dev &d, const Rows &rows, const typename Stor<S>::T *__restrict__ src,
                                           typename Stor<S>::T *__restrict__ dst, typename Stor<S>::R *__restrict__ tape,
-                                          int x0, int y, int z) {
+                                          int x0, int y, int z, double *red = nullptr) {
     typedef typename Stor<S>::T T;
     typedef typename Stor<S>::R R;
     typedef typename Pair2<R>::V V;  // lane x: cell x0, lane y: cell x0 + 1
@@ -208,7 +210,7 @@ __device__ __forceinline__ void step_pair(const Dev &d, const Rows &rows, const 
         m1 = mm.y;
         live0 = !(m0 & SOLID_BIT);
         live1 = has1 && !(m1 & SOLID_BIT);
-        if (!live0 && !live1) return;
+        if (!RED && !live0 && !live1) return;
     } else if (FLAGS) {
         const uchar2 fl = __ldg(reinterpret_cast<const uchar2 *>(d.flags + c));
         // (no early exit for two solid cells: branching on this load would put
@@ -292,6 +294,23 @@ __device__ __forceinline__ void step_pair(const Dev &d, const Rows &rows, const 
     const bool bad0 = live0 && !(m.rho.x > R(0) && m.rho.x < R(1e30));
     const bool bad1 = live1 && !(m.rho.y > R(0) && m.rho.y < R(1e30));
     if (bad0 || bad1) atomicOr(d.status, LBM_STATUS_DIVERGED);
+    if (RED) {
+        // momentum j + F/2: rho u, or u itself in the incompressible model
+        if (live0) {
+            const double mr = d.incomp ? 1.0 : (double)m.rho.x;
+            red[0] += (double)m.rho.x;
+            red[1] += mr * (double)m.ux.x;
+            red[2] += mr * (double)m.uy.x;
+            red[3] += mr * (double)m.uz.x;
+        }
+        if (live1) {
+            const double mr = d.incomp ? 1.0 : (double)m.rho.y;
+            red[0] += (double)m.rho.y;
+            red[1] += mr * (double)m.ux.y;
+            red[2] += mr * (double)m.uy.y;
+            red[3] += mr * (double)m.uz.y;
+        }
+    }
     if (RECORD) {
         const long long qs = g.qs;
         st2_real(tape + c, m.rho.x, m.rho.y);
@@ -355,6 +374,42 @@ __global__ void __launch_bounds__(256, StepBlocks<S>::value)
                    y, z))
         return;
     step_pair<S, FLAGS, FORCE, RECORD>(d, GlobalRows<S>{src}, src, dst, tape, x0, y, z);
+}
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// The step with the mass/momentum totals of its pre-collision state fused in
+// (the reduction of lbm_reduce without a pass of its own): every thread, in
+// the lattice or not, reaches the block reduction; partials[4 b + k] of block
+// b = blockIdx.y * gridDim.x + blockIdx.x, summed in a fixed order.
+template <int S, bool FLAGS, int FORCE>
+__global__ void __launch_bounds__(256, StepBlocks<S>::value)
+    k_step_reduce(const Dev d, const typename Stor<S>::T *__restrict__ src, typename Stor<S>::T *__restrict__ dst,
+                  double *__restrict__ partials) {
+    if (FLAGS && LinkBounce<S>::value) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    double red[4] = {0.0, 0.0, 0.0, 0.0};
+    int x0, y, z;
+    if (pair_cell(d.g, d.P, blockDim.x, blockDim.y, blockIdx.x, blockIdx.y, threadIdx.x, threadIdx.y, x0, y, z))
+        step_pair<S, FLAGS, FORCE, false, GlobalRows<S>, true>(d, GlobalRows<S>{src}, src, dst, nullptr, x0, y, z,
+                                                              red);
+    __shared__ double sm[8][4];  // blocks hold at most 256 threads, whole warps
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int nwarps = (blockDim.x * blockDim.y) >> 5;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const double v = warp_sum_d(red[k]);
+        if (lane == 0) sm[wid][k] = v;
+    }
+    __syncthreads();
+    if (tid < 4) {
+        double t = 0.0;
+        for (int w = 0; w < nwarps; ++w) t += sm[w][tid];
+        partials[4 * ((long long)blockIdx.y * gridDim.x + blockIdx.x) + tid] = t;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -847,6 +902,33 @@ cudaError_t Ops<S>::step(const Dev &d, const void *src, void *dst, void *tape) {
     cfg.numAttrs = 1;
     e = cudaLaunchKernelEx(&cfg, k_bounce<S>, d, static_cast<typename Stor<S>::T *>(dst));
     if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+template <int S>
+cudaError_t Ops<S>::step_reduce(const Dev &d, const void *src, void *dst, double *partials, double *out) {
+    typedef typename Stor<S>::T T;
+    if (d.flags && !d.mask) return cudaErrorInvalidValue;
+    const T *s = static_cast<const T *>(src);
+    T *t = static_cast<T *>(dst);
+    const dim3 grid = step_grid(d), block = step_block(d);
+    if (d.flags) {
+        if (d.Ffield) k_step_reduce<S, true, 2><<<grid, block, 0, d.stream>>>(d, s, t, partials);
+        else if (d.force_on) k_step_reduce<S, true, 1><<<grid, block, 0, d.stream>>>(d, s, t, partials);
+        else k_step_reduce<S, true, 0><<<grid, block, 0, d.stream>>>(d, s, t, partials);
+    } else {
+        if (d.Ffield) k_step_reduce<S, false, 2><<<grid, block, 0, d.stream>>>(d, s, t, partials);
+        else if (d.force_on) k_step_reduce<S, false, 1><<<grid, block, 0, d.stream>>>(d, s, t, partials);
+        else k_step_reduce<S, false, 0><<<grid, block, 0, d.stream>>>(d, s, t, partials);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (d.flags && LinkBounce<S>::value && d.link_max > 0) {
+        const int per_block = 256 * LINKS_PER_THREAD;
+        k_bounce<S><<<dim3((d.link_max + per_block - 1) / per_block, Q - 1), 256, 0, d.stream>>>(d, t);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    k_reduce_final<<<1, RED_THREADS, 0, d.stream>>>(partials, (int)(grid.x * grid.y), out);
     return cudaGetLastError();
 }
 

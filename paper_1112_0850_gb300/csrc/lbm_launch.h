@@ -73,6 +73,10 @@ template <int S> struct Ops {
     static cudaError_t macros(const Dev &d, const void *lat, void *rho, void *u);
     // partials: RED_BLOCKS * 4 doubles of scratch; out: 4 doubles (device).
     static cudaError_t reduce(const Dev &d, const void *lat, double *partials, double *out);
+    // One step (as step, no tape) that also sums the totals of reduce for its
+    // pre-collision state into out (4 doubles, device); partials: 4 doubles per
+    // block of the step grid.
+    static cudaError_t step_reduce(const Dev &d, const void *src, void *dst, double *partials, double *out);
     // lambda^T from dL/du, dL/drho at the current state; grad_F += explicit term.
     static cudaError_t adj_seed(const Dev &d, const void *lat, const void *dL_du,
                                 const void *dL_drho, void *lam, void *grad_F);

@@ -146,6 +146,18 @@ class Lattice:
         self._call("lbm_reduce", out)
         return np.array(out[:])
 
+    def step_reduce(self, n=1, out=None):
+        """Totals of the current state (as reduce()), then n steps, the totals
+        summed inside the first step. out: optional device float64 tensor [4]
+        (asynchronous); otherwise a host numpy array is returned."""
+        if out is not None:
+            assert out.is_cuda and out.dtype == torch.float64 and out.numel() >= 4
+            self._call("lbm_step_reduce", int(n), out.data_ptr())
+            return out
+        res = (ctypes.c_double * 4)()
+        self._call("lbm_step_reduce", int(n), res)
+        return np.array(res[:])
+
     def get_state(self, fmt=None, out=None):
         fmt = self.storage if fmt is None else _storage_code(fmt)
         if out is None:
