@@ -352,7 +352,11 @@ def main():
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     torch.cuda.set_device(local)
+    if world > 1 and rank != 0:
+        dist.barrier()  # rank 0 builds (if anything is out of date), the others then load
     build.build()
+    if world > 1 and rank == 0:
+        dist.barrier()
 
     def barrier():
         if world > 1:
