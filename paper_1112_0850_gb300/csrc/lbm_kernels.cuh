@@ -100,20 +100,26 @@ template <int S> __device__ __forceinline__ bool nan_marked(const Dev &d) {
 // populations with e_x = 0 (rest, +-y, +-z and the yz diagonals) move as one
 // aligned pair per load and every population is stored as one aligned pair;
 // populations with e_x = +-1 come from sources shifted by one cell and are
-// loaded per cell. Every pair with a fluid cell is stored whole, its solid
-// cell included, so 32-byte sectors are written complete; pairs of two solid
-// cells do nothing. Halfway bounce-back takes one of three
-// forms, chosen per storage format by measurement (Bounce<S>):
+// loaded per cell. Every pair is stored whole, a solid cell included, so
+// 32-byte sectors are written complete. Halfway bounce-back takes one of
+// these forms, chosen per storage format by measurement (Bounce<S>):
 //
 //  - load side (FP64): a 32-bit push mask per cell (bit j: x + e_j is solid)
 //    is loaded first; a population whose source x - e_i is solid (bit opp(i))
 //    loads the opposite population of the cell itself, so each value costs one
 //    load; threads whose two cells are solid skip everything.
-//  - NaN marks (FP32): every slot of a solid cell holds NaN (written at
-//    create, init and set_state, and stored by the step for solid cells). The
-//    gather loads all 19 values without looking at flags; a NaN marks a solid
-//    source, and only those lanes then load the opposite population of the
-//    cell itself. No dependent load in front of the gather, no extra kernel.
+//  - mask-guided reload (FP32): the push mask is loaded first but the gather
+//    does not wait for it (every load takes the neighbour's address); pairs
+//    with a bounce bit then reload their bounced populations from the cell's
+//    own opposite slots, over the gathered values, before the moments.
+//    Solid slots are never read. 37.5 against 34.0 GFLUPS for NaN marks on
+//    the channel, which test each value and take the moments twice.
+//  - NaN marks (kept as the measured alternative): every slot of a solid cell
+//    holds NaN (written at create, init and set_state, and stored by the step
+//    for solid cells). The gather loads all 19 values without looking at
+//    flags; a NaN marks a solid source, so a NaN rho finds the cells next to a
+//    solid, and only those lanes then load the opposite population of the
+//    cell itself and take their moments again.
 //  - separate kernel (16-bit storage), the paper's arrangement (Sec. 7: the
 //    non-fluid cells are treated in a separate kernel): a solid cell s keeps in
 //    slot i the value that its fluid neighbour s + e_i pulls next step (that
@@ -197,7 +203,8 @@ __device__ __forceinline__ void step_pair(const Dev &d, const Rows &rows, const 
     typedef typename Stor<S>::T T;
     typedef typename Stor<S>::R R;
     typedef typename Pair2<R>::V V;  // lane x: cell x0, lane y: cell x0 + 1
-    constexpr bool LINKS = Bounce<S>::mode != BB_LOAD;  // flag-free gather (links or NaN marks)
+    constexpr bool MFIX = Bounce<S>::mode == BB_MFIX;
+    constexpr bool LINKS = Bounce<S>::mode != BB_LOAD && !MFIX;  // flag-free gather (links or NaN marks)
     constexpr bool NANS = Bounce<S>::mode == BB_NANS;
     const Geom &g = d.g;
     const bool has1 = x0 + 1 < g.nx;
@@ -210,7 +217,7 @@ __device__ __forceinline__ void step_pair(const Dev &d, const Rows &rows, const 
         m1 = mm.y;
         live0 = !(m0 & SOLID_BIT);
         live1 = has1 && !(m1 & SOLID_BIT);
-        if (!RED && !live0 && !live1) return;
+        if (!MFIX && !RED && !live0 && !live1) return;
     } else if (FLAGS) {
         const uchar2 fl = __ldg(reinterpret_cast<const uchar2 *>(d.flags + c));
         // (no early exit for two solid cells: branching on this load would put
@@ -227,7 +234,7 @@ __device__ __forceinline__ void step_pair(const Dev &d, const Rows &rows, const 
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const T *Pi = rows.row(g, i, y, z);
-        if (FLAGS && !LINKS && i > 0) {
+        if (FLAGS && !LINKS && !MFIX && i > 0) {
             const T *Po = src + (long long)opp(i) * g.qs + c;  // own cell, opposite population
             const bool b0 = (m0 >> opp(i)) & 1u, b1 = (m1 >> opp(i)) & 1u;
             if (ex(i) == 0) {
@@ -246,6 +253,16 @@ __device__ __forceinline__ void step_pair(const Dev &d, const Rows &rows, const 
         } else {
             s[i].x = Rows::ld(Pi + (ex(i) > 0 ? xa : xb));
             s[i].y = Rows::ld(Pi + (ex(i) > 0 ? x0 : xc));
+        }
+    }
+    if (FLAGS && MFIX && ((m0 | m1) & 0x7fffeu)) {
+        // a pair next to a solid: its bounced populations come from the
+        // cell's own opposite slots, loaded over the gathered (unread) ones
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+            const T *Po = src + (long long)opp(i) * g.qs + c;
+            if ((m0 >> opp(i)) & 1u) s[i].x = Stor<S>::ld(Po);
+            if ((m1 >> opp(i)) & 1u) s[i].y = Stor<S>::ld(Po + 1);
         }
     }
     if (FLAGS && !LINKS && d.moving_on && ((m0 | m1) & MOVING_BIT)) {

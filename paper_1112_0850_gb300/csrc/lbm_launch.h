@@ -46,10 +46,12 @@ struct Dev {
 };
 
 // Bounce-back form per storage format (see k_step), the measured fastest on
-// the walled channel: FP64 load side, FP32 NaN marks, 16-bit link kernel.
-enum { BB_LOAD = 0, BB_LINKS = 1, BB_NANS = 2 };
+// the walled channel: FP64 load side, FP32 mask-guided reload, 16-bit link
+// kernel (BB_NANS, NaN marks with a rho-gated fix-up, is kept as the
+// measured alternative).
+enum { BB_LOAD = 0, BB_LINKS = 1, BB_NANS = 2, BB_MFIX = 3 };
 __host__ __device__ constexpr int bounce_mode(int s) {
-    return s == LBM_F64 ? BB_LOAD : (s == LBM_F32 ? BB_NANS : BB_LINKS);
+    return s == LBM_F64 ? BB_LOAD : (s == LBM_F32 ? BB_MFIX : BB_LINKS);
 }
 // The form in which a solid cell's slot holds the value bounced into it, so
 // the gather needs no flags (links).
