@@ -41,7 +41,7 @@ __device__ __forceinline__ void pair_live(const Dev &d, int c, bool has1, bool &
     }
 }
 
-template <class R, int FORCE>
+template <class R, int FORCE, bool TFORM>
 __device__ __forceinline__ void pair_force(const Dev &d, int c, typename Pair2<R>::V &Fx, typename Pair2<R>::V &Fy,
                                            typename Pair2<R>::V &Fz, Guo2<R> &G) {
     Fx = Fy = Fz = vsplat(R(0));
@@ -49,13 +49,13 @@ __device__ __forceinline__ void pair_force(const Dev &d, int c, typename Pair2<R
         Fx = vsplat(R(d.F[0]));
         Fy = vsplat(R(d.F[1]));
         Fz = vsplat(R(d.F[2]));
-        G = uniform_guo<R>(d);
+        G = uniform_guo<R, TFORM>(d);
     } else if (FORCE == 2) {
         const R *F = static_cast<const R *>(d.Ffield);
         ld2_real(F + c, Fx.x, Fx.y);
         ld2_real(F + d.g.qs + c, Fy.x, Fy.y);
         ld2_real(F + 2 * d.g.qs + c, Fz.x, Fz.y);
-        G = guo2<R>(R(d.omega), Fx, Fy, Fz);
+        G = guo2<R>(TFORM ? R(d.cs) : R(1) - R(0.5) * R(d.omega), Fx, Fy, Fz);
     }
 }
 
@@ -96,10 +96,10 @@ __global__ void __launch_bounds__(256, StepBlocks<S>::value)
     for (int i = 0; i < Q; ++i) Stor<S>::ld2(A + (long long)i * qs + c, s[i].x, s[i].y);
     V Fx, Fy, Fz;
     Guo2<R> G;
-    pair_force<R, FORCE>(d, c, Fx, Fy, Fz, G);
+    pair_force<R, FORCE, relax_about_t(S)>(d, c, Fx, Fy, Fz, G);
     const Mom2<R> m = moments2<R, FORCE != 0>(s, Fx, Fy, Fz, d.incomp);
     pair_check_record<R, RECORD>(d, c, live0, live1, m, tape);
-    collide2<R, FORCE != 0>(s, m, R(d.omega), Fx, Fy, Fz, G, d.incomp);
+    collide2<R, FORCE != 0, relax_about_t(S)>(s, m, R(d.omega), R(d.cs), Fx, Fy, Fz, G, d.incomp);
     // a solid lane writes its NaN back (its slots stay marked)
 #pragma unroll
     for (int i = 0; i < Q; ++i)
@@ -178,10 +178,10 @@ __global__ void __launch_bounds__(256, AaOddBlocks<S, FLAGS>::value)
     }
     V Fx, Fy, Fz;
     Guo2<R> G;
-    pair_force<R, FORCE>(d, c, Fx, Fy, Fz, G);
+    pair_force<R, FORCE, relax_about_t(S)>(d, c, Fx, Fy, Fz, G);
     const Mom2<R> m = moments2<R, FORCE != 0>(s, Fx, Fy, Fz, d.incomp);
     pair_check_record<R, RECORD>(d, c, live0, live1, m, tape);
-    collide2<R, FORCE != 0>(s, m, R(d.omega), Fx, Fy, Fz, G, d.incomp);
+    collide2<R, FORCE != 0, relax_about_t(S)>(s, m, R(d.omega), R(d.cs), Fx, Fy, Fz, G, d.incomp);
     // P_i(x) to slot i of x + e_i, or to slot opp(i) of x if x + e_i is solid
 #pragma unroll
     for (int i = 0; i < Q; ++i) {

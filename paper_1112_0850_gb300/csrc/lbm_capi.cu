@@ -103,6 +103,7 @@ Dev make_dev(const lbm_ctx *ctx) {
     d.F[2] = ctx->F[2];
     d.force_on = ctx->Ffield_d != nullptr || ctx->F[0] != 0.0 || ctx->F[1] != 0.0 || ctx->F[2] != 0.0;
     d.omega = 1.0 / ctx->tau;
+    d.cs = ctx->tau - 0.5;
     const double cF = 1.0 - 0.5 * d.omega;
     for (int p = 0; p < NPAIR; ++p) {
         const int i = pair_first(p);
@@ -111,6 +112,8 @@ Dev make_dev(const lbm_ctx *ctx) {
         d.gC[p] = 3.0 * cF * weight(i) * eF;
         d.gAf[p] = (float)d.gA[p];
         d.gCf[p] = (float)d.gC[p];
+        d.gAtf[p] = (float)(9.0 * d.cs * weight(i) * eF);
+        d.gCtf[p] = (float)(3.0 * d.cs * weight(i) * eF);
     }
     d.has_moving = ctx->has_moving;
     d.moving_on = ctx->has_moving && (ctx->u_wall[0] != 0.0 || ctx->u_wall[1] != 0.0 || ctx->u_wall[2] != 0.0);

@@ -389,6 +389,8 @@ template <class V> __device__ __forceinline__ V edot_first(int i, V vx, V vy, V 
 template <class R> struct Mom2 {
     typedef typename Pair2<R>::V V;
     V rho1, rho, ux, uy, uz;
+    V jx, jy, jz;  // j + F/2 (= rho u, or u itself in the incompressible model)
+    V inv;         // 1/rho (1 in the incompressible model): u = j' inv
 };
 
 // Moments of both cells: rho - 1 summed over opposite pairs first (the odd
@@ -416,21 +418,27 @@ __device__ __forceinline__ Mom2<R> moments2(const typename Pair2<R>::V s[Q], typ
     }
     m.rho1 = r;
     m.rho = vadd(vsplat(R(1)), r);
+    m.jx = jx;
+    m.jy = jy;
+    m.jz = jz;
     if (incomp) {
         m.ux = jx;
         m.uy = jy;
         m.uz = jz;
+        m.inv = vsplat(R(1));
         return m;
     }
     const V inv = vrcp(m.rho);
+    m.inv = inv;
     m.ux = vmul(jx, inv);
     m.uy = vmul(jy, inv);
     m.uz = vmul(jz, inv);
     return m;
 }
 
-// Guo source with c = 1 - omega/2: rest S_0 = -c u.F (3 w_0 = 1), and per
-// opposite pair p (direction i = pair_first(p)):
+// Guo source with c = 1 - omega/2 (or c' = c/omega = tau - 1/2 for the form of
+// collide2 that adds S/omega to the equilibrium): rest S_0 = -c u.F
+// (3 w_0 = 1), and per opposite pair p (direction i = pair_first(p)):
 //   even part  (e_i.u) A_p - 3 c w_p (u.F),   odd part  C_p,
 //   A_p = 9 c w_p (e_i.F),  C_p = 3 c w_p (e_i.F).
 // A and C depend only on F and tau: a uniform force passes them in precomputed.
@@ -440,10 +448,9 @@ template <class R> struct Guo2 {
 };
 
 template <class R>
-__device__ __forceinline__ Guo2<R> guo2(R omega, typename Pair2<R>::V Fx, typename Pair2<R>::V Fy,
+__device__ __forceinline__ Guo2<R> guo2(R cF, typename Pair2<R>::V Fx, typename Pair2<R>::V Fy,
                                         typename Pair2<R>::V Fz) {
     Guo2<R> t;
-    const R cF = R(1) - R(0.5) * omega;
 #pragma unroll
     for (int p = 0; p < NPAIR; ++p) {
         const int i = pair_first(p);
@@ -455,38 +462,68 @@ __device__ __forceinline__ Guo2<R> guo2(R omega, typename Pair2<R>::V Fx, typena
     return t;
 }
 
+// 3 w_i of the odd part of the equilibrium, P_i = 3 w_i (e_i . j'): 1/6 for
+// the axis pairs and 1/12 for the diagonal ones, rounded so that the momentum
+// they carry, (2 K_AXIS + 8 K_DIAG) j', is j' with no rounding (the nearest
+// 1/6 and 1/12 give j' (1 + 3e-8) in FP32). A relative bias of that size in
+// every cell's momentum, repeated every step of a slowly varying flow, adds
+// up linearly over the steps.
+template <class R> struct OddK;
+template <> struct OddK<float> {
+    static constexpr float AXIS = 0x1.555554p-3f, DIAG = 0x1.555556p-4f;
+};
+template <> struct OddK<double> {
+    static constexpr double AXIS = 0x1.5555555555554p-3, DIAG = 0x1.5555555555556p-4;
+};
+
 // BGK relaxation (Eq. 1) with the Qian equilibrium and the Guo source, both
-// cells of the pair, populations in shifted form. With e = e_i . u, weight w
-// and t = 9/2 e^2 - 3/2 u.u,
-//   s_i <- (1 - omega) s_i + E + P,   s_opp(i) <- (1 - omega) s_opp(i) + E - P,
-//   E = a + b t [+ e A],   P = 3 b e [+ C],
-//   a = omega w rho1 [- 3 w c u.F],   b = omega w rho,
-// i.e. omega times the even and odd parts of the shifted equilibrium plus the
-// even and odd parts of the source (bracketed terms only with a force).
-// Without a force E +- P = a + b (t +- 3 e). a and b are formed per weight
-// class, the diagonal ones (w = 1/36) by halving the axis ones (w = 1/18),
-// so only one class's factors are held at a time. The incompressible model
-// (He & Luo) has the reference density 1 in place of rho in b.
-template <class R, bool FORCE>
-__device__ __forceinline__ void collide2(typename Pair2<R>::V s[Q], const Mom2<R> &m, R omega,
+// cells of the pair, populations in shifted form. Per opposite pair
+// (i, opp(i)), with weight w, e = e_i . u and t = 9/2 e^2 - 3/2 u.u, both forms
+// below compute E and P, the even and odd parts of the equilibrium plus the
+// source, and differ in how the relaxation is rounded.
+//
+// TFORM (FP32 storage): s_i <- T_i + (1 - omega)(s_i - T_i) with
+// T_i = s_eq_i + S_i / omega, the same update as (1 - omega) s_i + omega s_eq_i
+// + S_i. Near tau = 1/2 the two terms of the latter are about twice the result
+// and of opposite sign; this form rounds terms of the size of s_i, so T's mass
+// and momentum carry over. With j' = j + F/2 (= rho u) and e = (e_i . j')/rho:
+//   T_i, T_opp(i) = E +- P,   E = a + b t [+ e A],   P = K (e_i . j') [+ C],
+//   a = w rho1 [- 3 w c' u.F],   b = w rho,   K = 3 w (OddK),
+// A, C and c' = tau - 1/2 those of the source over omega (guo2).
+//
+// Otherwise (FP64, 16-bit storage): s_i <- (1 - omega) s_i + E + P and
+// s_opp(i) <- (1 - omega) s_opp(i) + E - P, with omega folded in:
+//   E = a + b t [+ e A],   P = 3 b e [+ C],   a = omega w rho1 [- 3 w c u.F],
+//   b = omega w rho,   c = 1 - omega/2,
+// so without a force E +- P = a + b (t +- 3e).
+//
+// Bracketed terms only with a force. a and b are formed per weight class, the
+// diagonal ones (w = 1/36) by halving the axis ones (w = 1/18), so only one
+// class's factors are held at a time. The incompressible model (He & Luo)
+// has the reference density 1 in place of rho in b, and j' = u.
+template <class R, bool FORCE, bool TFORM>
+__device__ __forceinline__ void collide2(typename Pair2<R>::V s[Q], const Mom2<R> &m, R omega, R cs,
                                          typename Pair2<R>::V Fx, typename Pair2<R>::V Fy,
                                          typename Pair2<R>::V Fz, const Guo2<R> &G, bool incomp) {
     typedef typename Pair2<R>::V V;
     const V rho_e = incomp ? vsplat(R(1)) : m.rho;
     const V omc = vsplat(R(1) - omega);
     const V nusq15 = vmul(vsplat(R(-1.5)), vfma(m.uz, m.uz, vfma(m.uy, m.uy, vmul(m.ux, m.ux))));
-    const R cF = R(1) - R(0.5) * omega;
+    // the factors of the equilibrium: w, or omega w with omega folded in
+    const R k3 = TFORM ? R(1.0 / 3.0) : omega * R(1.0 / 3.0);
+    const R k18 = TFORM ? R(1.0 / 18.0) : omega * R(1.0 / 18.0);
+    const R cF = TFORM ? cs : R(1) - R(0.5) * omega;  // Guo factor (over omega for TFORM)
     V uF = vsplat(R(0));
     if (FORCE) uF = vfma(m.uz, Fz, vfma(m.uy, Fy, vmul(m.ux, Fx)));
     {  // rest population, w = 1/3 (3 w c = c)
-        V a0 = vmul(vsplat(omega * R(1.0 / 3.0)), m.rho1);
+        V a0 = vmul(vsplat(k3), m.rho1);
         if (FORCE) a0 = vfma(vsplat(-cF), uF, a0);
-        const V b0 = vmul(vsplat(omega * R(1.0 / 3.0)), rho_e);
-        s[0] = vfma(omc, s[0], vfma(b0, nusq15, a0));
+        const V T0 = vfma(vmul(vsplat(k3), rho_e), nusq15, a0);
+        s[0] = TFORM ? vfma(omc, vsub(s[0], T0), T0) : vfma(omc, s[0], T0);
     }
-    V a = vmul(vsplat(omega * R(1.0 / 18.0)), m.rho1);
+    V a = vmul(vsplat(k18), m.rho1);
     if (FORCE) a = vfma(vsplat(R(-1.0 / 6.0) * cF), uF, a);
-    V b = vmul(vsplat(omega * R(1.0 / 18.0)), rho_e);
+    V b = vmul(vsplat(k18), rho_e);
 #pragma unroll
     for (int p = 0; p < NPAIR; ++p) {
         const int i = pair_first(p), io = opp(i);
@@ -494,16 +531,34 @@ __device__ __forceinline__ void collide2(typename Pair2<R>::V s[Q], const Mom2<R
             a = vmul(vsplat(R(0.5)), a);
             b = vmul(vsplat(R(0.5)), b);
         }
-        const V e = edot_first(i, m.ux, m.uy, m.uz);
-        const V t = vfma(vsplat(R(4.5)), vmul(e, e), nusq15);
-        if (FORCE) {
-            const V E = vfma(e, G.A[p], vfma(b, t, a));
-            const V P = vfma(vmul(vsplat(R(3)), b), e, G.C[p]);
-            s[i] = vfma(omc, s[i], vadd(E, P));
-            s[io] = vfma(omc, s[io], vsub(E, P));
+        if (TFORM) {
+            const V ej = edot_first(i, m.jx, m.jy, m.jz);
+            const V e = vmul(ej, m.inv);
+            const V K = vsplat(p < 3 ? OddK<R>::AXIS : OddK<R>::DIAG);
+            const V t = vfma(vsplat(R(4.5)), vmul(e, e), nusq15);
+            V E = vfma(b, t, a);
+            V P;
+            if (FORCE) {
+                E = vfma(e, G.A[p], E);
+                P = vfma(K, ej, G.C[p]);
+            } else {
+                P = vmul(K, ej);
+            }
+            const V Ti = vadd(E, P), To = vsub(E, P);
+            s[i] = vfma(omc, vsub(s[i], Ti), Ti);
+            s[io] = vfma(omc, vsub(s[io], To), To);
         } else {
-            s[i] = vfma(omc, s[i], vfma(b, vfma(vsplat(R(3)), e, t), a));
-            s[io] = vfma(omc, s[io], vfma(b, vfma(vsplat(R(-3)), e, t), a));
+            const V e = edot_first(i, m.ux, m.uy, m.uz);
+            const V t = vfma(vsplat(R(4.5)), vmul(e, e), nusq15);
+            if (FORCE) {
+                const V E = vfma(e, G.A[p], vfma(b, t, a));
+                const V P = vfma(vmul(vsplat(R(3)), b), e, G.C[p]);
+                s[i] = vfma(omc, s[i], vadd(E, P));
+                s[io] = vfma(omc, s[io], vsub(E, P));
+            } else {
+                s[i] = vfma(omc, s[i], vfma(b, vfma(vsplat(R(3)), e, t), a));
+                s[io] = vfma(omc, s[io], vfma(b, vfma(vsplat(R(-3)), e, t), a));
+            }
         }
     }
 }

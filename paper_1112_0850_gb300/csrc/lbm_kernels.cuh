@@ -149,8 +149,10 @@ template <> __device__ __forceinline__ double quiet_nan<double>() {
     return __longlong_as_double(0x7fffffffffffffffLL);
 }
 
-template <class R> __device__ __forceinline__ Guo2<R> uniform_guo(const Dev &d);
-template <> __device__ __forceinline__ Guo2<float> uniform_guo<float>(const Dev &d) {
+// The precomputed Guo constants of a uniform force, with c = 1 - omega/2, or
+// over omega (c' = tau - 1/2) for the form of collide2 that relaxes about T.
+template <class R, bool TFORM> __device__ __forceinline__ Guo2<R> uniform_guo(const Dev &d);
+template <> __device__ __forceinline__ Guo2<float> uniform_guo<float, false>(const Dev &d) {
     Guo2<float> t;
 #pragma unroll
     for (int p = 0; p < NPAIR; ++p) {
@@ -159,7 +161,16 @@ template <> __device__ __forceinline__ Guo2<float> uniform_guo<float>(const Dev 
     }
     return t;
 }
-template <> __device__ __forceinline__ Guo2<double> uniform_guo<double>(const Dev &d) {
+template <> __device__ __forceinline__ Guo2<float> uniform_guo<float, true>(const Dev &d) {
+    Guo2<float> t;
+#pragma unroll
+    for (int p = 0; p < NPAIR; ++p) {
+        t.A[p] = vsplat(d.gAtf[p]);
+        t.C[p] = vsplat(d.gCtf[p]);
+    }
+    return t;
+}
+template <> __device__ __forceinline__ Guo2<double> uniform_guo<double, false>(const Dev &d) {
     Guo2<double> t;
 #pragma unroll
     for (int p = 0; p < NPAIR; ++p) {
@@ -279,13 +290,13 @@ __device__ __forceinline__ void step_pair(const Dev &d, const Rows &rows, const 
         Fx = vsplat(R(d.F[0]));
         Fy = vsplat(R(d.F[1]));
         Fz = vsplat(R(d.F[2]));
-        G = uniform_guo<R>(d);
+        G = uniform_guo<R, relax_about_t(S)>(d);
     } else if (FORCE == 2) {
         const R *F = static_cast<const R *>(d.Ffield);
         ld2_real(F + c, Fx.x, Fx.y);
         ld2_real(F + g.qs + c, Fy.x, Fy.y);
         ld2_real(F + 2 * g.qs + c, Fz.x, Fz.y);
-        G = guo2<R>(R(d.omega), Fx, Fy, Fz);
+        G = guo2<R>(relax_about_t(S) ? R(d.cs) : R(1) - R(0.5) * R(d.omega), Fx, Fy, Fz);
     }
     Mom2<R> m = moments2<R, FORCE != 0>(s, Fx, Fy, Fz, d.incomp);
     if (FLAGS && NANS && ((live0 && m.rho.x != m.rho.x) || (live1 && m.rho.y != m.rho.y))) {
@@ -335,7 +346,7 @@ __device__ __forceinline__ void step_pair(const Dev &d, const Rows &rows, const 
         st2_real(tape + 2 * qs + c, m.uy.x, m.uy.y);
         st2_real(tape + 3 * qs + c, m.uz.x, m.uz.y);
     }
-    collide2<R, FORCE != 0>(s, m, R(d.omega), Fx, Fy, Fz, G, d.incomp);
+    collide2<R, FORCE != 0, relax_about_t(S)>(s, m, R(d.omega), R(d.cs), Fx, Fy, Fz, G, d.incomp);
     // The pair is stored whole, a solid cell included, so 32-byte sectors are
     // written complete: a solid cell's values are never read (load side), it
     // stores the NaN that marks it (NaN marks), or its slots are link targets

@@ -25,8 +25,9 @@ struct Dev {
     const uint32_t *mask;  // padded [qs] push masks (SOLID_BIT, bounce bits), null iff flags is
     const void *Ffield;    // padded [3][qs] of R, or nullptr
     double F[3];           // uniform force (used when Ffield == nullptr)
-    double gA[9], gC[9];   // Guo constants of the uniform force per opposite pair (see collide)
+    double gA[9], gC[9];   // Guo constants of the uniform force per opposite pair (see guo2)
     float gAf[9], gCf[9];  // the same, rounded to float
+    float gAtf[9], gCtf[9];  // the same over omega, rounded to float (the FP32 form of collide2)
     bool has_moving;       // some cell is a moving wall (flag 2)
     bool moving_on;        // has_moving and the wall velocity is nonzero
     double wc[19];         // moving-wall term 6 w_i (e_i . u_w) added to a population bounced into direction i
@@ -36,6 +37,7 @@ struct Dev {
     int link_max;          // largest per-direction count
     bool force_on;         // Ffield != nullptr or F != 0
     double omega;          // 1 / tau
+    double cs;             // tau - 1/2: the Guo factor 1 - omega/2 over omega
     unsigned *status;      // device status word
     cudaStream_t stream;
     long long n_cells;     // nx * ny * nz
@@ -56,6 +58,13 @@ __host__ __device__ constexpr int bounce_mode(int s) {
 // The form in which a solid cell's slot holds the value bounced into it, so
 // the gather needs no flags (links).
 __host__ __device__ constexpr bool bounce_in_solid(int s) { return bounce_mode(s) == BB_LINKS; }
+
+// The collision's rounding form per storage format (collide2): FP32 relaxes
+// about T = s_eq + S/omega with the momentum-exact odd part, which keeps
+// rounding from biasing mass and momentum step after step; FP64 (bias at the
+// 1e-16 level, ALU-bound) and 16-bit storage (error set by the storage
+// rounding) keep the cheaper omega-scaled form.
+__host__ __device__ constexpr bool relax_about_t(int s) { return s == LBM_F32; }
 
 constexpr int RED_BLOCKS = 152 * 8;  // fixed grid of the reduction: deterministic order
 constexpr int RED_THREADS = 256;

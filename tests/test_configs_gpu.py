@@ -75,12 +75,15 @@ def test_taylor_green_512_storage_accuracy():
     for s, (du, dr, dm) in errs.items():
         print("taylor-green 512^3, 200 steps, %s vs FP64: rel u %.3e, max |drho| %.3e, mass drift %.3e" %
               (s, du, dr, dm))
-    # FP32 storage misses the 1e-5 target here (measured 1.5e-5): the flow is
-    # smooth and, at k = 2 pi / 512, viscous damping is ~1e-6 per step, so the
-    # rounding of neighbouring cells' deviations is coherent and accumulates
-    # about linearly, ~T ulp(s) over T = 200 steps. Held to 2e-5.
-    assert errs["f32"][0] <= 2e-5
+    # The flow is smooth and, at k = 2 pi / 512, viscous damping is ~1e-6 per
+    # step, so each cell meets nearly the same rounding every step and any bias
+    # of mass or momentum adds up linearly over the steps. The FP32 collision
+    # relaxes about T = s_eq + S/omega with a momentum-exact odd part, which
+    # keeps such biases out (measured 1.0e-6; 1.5e-5 with the omega-folded form).
+    assert errs["f32"][0] <= 1e-5
     assert errs["f16s"][0] <= 1e-3
+    # BF16 keeps 8 significant bits of deviations of ~3e-3: storing the initial
+    # state alone costs ~9e-4 of the velocity, and 200 steps give 2.6e-3.
     assert errs["bf16s"][0] <= 1e-2
 
 
