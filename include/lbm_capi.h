@@ -243,6 +243,39 @@ lbm_status lbm_get_state(lbm_ctx *ctx, void *dst, lbm_storage fmt);
  * Resets steps_done to 0. Round trip in the context's own format is exact. */
 lbm_status lbm_set_state(lbm_ctx *ctx, const void *src, lbm_storage fmt);
 
+/* z-slab halo exchange, the one exchange per step when a lattice is split
+ * along z into slabs (a domain decomposition over GPUs; Sec. 2's pull update
+ * makes each step read only the nearest planes). A slab is a context of its
+ * own whose planes 0 and nz - 1 are ghosts: copies of the neighbouring slabs'
+ * boundary planes, with the flags (and force field) of those planes passed to
+ * lbm_create. The interior plane 1 reads from ghost plane 0 only the five
+ * populations with e_z = +1, and plane nz - 2 reads from plane nz - 1 only
+ * the five with e_z = -1. Before each lbm_step(ctx, 1) of every slab:
+ *   lbm_halo_pack(slab k, 1, b)   then lbm_halo_unpack(slab k + 1, 0, b)
+ *   lbm_halo_pack(slab k, 0, b')  then lbm_halo_unpack(slab k - 1, 1, b')
+ * and the interior planes then evolve bit for bit as the same planes of the
+ * unsplit lattice. The readers (lbm_get_state, lbm_macros, lbm_reduce) gather
+ * each cell's populations from its pull sources, which for the boundary
+ * planes lie in the ghosts: exchange before reading a slab.
+ *
+ * lbm_halo_bytes: size of one packed buffer, 5 * ny * pitch elements of the
+ * storage type (0 for an invalid context).
+ * lbm_halo_pack: copies from the current state the five outgoing populations
+ * of an interior boundary plane, side 0: plane 1, e_z = -1; side 1: plane
+ * nz - 2, e_z = +1. Layout [5][ny][pitch], directions in increasing index
+ * order (lbm_lattice_table), padding columns included.
+ * lbm_halo_unpack: writes such a buffer into a ghost plane, side 0: plane 0
+ * (the e_z = +1 populations packed by the slab below), side 1: plane nz - 1
+ * (the e_z = -1 ones packed by the slab above), at fluid cells only: a solid
+ * ghost cell's slots hold the bounce-back values of this slab's own step.
+ * buf: host or device, owned by the caller (a host buffer is staged and the
+ * call synchronizes). Returns LBM_ERR_ARG for a null buffer, side not 0 or 1,
+ * or nz < 3; LBM_ERR_UNSUPPORTED with LBM_PATTERN_AA (its layout alternates
+ * between steps). Asynchronous on cuda_stream for device buffers. */
+size_t lbm_halo_bytes(const lbm_ctx *ctx);
+lbm_status lbm_halo_pack(lbm_ctx *ctx, int side, void *buf);
+lbm_status lbm_halo_unpack(lbm_ctx *ctx, int side, const void *buf);
+
 /* As lbm_step, and also record, for each of the n steps k, the moments the
  * adjoint needs: (rho, u_x, u_y, u_z) of the pre-collision state at step k,
  * u including the F/2 shift. tape: device array of n * tape_bytes_per_step
@@ -292,7 +325,7 @@ int lbm_lattice_table(int *e, double *w, int *opp);
  * row_align bytes (as in lbm_options; 0 = pairs only): walks every thread of each
  * launch configuration on the CPU and verifies that every address it forms
  * lies inside its buffer (two-grid and AA step kernels, reverse step,
- * per-cell kernels, reduction). Returns the number of violations (0 = all in
+ * per-cell kernels, reduction, halo copies). Returns the number of violations (0 = all in
  * bounds), or -1 for invalid sizes or alignment. Needs no GPU. */
 int64_t lbm_check_launch_indices(int nx, int ny, int nz, lbm_storage fmt, int row_align);
 

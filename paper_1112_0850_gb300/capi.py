@@ -62,6 +62,9 @@ PROTOTYPES = {
     "lbm_reduce_state_noalloc": (_st, [_vp, _i, _i, _i, _i, _vp, _vp, _vp, _vp]),
     "lbm_get_state": (_st, [_vp, _vp, _i]),
     "lbm_set_state": (_st, [_vp, _vp, _i]),
+    "lbm_halo_bytes": (ctypes.c_size_t, [_vp]),
+    "lbm_halo_pack": (_st, [_vp, _i, _vp]),
+    "lbm_halo_unpack": (_st, [_vp, _i, _vp]),
     "lbm_step_record": (_st, [_vp, _i, _vp]),
     "lbm_adjoint_seed": (_st, [_vp, _vp, _vp, _vp]),
     "lbm_adjoint_step": (_st, [_vp, _i, _vp, _vp]),

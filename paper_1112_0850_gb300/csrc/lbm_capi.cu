@@ -729,6 +729,36 @@ lbm_status lbm_set_state(lbm_ctx *ctx, const void *src, lbm_storage fmt) {
     return LBM_OK;
 }
 
+size_t lbm_halo_bytes(const lbm_ctx *ctx) {
+    if (check_ctx(ctx)) return 0;
+    return (size_t)5 * ctx->g.ny * ctx->g.pitch * storage_bytes(ctx->storage);
+}
+
+// Pack copies the boundary interior plane's outgoing populations (side 0:
+// plane 1, e_z = -1; side 1: plane nz - 2, e_z = +1); unpack writes the
+// incoming ones into the ghost plane (side 0: plane 0, e_z = +1; side 1:
+// plane nz - 1, e_z = -1) at fluid cells.
+static lbm_status halo_copy(lbm_ctx *ctx, int side, const void *buf, bool unpack) {
+    if (check_ctx(ctx)) return LBM_ERR_ARG;
+    if (!buf || (side != 0 && side != 1)) return fail(ctx, LBM_ERR_ARG, "bad halo buffer or side");
+    if (ctx->g.nz < 3) return fail(ctx, LBM_ERR_ARG, "a slab needs nz >= 3: two ghost planes and an interior");
+    if (ctx->pattern != LBM_PATTERN_PULL) return fail(ctx, LBM_ERR_UNSUPPORTED, "halo copies need the pull pattern");
+    Staged st(ctx);
+    const int k = st.add(buf, lbm_halo_bytes(ctx), !unpack);
+    lbm_status s = st.prepare();
+    if (s) return s;
+    const int z = unpack ? (side == 0 ? 0 : ctx->g.nz - 1) : (side == 0 ? 1 : ctx->g.nz - 2);
+    const int dir = (side == 1) != unpack ? 1 : -1;
+    cudaError_t e = launch_halo(ctx->g, state_lat(ctx), (int)storage_bytes(ctx->storage), st.dev(k), z, dir, unpack,
+                                ctx->flags_d, ctx->num_sms, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, unpack ? "halo unpack launch" : "halo pack launch");
+    return st.finish();
+}
+
+lbm_status lbm_halo_pack(lbm_ctx *ctx, int side, void *buf) { return halo_copy(ctx, side, buf, false); }
+
+lbm_status lbm_halo_unpack(lbm_ctx *ctx, int side, const void *buf) { return halo_copy(ctx, side, buf, true); }
+
 static lbm_status ensure_lambda(lbm_ctx *ctx) {
     // the reverse step gathers with the push masks (built at create; kept
     // here for a context whose masks are missing)
@@ -929,6 +959,26 @@ int64_t lbm_check_launch_indices(int nx, int ny, int nz, lbm_storage fmt, int ro
     if (visited2 != N) ++bad;
     if (P.bx_threads * P.by_threads > 256 || P.bx_threads % 32 || P.by_threads < 1) ++bad;
     if (L.bx_threads * L.by_threads != 256 || L.bx_threads % 32) ++bad;
+    // z-slab halo copies (lbm_halo.cu): the ghost and boundary planes, five
+    // directions each, buffer [5][ny][pitch]
+    if (nz >= 3) {
+        const long long plane = (long long)ny * g.pitch;
+        const int zs[4] = {0, 1, nz - 2, nz - 1};
+        for (int dir = -1; dir <= 1; dir += 2)
+            for (int zi = 0; zi < 4; ++zi) {
+                int k = 0;
+                for (int i = 0; i < Q; ++i) {
+                    if (ez(i) != dir) continue;
+                    for (long long r = 0; r < plane; ++r) {
+                        const long long at = (long long)i * g.qs + zs[zi] * plane + r;
+                        if (at < 0 || at >= (long long)Q * g.qs || zs[zi] * plane + r >= g.qs) ++bad;
+                        if (k * plane + r >= 5 * plane) ++bad;
+                    }
+                    ++k;
+                }
+                if (k != 5) ++bad;
+            }
+    }
     // reduction: canonical walk
     for (long long cc = 0; cc < N; ++cc) {
         const int x = (int)(cc % nx);

@@ -103,6 +103,10 @@ template <int S> struct AaOps {
 
 // Set-up: push masks of every padded cell from the padded flags (device).
 cudaError_t build_push_mask(const Geom &g, const uint8_t *flags, uint32_t *mask, cudaStream_t st);
+// z-slab halo copy between plane z of the lattice and a packed buffer of the
+// five populations with e_z = dir (lbm_halo.cu); unpack writes fluid cells only.
+cudaError_t launch_halo(const Geom &g, void *lat, int elem_bytes, void *buf, int z, int dir, bool unpack,
+                        const uint8_t *flags, int num_sms, cudaStream_t s);
 
 // Adjoint kernels that only depend on the arithmetic type R (double or float).
 template <class R> struct AdjOps {

@@ -169,6 +169,24 @@ class Lattice:
         fmt = {v: k for k, v in _FMT_DTYPE.items()}[state.dtype]
         self._call("lbm_set_state", self._ptr(state, state.dtype, (capi.Q,) + self.shape), fmt)
 
+    def new_halo(self):
+        """A device buffer for one packed halo: [5][ny][pitch] of the storage type."""
+        dt = _FMT_DTYPE[self.storage]
+        n = capi.lib().lbm_halo_bytes(self.handle) // torch.empty(0, dtype=dt).element_size()
+        return torch.empty(n, dtype=dt, device="cuda")
+
+    def halo_pack(self, side, buf):
+        """Outgoing populations of interior plane 1 (side 0) or nz - 2 (side 1)."""
+        assert buf.dtype == _FMT_DTYPE[self.storage] and buf.is_contiguous()
+        assert buf.numel() * buf.element_size() >= capi.lib().lbm_halo_bytes(self.handle)
+        self._call("lbm_halo_pack", int(side), buf.data_ptr())
+
+    def halo_unpack(self, side, buf):
+        """Incoming populations into ghost plane 0 (side 0) or nz - 1 (side 1), fluid cells."""
+        assert buf.dtype == _FMT_DTYPE[self.storage] and buf.is_contiguous()
+        assert buf.numel() * buf.element_size() >= capi.lib().lbm_halo_bytes(self.handle)
+        self._call("lbm_halo_unpack", int(side), buf.data_ptr())
+
     def new_tape(self, n):
         return torch.empty(int(n) * self.info.tape_bytes_per_step, dtype=torch.uint8, device="cuda")
 

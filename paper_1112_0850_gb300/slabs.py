@@ -1,0 +1,150 @@
+"""z-slab domain decomposition of a lattice: the method's one exchange per step.
+
+The pull update (Sec. 2) reads only nearest neighbours, so a lattice split
+along z into slabs needs, before each step, one plane from each neighbouring
+slab, and of that plane only the five populations that cross the face. Each
+slab is a lattice of its own whose first and last planes are ghosts; the
+library's halo calls (lbm_halo_pack / lbm_halo_unpack) move the crossing
+populations between a slab's boundary planes and packed buffers.
+
+- `split_planes`, `with_ghosts`: which planes each slab holds (host logic).
+- `SlabSet`: k slabs of one lattice on one device, exchanged through device
+  buffers; the interior planes evolve bit for bit as in the unsplit lattice.
+- `exchange_ranks`: the same exchange between processes, one slab per rank,
+  over torch.distributed point-to-point calls with bounded waits. It moves
+  whatever tensors it is given (packed halos, or whole planes).
+"""
+import datetime
+
+import numpy as np
+import torch
+
+
+def split_planes(nz, k):
+    """Interior planes [z0, z1) of k slabs covering planes 0 .. nz - 1, sizes
+    differing by at most one."""
+    if not 1 <= k <= nz:
+        raise ValueError("cannot split %d planes into %d slabs" % (nz, k))
+    b = [nz * i // k for i in range(k + 1)]
+    return [(b[i], b[i + 1]) for i in range(k)]
+
+
+def ghost_planes(nz, z0, z1):
+    """Global plane indices of a slab with its ghosts: z0 - 1, z0 .. z1 - 1, z1
+    (periodic in z)."""
+    return [(z0 - 1) % nz] + list(range(z0, z1)) + [z1 % nz]
+
+
+def with_ghosts(a, z0, z1, axis=-3):
+    """Planes z0 - 1 .. z1 of field `a` along `axis` (z of [..][nz][ny][nx]),
+    periodic; numpy array or torch tensor, returned contiguous."""
+    nz = a.shape[axis]
+    idx = ghost_planes(nz, z0, z1)
+    if torch.is_tensor(a):
+        return a.index_select(axis % a.dim(), torch.tensor(idx, device=a.device)).contiguous()
+    return np.ascontiguousarray(np.take(a, idx, axis=axis))
+
+
+class SlabSet:
+    """k z-slabs of an nx x ny x nz lattice on the current device.
+
+    Slab j is a `Lattice` of nz_j + 2 planes: the interior planes of
+    `split_planes(nz, k)[j]` between two ghost planes, created with the flags
+    of those planes. `step` exchanges the halos, then steps every slab once.
+    Keyword arguments go to `Lattice` (storage, model, ...; pull pattern)."""
+
+    def __init__(self, nx, ny, nz, tau, k, flags=None, force=None, **kw):
+        from .lattice import Lattice
+        self.shape = (nz, ny, nx)
+        self.bounds = split_planes(nz, k)
+        self.slabs = []
+        try:
+            for z0, z1 in self.bounds:
+                fl = None if flags is None else with_ghosts(np.asarray(flags, dtype=np.uint8), z0, z1)
+                self.slabs.append(Lattice(nx, ny, z1 - z0 + 2, tau, flags=fl, force=force, **kw))
+        except Exception:
+            self.close()
+            raise
+        self.up = [lat.new_halo() for lat in self.slabs]    # side-1 packs, for the slab above
+        self.down = [lat.new_halo() for lat in self.slabs]  # side-0 packs, for the slab below
+
+    def set_force_field(self, F):
+        """Per-cell force [3][nz][ny][nx] (device tensor of the arithmetic type)."""
+        for lat, (z0, z1) in zip(self.slabs, self.bounds):
+            lat.set_force_field(with_ghosts(F, z0, z1))
+
+    def set_wall_velocity(self, u_w):
+        for lat in self.slabs:
+            lat.set_wall_velocity(u_w)
+
+    def init_equilibrium(self, u0, rho0=None):
+        """u0 [3][nz][ny][nx], rho0 [nz][ny][nx] or None, as for `Lattice`."""
+        for lat, (z0, z1) in zip(self.slabs, self.bounds):
+            lat.init_equilibrium(with_ghosts(u0, z0, z1), None if rho0 is None else with_ghosts(rho0, z0, z1))
+
+    def exchange(self):
+        """Fill every ghost plane from the neighbouring slab (periodic in z)."""
+        k = len(self.slabs)
+        for j, lat in enumerate(self.slabs):
+            lat.halo_pack(1, self.up[j])
+            lat.halo_pack(0, self.down[j])
+        for j, lat in enumerate(self.slabs):
+            lat.halo_unpack(0, self.up[(j - 1) % k])
+            lat.halo_unpack(1, self.down[(j + 1) % k])
+
+    def step(self, n=1):
+        for _ in range(int(n)):
+            self.exchange()
+            for lat in self.slabs:
+                lat.step(1)
+
+    def get_state(self, fmt=None):
+        """The interior planes of all slabs joined: [19][nz][ny][nx]. The
+        state is read by gathering each cell's populations from its pull
+        sources, which for the boundary planes lie in the ghosts, so the
+        ghosts are refreshed first."""
+        self.exchange()
+        return torch.cat([lat.get_state(fmt)[:, 1:-1] for lat in self.slabs], dim=1)
+
+    def status_word(self, clear=False):
+        w = 0
+        for lat in self.slabs:
+            w |= lat.status_word(clear)
+        return w
+
+    def close(self):
+        for lat in self.slabs:
+            lat.close()
+        self.slabs = []
+
+
+# Status of `exchange_ranks`: done, or a wait that ran out or lost its peer.
+EXCHANGE_OK = 0
+EXCHANGE_FAILED = 1
+
+
+def exchange_ranks(send_down, send_up, recv_below, recv_above, timeout=datetime.timedelta(seconds=10), group=None):
+    """One step's halo exchange between ranks that each hold one slab, the
+    slabs in rank order and periodic: `send_up` goes to rank + 1 (its
+    `recv_below`), `send_down` to rank - 1 (its `recv_above`). Every wait is
+    bounded by `timeout`; a wait that runs out, or whose peer has gone, returns
+    (EXCHANGE_FAILED, which wait and why) instead of blocking, so that the
+    caller can stop before its next step. Returns (EXCHANGE_OK, "") otherwise."""
+    import torch.distributed as dist
+    r, n = dist.get_rank(group), dist.get_world_size(group)
+    if n == 1:
+        recv_below.copy_(send_up)
+        recv_above.copy_(send_down)
+        return EXCHANGE_OK, ""
+    lo, hi = (r - 1) % n, (r + 1) % n
+    # with two ranks lo == hi: the tag tells the two messages apart
+    works = [("receive from rank %d (below)" % lo, dist.irecv(recv_below, src=lo, group=group, tag=1)),
+             ("receive from rank %d (above)" % hi, dist.irecv(recv_above, src=hi, group=group, tag=2)),
+             ("send to rank %d (above)" % hi, dist.isend(send_up, dst=hi, group=group, tag=1)),
+             ("send to rank %d (below)" % lo, dist.isend(send_down, dst=lo, group=group, tag=2))]
+    for what, w in works:
+        try:
+            w.wait(timeout=timeout)
+        except RuntimeError as e:
+            return EXCHANGE_FAILED, "%s: %s" % (what, str(e).splitlines()[0][:200])
+    return EXCHANGE_OK, ""

@@ -1,0 +1,141 @@
+"""z-slab decomposition on the host: the plane bookkeeping of
+paper_1112_0850_gb300.slabs, and its rank-to-rank exchange run on gloo ranks
+on the CPU, each rank advancing one slab with the FP64 oracle. The oracle's
+state is pre-collision and a step pushes, so its slabs exchange whole planes
+(all 19 populations) before every step; after T steps the joined interiors
+must equal the unsplit oracle run bit for bit. A rank that stops sending makes
+its neighbour's exchange return EXCHANGE_FAILED within the bounded wait
+instead of blocking."""
+import datetime
+import os
+import socket
+import sys
+import time
+
+import numpy as np
+import pytest
+
+import lbm_inputs
+from paper_1112_0850_gb300 import slabs
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+NX, NY, NZ, TAU, T = 9, 7, 10, 0.58, 6
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def _problem():
+    flags = lbm_inputs.channel_flags(NX, NY, NZ, 0.15, 41)
+    rng = np.random.default_rng(41)
+    u0 = 0.03 * rng.standard_normal((3, NZ, NY, NX)) * (flags == 0)
+    rho0 = 1.0 + 0.02 * rng.standard_normal((NZ, NY, NX))
+    F = np.array([3e-5, 1e-5, -2e-5])
+    return flags, u0, rho0, F
+
+
+def test_split_planes_cover_and_balance():
+    for nz in (1, 2, 7, 10, 64):
+        for k in range(1, min(nz, 6) + 1):
+            b = slabs.split_planes(nz, k)
+            assert b[0][0] == 0 and b[-1][1] == nz
+            assert all(b[j][1] == b[j + 1][0] for j in range(k - 1))
+            sizes = [z1 - z0 for z0, z1 in b]
+            assert min(sizes) >= 1 and max(sizes) - min(sizes) <= 1
+    with pytest.raises(ValueError):
+        slabs.split_planes(3, 4)
+    with pytest.raises(ValueError):
+        slabs.split_planes(3, 0)
+
+
+def test_with_ghosts_wraps_periodically():
+    import torch
+    a = np.arange(2 * 5 * 3 * 4).reshape(2, 5, 3, 4)
+    g = slabs.with_ghosts(a, 0, 2)
+    assert g.shape == (2, 4, 3, 4)
+    assert np.array_equal(g[:, 0], a[:, 4]) and np.array_equal(g[:, 1:3], a[:, 0:2])
+    assert np.array_equal(g[:, 3], a[:, 2])
+    g = slabs.with_ghosts(a, 3, 5)
+    assert np.array_equal(g[:, 0], a[:, 2]) and np.array_equal(g[:, 3], a[:, 0])
+    t = slabs.with_ghosts(torch.from_numpy(a), 3, 5)
+    assert np.array_equal(t.numpy(), g) and t.is_contiguous()
+    f = np.arange(5 * 3 * 4).reshape(5, 3, 4)  # a scalar field: z is axis 0 = -3
+    assert np.array_equal(slabs.with_ghosts(f, 1, 4), f[[0, 1, 2, 3, 4]])
+    assert slabs.ghost_planes(5, 0, 5) == [4, 0, 1, 2, 3, 4, 0]
+
+
+def _rank_worker(rank, world, port, q, stop_at):
+    """One slab per rank: exchange whole planes, then one oracle step."""
+    import torch
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    import oracle
+    from paper_1112_0850_gb300 import slabs as sl
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=60))
+    flags, u0, rho0, F = _problem()
+    z0, z1 = sl.split_planes(NZ, world)[rank]
+    fl = sl.with_ghosts(flags, z0, z1)
+    f = oracle.init_equilibrium(sl.with_ghosts(u0, z0, z1), rho0=sl.with_ghosts(rho0, z0, z1), flags=fl)
+    plane = f[:, 0].shape
+    below, above = torch.zeros(plane, dtype=torch.float64), torch.zeros(plane, dtype=torch.float64)
+    status, msg, t_fail = sl.EXCHANGE_OK, "", 0.0
+    for step in range(T):
+        if rank == 1 and step == stop_at:
+            time.sleep(4.0)  # this rank stops sending (a dropped message), then leaves
+            break
+        t0 = time.time()
+        status, msg = sl.exchange_ranks(torch.from_numpy(np.ascontiguousarray(f[:, 1])),
+                                        torch.from_numpy(np.ascontiguousarray(f[:, -2])), below, above,
+                                        timeout=datetime.timedelta(seconds=1.5))
+        if status != sl.EXCHANGE_OK:
+            t_fail = time.time() - t0
+            break
+        f[:, 0] = below.numpy()
+        f[:, -1] = above.numpy()
+        f = oracle.run(f, TAU, 1, flags=fl, F=F, threads=1)
+    q.put((rank, status, msg, t_fail, f[:, 1:-1] if status == sl.EXCHANGE_OK else None))
+    q.close()
+    q.join_thread()  # flush the result before leaving
+    os._exit(0)  # no collective teardown: a failed rank's peer may be gone
+
+
+def _run_ranks(world, stop_at=-1):
+    import torch.multiprocessing as mp
+    import oracle
+    oracle.default()  # build once before the ranks start
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_worker, args=(r, world, port, q, stop_at)) for r in range(world)]
+    for p in procs:
+        p.start()
+    res = sorted((q.get(timeout=180) for _ in procs), key=lambda r: r[0])
+    for p in procs:
+        p.join(timeout=60)
+    return res
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_oracle_slabs_over_gloo_ranks_equal_unsplit(world):
+    import oracle
+    flags, u0, rho0, F = _problem()
+    ref = oracle.run(oracle.init_equilibrium(u0, rho0=rho0, flags=flags), TAU, T, flags=flags, F=F, threads=1)
+    res = _run_ranks(world)
+    assert all(r[1] == slabs.EXCHANGE_OK for r in res), [r[2] for r in res]
+    joined = np.concatenate([r[4] for r in res], axis=1)
+    assert joined.shape == ref.shape
+    assert np.array_equal(joined, ref)
+
+
+def test_rank_that_stops_sending_fails_the_exchange_in_bounded_time():
+    res = _run_ranks(2, stop_at=2)
+    r0 = res[0]
+    assert r0[1] == slabs.EXCHANGE_FAILED, r0[2]
+    assert "rank 1" in r0[2]
+    assert r0[3] < 10.0  # the 1.5 s bound, not the 60 s process-group timeout

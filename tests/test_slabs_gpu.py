@@ -1,0 +1,154 @@
+"""z-slab decomposition on one GPU: a lattice split into 1-4 slabs, each a
+context with two ghost planes, exchanging the five crossing populations per
+face through lbm_halo_pack / lbm_halo_unpack before every step. The interior
+planes must evolve bit for bit as in the unsplit lattice, for every storage
+format, with walls, obstacles, a uniform or per-cell force and moving walls
+(solid ghost cells keep their own bounce-back values)."""
+import numpy as np
+import pytest
+import torch
+
+import lbm_inputs
+from gpu_helpers import REAL, STORAGES, ensure_built
+
+pytestmark = pytest.mark.gpu
+
+
+def _fields(nx, ny, nz, seed, flags_kind):
+    rng = np.random.default_rng(seed)
+    shape = (nz, ny, nx)
+    u0 = 0.02 * rng.standard_normal((3,) + shape)
+    rho0 = 1.0 + 0.01 * rng.standard_normal(shape)
+    flags = None
+    if flags_kind == "channel":
+        flags = lbm_inputs.channel_flags(nx, ny, nz, 0.1, seed)
+    elif flags_kind == "random":
+        flags = lbm_inputs.random_flags(nx, ny, nz, 0.2, seed)
+    elif flags_kind == "moving":
+        flags = lbm_inputs.random_flags(nx, ny, nz, 0.15, seed)
+        flags[:, 0, :] = 1
+        flags[:, ny - 1, :] = 2
+        flags[3, :, :] = np.where(flags[3] == 0, 2, flags[3])  # a moving plane across z
+    if flags is not None:
+        u0 *= flags == 0
+    return u0, rho0, flags
+
+
+def _pair(storage, k, nx=21, ny=10, nz=14, flags_kind="channel", force="uniform", u_wall=None, steps=9, seed=5):
+    from paper_1112_0850_gb300.lattice import Lattice
+    from paper_1112_0850_gb300.slabs import SlabSet
+    ensure_built()
+    u0, rho0, flags = _fields(nx, ny, nz, seed, flags_kind)
+    real = REAL[storage]
+    F = (2e-5, -1e-5, 3e-5) if force == "uniform" else None
+    Ff = None
+    if force == "field":
+        Ff = torch.as_tensor(lbm_inputs.force_field((nz, ny, nx), 1e-4, seed + 1), dtype=real).cuda()
+    tau = 0.56
+    whole = Lattice(nx, ny, nz, tau, flags=flags, force=F, storage=storage)
+    slabs = SlabSet(nx, ny, nz, tau, k, flags=flags, force=F, storage=storage)
+    u0t, rho0t = torch.as_tensor(u0, dtype=real).cuda(), torch.as_tensor(rho0, dtype=real).cuda()
+    for lat in (whole, slabs):
+        if Ff is not None:
+            lat.set_force_field(Ff)
+        if u_wall is not None:
+            lat.set_wall_velocity(u_wall)
+        lat.init_equilibrium(u0t, rho0t)
+    whole.step(steps)
+    slabs.step(steps)
+    a, b = whole.get_state(), slabs.get_state()
+    sa, sb = whole.status_word(), slabs.status_word()
+    whole.close()
+    slabs.close()
+    return a, b, sa, sb
+
+
+@pytest.mark.parametrize("storage", STORAGES)
+@pytest.mark.parametrize("k", [1, 2, 3, 4])
+def test_slabs_equal_unsplit_channel(storage, k):
+    a, b, sa, sb = _pair(storage, k)
+    assert torch.equal(a, b), (storage, k)
+    assert sa == sb == 0
+
+
+@pytest.mark.parametrize("storage", STORAGES)
+def test_slabs_equal_unsplit_random_obstacles_force_field(storage):
+    a, b, _, _ = _pair(storage, 3, nx=17, ny=9, nz=11, flags_kind="random", force="field")
+    assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("storage", STORAGES)
+def test_slabs_equal_unsplit_periodic(storage):
+    # no flags: every ghost cell is fluid and takes the neighbour's values
+    a, b, _, _ = _pair(storage, 4, nx=16, ny=8, nz=12, flags_kind=None, force=None)
+    assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("storage", STORAGES)
+def test_slabs_equal_unsplit_moving_walls(storage):
+    a, b, _, _ = _pair(storage, 3, nx=19, ny=9, nz=12, flags_kind="moving", u_wall=(0.03, 0.0, -0.01))
+    assert torch.equal(a, b)
+
+
+def test_slab_of_one_interior_plane():
+    # six slabs of one interior plane each: both ghosts border the same plane
+    a, b, _, _ = _pair("f32", 6, nx=12, ny=7, nz=6)
+    assert torch.equal(a, b)
+
+
+def test_halo_pack_layout_and_host_buffer():
+    """The packed buffer holds the five crossing populations of the boundary
+    plane, [5][ny][pitch] in increasing direction order, and a host buffer
+    (staged by the library) receives the same bytes. The slot P_i(x) is what
+    cell x + e_i gathers, so where x and x + e_i are both fluid it equals the
+    state read at x + e_i."""
+    from paper_1112_0850_gb300.lattice import Lattice, lattice_table
+    ensure_built()
+    nx, ny, nz = 13, 6, 7
+    u0, rho0, flags = _fields(nx, ny, nz, 9, "random")
+    lat = Lattice(nx, ny, nz, 0.6, flags=flags, storage="f32")
+    lat.init_equilibrium(torch.as_tensor(u0, dtype=torch.float32).cuda(),
+                         torch.as_tensor(rho0, dtype=torch.float32).cuda())
+    lat.step(3)
+    state = lat.get_state()
+    fluid = torch.as_tensor(flags == 0, device="cuda")
+    e = np.asarray(lattice_table()[0])
+    pitch = lat.info.pitch
+    for side, z, ez in ((0, 1, -1), (1, nz - 2, 1)):
+        buf = lat.new_halo()
+        lat.halo_pack(side, buf)
+        host = torch.empty_like(buf, device="cpu")
+        lat.halo_pack(side, host)
+        assert torch.equal(buf.cpu(), host)
+        dirs = [i for i in range(19) if e[i][2] == ez]
+        assert len(dirs) == 5
+        got = buf.view(5, ny, pitch)[:, :, :nx]
+        for k, i in enumerate(dirs):
+            sh = (-int(e[i][1]), -int(e[i][0]))  # [y][x] -> value at (y + e_y, x + e_x)
+            want = torch.roll(state[i, z + ez], shifts=sh, dims=(0, 1))
+            m = fluid[z] & torch.roll(fluid[z + ez], shifts=sh, dims=(0, 1))
+            assert int(m.sum()) > 0
+            assert torch.equal(got[k][m], want[m]), (side, i)
+    lat.close()
+
+
+def test_halo_argument_errors():
+    from paper_1112_0850_gb300.capi import LBMError
+    from paper_1112_0850_gb300.lattice import Lattice
+    ensure_built()
+    lat = Lattice(8, 5, 6, 0.6, storage="f32")
+    buf = lat.new_halo()
+    assert buf.numel() == 5 * 5 * lat.info.pitch
+    with pytest.raises(LBMError):
+        lat.halo_pack(2, buf)
+    with pytest.raises(LBMError):
+        lat.halo_unpack(-1, buf)
+    lat.close()
+    thin = Lattice(8, 5, 2, 0.6, storage="f32")
+    with pytest.raises(LBMError):
+        thin.halo_pack(0, thin.new_halo())
+    thin.close()
+    aa = Lattice(8, 5, 6, 0.6, storage="f32", pattern="aa")
+    with pytest.raises(LBMError, match="UNSUPPORTED|pull"):
+        aa.halo_pack(0, aa.new_halo())
+    aa.close()
