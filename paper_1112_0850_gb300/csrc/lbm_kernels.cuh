@@ -389,10 +389,18 @@ __device__ __forceinline__ void step_pair(const Dev &d, const Rows &rows, const 
     }
 }
 
+// Launch the step kernel of the link form as a programmatic dependent of the
+// previous step's bounce kernel: its blocks are scheduled as the bounce
+// kernel drains, and wait for it before their first load.
+constexpr int STEP_PDL = 1;
+
 template <int S, bool FLAGS, int FORCE, bool RECORD>
 __global__ void __launch_bounds__(256, StepBlocks<S>::value)
     k_step(const Dev d, const typename Stor<S>::T *__restrict__ src, typename Stor<S>::T *__restrict__ dst,
            typename Stor<S>::R *__restrict__ tape) {
+    // launched after a bounce kernel whose links land in src: wait for it
+    // (a no-op when launched normally)
+    if (FLAGS && LinkBounce<S>::value && STEP_PDL) asm volatile("griddepcontrol.wait;" ::: "memory");
     // let the bounce kernel (a programmatic dependent) be scheduled once every
     // block of this grid is running; it still waits for this grid to complete
     // before it reads what this grid writes
@@ -591,6 +599,9 @@ __global__ void __launch_bounds__(256) k_bounce(const Dev d, typename Stor<S>::T
     // do not depend on it, the values below do. Wait here for the step's grid
     // to complete (a no-op when launched normally).
     asm volatile("griddepcontrol.wait;" ::: "memory");
+    // the next step kernel may be scheduled from here on: no earlier, so that
+    // it cannot start before the step this kernel waited for has completed
+    if (STEP_PDL) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 #pragma unroll
     for (int r = 0; r < LINKS_PER_THREAD; ++r)
         if (k0 + r * blockDim.x < n) v[r] = from[l[r].x];
@@ -849,6 +860,23 @@ template <int S, bool FLAGS, int FORCE>
 static cudaError_t launch_step3(const Dev &d, const void *src, void *dst, void *tape) {
     typedef typename Stor<S>::T T;
     typedef typename Stor<S>::R R;
+    if (FLAGS && LinkBounce<S>::value && STEP_PDL) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = step_grid(d);
+        cfg.blockDim = step_block(d);
+        cfg.stream = d.stream;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        cudaError_t e = tape ? cudaLaunchKernelEx(&cfg, k_step<S, FLAGS, FORCE, true>, d, static_cast<const T *>(src),
+                                                  static_cast<T *>(dst), static_cast<R *>(tape))
+                             : cudaLaunchKernelEx(&cfg, k_step<S, FLAGS, FORCE, false>, d,
+                                                  static_cast<const T *>(src), static_cast<T *>(dst), (R *)nullptr);
+        if (e != cudaSuccess) return e;
+        return cudaGetLastError();
+    }
     if (tape)
         k_step<S, FLAGS, FORCE, true><<<step_grid(d), step_block(d), 0, d.stream>>>(
             d, static_cast<const T *>(src), static_cast<T *>(dst), static_cast<R *>(tape));
