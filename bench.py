@@ -12,7 +12,8 @@ Prints one JSON line: value = million fluid-cell updates per second (MFLUPS,
 the paper's metric), the roofline of the step kernel against measured HBM
 bandwidth, the FP64 oracle timed on the host cores, an end-to-end figure
 through host buffers, the other storage formats and the adjoint/forward
-step-time ratio on the same workload.
+step-time ratio on the same workload, the 512^3 Taylor-Green box in every
+format and pattern, and the cost of a z-slab halo exchange on that box.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -471,6 +472,27 @@ def main():
             aa["channel_" + s] = {"mflups": n_fluid / t / 1e6, "gbs": gbs, "frac": gbs / peak}
             l2.close()
         extras["aa_pattern"] = aa
+        # ---- the 512^3 box as two z-slabs on this GPU: what the halo exchange costs ---------
+        from paper_1112_0850_gb300.slabs import SlabSet
+        sl = SlabSet(n, n, n, 0.52, 2, storage="f32")
+        sl.init_equilibrium(u_tg, rho_tg)
+        t_sl = time_steps(torch, sl, 10, 3) / 10  # an exchange, then a step of each slab
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for _ in range(3):
+            sl.exchange()
+        torch.cuda.synchronize()
+        ev0.record(sl.stream)
+        for _ in range(20):
+            sl.exchange()
+        ev1.record(sl.stream)
+        torch.cuda.synchronize()
+        t_ex = ev0.elapsed_time(ev1) / 1e3 / 20
+        face = 5 * n * n * 4  # five FP32 populations of one 512^2 plane
+        extras["z_slabs"] = {
+            "workload": "Taylor-Green 512^3 FP32 as 2 z-slabs of 256 planes plus 2 ghost planes each",
+            "mlups": n ** 3 / t_sl / 1e6, "exchange_us": t_ex * 1e6, "face_bytes": face,
+            "exchange_gbs": 16 * face / t_ex / 1e9, "exchange_share_of_step": t_ex / t_sl}
+        sl.close()
         del rho_tg, u_tg
         # ---- adjoint / forward step-time ratio (FP32, per-cell force gradient) -------------
         K = 50

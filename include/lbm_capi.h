@@ -60,7 +60,7 @@ typedef enum {
     LBM_ERR_STATE = 4,       /* call out of order (e.g. adjoint step before seed) */
     LBM_ERR_DIVERGED = 5,    /* a kernel saw a non-finite or non-positive density */
     LBM_ERR_INDEX = 6,       /* an index check failed (checked builds only) */
-    LBM_ERR_UNSUPPORTED = 7  /* combination not provided by this build */
+    LBM_ERR_UNSUPPORTED = 7  /* combination the library does not support */
 } lbm_status;
 
 /* Population storage formats. S = shifted: the stored value is f_i - w_i

@@ -65,6 +65,7 @@ class SlabSet:
         except Exception:
             self.close()
             raise
+        self.stream = self.slabs[0].stream
         self.up = [lat.new_halo() for lat in self.slabs]    # side-1 packs, for the slab above
         self.down = [lat.new_halo() for lat in self.slabs]  # side-0 packs, for the slab below
 
