@@ -223,7 +223,7 @@ __device__ __forceinline__ void step_pair(const Dev &d, const Rows &rows, const 
     uint32_t m0 = 0u, m1 = 0u;
     bool live0 = true, live1 = has1;
     if (FLAGS && !LINKS) {
-        const uint2 mm = __ldg(reinterpret_cast<const uint2 *>(d.mask + c));
+        const uint2 mm = ld_mask2(d.mask + c);
         m0 = mm.x;
         m1 = mm.y;
         live0 = !(m0 & SOLID_BIT);
@@ -372,7 +372,7 @@ __device__ __forceinline__ void step_pair(const Dev &d, const Rows &rows, const 
         // Links into a moving wall (not in the link list): slot opp(j) of the
         // wall cell x + e_j gets P_j(x) + 6 w_opp(j) (e_opp(j) . u_w), formed
         // from the unrounded P_j(x) so that it is rounded to storage once.
-        const uint2 mm = __ldg(reinterpret_cast<const uint2 *>(d.mask + c));
+        const uint2 mm = ld_mask2(d.mask + c);
         if ((mm.x | mm.y) & MOVING_BIT) {
 #pragma unroll
             for (int j = 1; j < Q; ++j) {
