@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(256, AaOddBlocks<S, FLAGS>::value)
     const int c = cell_index(g, x0, y, z);
     uint32_t m0 = 0u, m1 = has1 ? 0u : SOLID_BIT;
     if (FLAGS) {
-        const uint2 mm = ld_mask2(d.mask + c);
+        const uint2 mm = ld_resident2(d.mask + c);
         m0 = mm.x;
         m1 |= mm.y;
     }

@@ -163,11 +163,12 @@ template <> struct Stor<LBM_BF16S> {
     }
 };
 
-// The push masks of a cell pair (4 B a cell, read once a step by every kernel
-// that bounces on the load side), loaded with an L2 evict-last policy: while
-// the lattices stream through L2 every step, the masks stay resident, so the
-// loads that bounce-back waits on hit L2 (measured +2% on the walled channel).
-__device__ __forceinline__ uint2 ld_mask2(const uint32_t *p) {
+// Two 32-bit words of a small array read every step (the push masks of a
+// cell pair, 4 B a cell; a bounce-back link), loaded with an L2 evict-last
+// policy: while the lattices stream through L2 every step, these arrays stay
+// resident, so the loads that bounce-back waits on hit L2 (measured +2% on the
+// walled channel in FP32, +1% in 16-bit storage).
+__device__ __forceinline__ uint2 ld_resident2(const uint32_t *p) {
     unsigned long long pol;
     uint2 m;
     asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));

@@ -223,7 +223,7 @@ __device__ __forceinline__ void step_pair(const Dev &d, const Rows &rows, const 
     uint32_t m0 = 0u, m1 = 0u;
     bool live0 = true, live1 = has1;
     if (FLAGS && !LINKS) {
-        const uint2 mm = ld_mask2(d.mask + c);
+        const uint2 mm = ld_resident2(d.mask + c);
         m0 = mm.x;
         m1 = mm.y;
         live0 = !(m0 & SOLID_BIT);
@@ -372,7 +372,7 @@ __device__ __forceinline__ void step_pair(const Dev &d, const Rows &rows, const 
         // Links into a moving wall (not in the link list): slot opp(j) of the
         // wall cell x + e_j gets P_j(x) + 6 w_opp(j) (e_opp(j) . u_w), formed
         // from the unrounded P_j(x) so that it is rounded to storage once.
-        const uint2 mm = ld_mask2(d.mask + c);
+        const uint2 mm = ld_resident2(d.mask + c);
         if ((mm.x | mm.y) & MOVING_BIT) {
 #pragma unroll
             for (int j = 1; j < Q; ++j) {
@@ -593,7 +593,7 @@ __global__ void __launch_bounds__(256) k_bounce(const Dev d, typename Stor<S>::T
 #pragma unroll
     for (int r = 0; r < LINKS_PER_THREAD; ++r) {
         const int k = k0 + r * blockDim.x;
-        l[r] = k < n ? __ldg(L + k) : make_uint2(0u, 0u);  // (fluid cell, solid cell)
+        l[r] = k < n ? ld_resident2(reinterpret_cast<const uint32_t *>(L + k)) : make_uint2(0u, 0u);  // (fluid, solid)
     }
     // Launched as a programmatic dependent of the step kernel: the links above
     // do not depend on it, the values below do. Wait here for the step's grid
