@@ -95,6 +95,8 @@ Dev make_dev(const lbm_ctx *ctx) {
     d.g = ctx->g;
     d.L = ctx->L;
     d.P = pair_launch(ctx->g, ctx->box[0], ctx->box[1], ctx->box[2], ctx->box[3]);
+    d.PF = flat_launch(d.P);
+    d.flat_step = rows_leave_lanes_idle(d.P);
     d.flags = ctx->flags_d;
     d.mask = ctx->mask_d;
     d.Ffield = ctx->Ffield_d;
@@ -924,7 +926,8 @@ int64_t lbm_check_launch_indices(int nx, int ny, int nz, lbm_storage fmt, int ro
     // paired launch of the step kernels: every address k_step forms, which
     // covers the AA kernels too (the odd step loads at the pull sources and
     // stores at the reverse step's rows and columns; both touch the pair at c)
-    const RowLaunch P = pair_launch(g);
+    const RowLaunch Prows = pair_launch(g);
+    auto walk_pairs = [&](const RowLaunch &P, bool flat) {
     long long visited2 = 0;
     auto in_row = [&](int rowbase, int x) { return x >= 0 && x < g.pitch && rowbase + x < g.qs && rowbase >= 0; };
     for (int bz = 0; bz < nz; ++bz)
@@ -932,7 +935,8 @@ int64_t lbm_check_launch_indices(int nx, int ny, int nz, lbm_storage fmt, int ro
             for (int ty = 0; ty < P.by_threads; ++ty)
                 for (int tx = 0; tx < P.bx_threads; ++tx) {
                     int x0, y, z;
-                    if (!pair_cell(g, P, P.bx_threads, P.by_threads, bx, bz, tx, ty, x0, y, z)) continue;
+                    if (!(flat ? pair_cell<true>(g, P, P.bx_threads, P.by_threads, bx, bz, tx, ty, x0, y, z)
+                             : pair_cell<false>(g, P, P.bx_threads, P.by_threads, bx, bz, tx, ty, x0, y, z))) continue;
                     const bool has1 = x0 + 1 < nx;
                     visited2 += has1 ? 2 : 1;
                     const int c = cell_index(g, x0, y, z);
@@ -957,6 +961,10 @@ int64_t lbm_check_launch_indices(int nx, int ny, int nz, lbm_storage fmt, int ro
                     }
                 }
     if (visited2 != N) ++bad;
+    };
+    walk_pairs(Prows, false);
+    walk_pairs(flat_launch(Prows), true);  // the two-grid step's launch when rows leave lanes idle
+    const RowLaunch &P = Prows;
     if (P.bx_threads * P.by_threads > 256 || P.bx_threads % 32 || P.by_threads < 1) ++bad;
     if (L.bx_threads * L.by_threads != 256 || L.bx_threads % 32) ++bad;
     // z-slab halo copies (lbm_halo.cu): the ghost and boundary planes, five

@@ -216,6 +216,7 @@ struct RowLaunch {
     int bx_threads, by_threads;  // block shape
     int nxb, nyb;                // x blocks per row, y groups
     int y0, z0, nyr, nzr;        // paired launch: the rows y0 .. y0 + nyr - 1 of planes z0 .. z0 + nzr - 1
+    int W;                       // flat paired launch: pairs per row
 };
 
 inline RowLaunch row_launch(const Geom &g) {
@@ -229,6 +230,7 @@ inline RowLaunch row_launch(const Geom &g) {
     L.y0 = L.z0 = 0;
     L.nyr = g.ny;
     L.nzr = g.nz;
+    L.W = 0;
     return L;
 }
 
@@ -253,11 +255,36 @@ inline RowLaunch pair_launch(const Geom &g, int y0 = 0, int nyr = -1, int z0 = 0
     L.nyr = nyr < 0 ? g.ny : nyr;
     L.nzr = nzr < 0 ? g.nz : nzr;
     L.nyb = (L.nyr + L.by_threads - 1) / L.by_threads;
+    L.W = (g.nx + 1) / 2;
     return L;
 }
 
+// Whole rows per block leave the last warp of a row partly idle when the row's
+// pairs are not a multiple of 32 (n = 200: 28 of 128 threads). The flat launch
+// gives consecutive threads consecutive pairs of a plane's rows, across row
+// ends (with rows padded only to pairs, consecutive rows are adjacent in
+// memory, so such warps still load contiguous runs): blocks of 256 x 1.
+inline bool rows_leave_lanes_idle(const RowLaunch &P) { return P.nxb * P.bx_threads != P.W; }
+inline RowLaunch flat_launch(const RowLaunch &rows) {
+    RowLaunch L = rows;
+    L.nxb = 1;
+    L.bx_threads = 256;
+    L.by_threads = 1;
+    L.nyb = (int)(((long long)L.nyr * L.W + 255) / 256);
+    return L;
+}
+
+template <bool FLAT = false>
 LBM_HD bool pair_cell(const Geom &g, const RowLaunch &P, int bdx, int bdy, int bx, int bz, int tx, int ty, int &x0,
                       int &y, int &z) {
+    if (FLAT) {  // thread k of the plane takes pair k of the box rows
+        const int k = bx * (bdx * bdy) + ty * bdx + tx;
+        const int r = k / P.W;
+        x0 = 2 * (k - r * P.W);
+        y = P.y0 + r;
+        z = P.z0 + bz;
+        return r < P.nyr && z < P.z0 + P.nzr;
+    }
     const int xb = bx % P.nxb;
     const int yg = bx / P.nxb;
     x0 = 2 * (xb * bdx + tx);

@@ -394,7 +394,8 @@ __device__ __forceinline__ void step_pair(const Dev &d, const Rows &rows, const 
 // kernel drains, and wait for it before their first load.
 constexpr int STEP_PDL = 1;
 
-template <int S, bool FLAGS, int FORCE, bool RECORD>
+// FLAT: the launch of d.PF (pairs in plane order), else of d.P (whole rows).
+template <int S, bool FLAGS, int FORCE, bool RECORD, bool FLAT = false>
 __global__ void __launch_bounds__(256, StepBlocks<S>::value)
     k_step(const Dev d, const typename Stor<S>::T *__restrict__ src, typename Stor<S>::T *__restrict__ dst,
            typename Stor<S>::R *__restrict__ tape) {
@@ -406,8 +407,8 @@ __global__ void __launch_bounds__(256, StepBlocks<S>::value)
     // before it reads what this grid writes
     if (FLAGS && LinkBounce<S>::value) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     int x0, y, z;
-    if (!pair_cell(d.g, d.P, blockDim.x, blockDim.y, blockIdx.x, blockIdx.y, threadIdx.x, threadIdx.y, x0,
-                   y, z))
+    if (!pair_cell<FLAT>(d.g, FLAT ? d.PF : d.P, blockDim.x, blockDim.y, blockIdx.x, blockIdx.y, threadIdx.x,
+                         threadIdx.y, x0, y, z))
         return;
     step_pair<S, FLAGS, FORCE, RECORD>(d, GlobalRows<S>{src}, src, dst, tape, x0, y, z);
 }
@@ -856,34 +857,52 @@ inline dim3 row_block(const Dev &d) { return dim3(d.L.bx_threads, d.L.by_threads
 inline dim3 step_grid(const Dev &d) { return dim3(d.P.nxb * d.P.nyb, d.P.nzr); }
 inline dim3 step_block(const Dev &d) { return dim3(d.P.bx_threads, d.P.by_threads); }
 
-template <int S, bool FLAGS, int FORCE>
-static cudaError_t launch_step3(const Dev &d, const void *src, void *dst, void *tape) {
+template <int S, bool FLAGS, int FORCE, bool FLAT>
+static cudaError_t launch_step3f(const Dev &d, const void *src, void *dst, void *tape) {
     typedef typename Stor<S>::T T;
     typedef typename Stor<S>::R R;
+    const RowLaunch &P = FLAT ? d.PF : d.P;
+    const dim3 grid(P.nxb * P.nyb, P.nzr), block(P.bx_threads, P.by_threads);
     if (FLAGS && LinkBounce<S>::value && STEP_PDL) {
         cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = step_grid(d);
-        cfg.blockDim = step_block(d);
+        cfg.gridDim = grid;
+        cfg.blockDim = block;
         cfg.stream = d.stream;
         cudaLaunchAttribute attr[1];
         attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
         attr[0].val.programmaticStreamSerializationAllowed = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        cudaError_t e = tape ? cudaLaunchKernelEx(&cfg, k_step<S, FLAGS, FORCE, true>, d, static_cast<const T *>(src),
-                                                  static_cast<T *>(dst), static_cast<R *>(tape))
-                             : cudaLaunchKernelEx(&cfg, k_step<S, FLAGS, FORCE, false>, d,
+        cudaError_t e = tape ? cudaLaunchKernelEx(&cfg, k_step<S, FLAGS, FORCE, true, FLAT>, d,
+                                                  static_cast<const T *>(src), static_cast<T *>(dst),
+                                                  static_cast<R *>(tape))
+                             : cudaLaunchKernelEx(&cfg, k_step<S, FLAGS, FORCE, false, FLAT>, d,
                                                   static_cast<const T *>(src), static_cast<T *>(dst), (R *)nullptr);
         if (e != cudaSuccess) return e;
         return cudaGetLastError();
     }
     if (tape)
-        k_step<S, FLAGS, FORCE, true><<<step_grid(d), step_block(d), 0, d.stream>>>(
+        k_step<S, FLAGS, FORCE, true, FLAT><<<grid, block, 0, d.stream>>>(
             d, static_cast<const T *>(src), static_cast<T *>(dst), static_cast<R *>(tape));
     else
-        k_step<S, FLAGS, FORCE, false><<<step_grid(d), step_block(d), 0, d.stream>>>(
+        k_step<S, FLAGS, FORCE, false, FLAT><<<grid, block, 0, d.stream>>>(
             d, static_cast<const T *>(src), static_cast<T *>(dst), nullptr);
     return cudaGetLastError();
+}
+
+// The flat launch where whole rows would leave lanes idle, and also where it
+// measured faster with whole-warp rows (its index code compiles to fewer
+// spills): FP32 (walled channel +1%) and 16-bit storage without flags (512^3
+// box +3%). The 16-bit link form with flags keeps whole rows there (the flat
+// form spilled more: -4.5%); so does FP64.
+template <int S, bool FLAGS> constexpr bool flat_preferred() {
+    return S == LBM_F32 || (S != LBM_F64 && !FLAGS);
+}
+
+template <int S, bool FLAGS, int FORCE>
+static cudaError_t launch_step3(const Dev &d, const void *src, void *dst, void *tape) {
+    return d.flat_step || flat_preferred<S, FLAGS>() ? launch_step3f<S, FLAGS, FORCE, true>(d, src, dst, tape)
+                                                     : launch_step3f<S, FLAGS, FORCE, false>(d, src, dst, tape);
 }
 
 // Shared memory of the row-staged step: two buffers of 19 padded rows.

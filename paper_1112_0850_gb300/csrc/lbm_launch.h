@@ -21,6 +21,8 @@ struct Dev {
     Geom g;
     RowLaunch L;           // one cell per thread
     RowLaunch P;           // two x-adjacent cells per thread (step kernels)
+    RowLaunch PF;          // the same pairs in plane order (flat_launch), for the two-grid step
+    bool flat_step;        // the two-grid step uses PF: whole rows would leave lanes idle
     const uint8_t *flags;  // padded [qs] (1 = solid, also on padding), or nullptr = all fluid
     const uint32_t *mask;  // padded [qs] push masks (SOLID_BIT, bounce bits), null iff flags is
     const void *Ffield;    // padded [3][qs] of R, or nullptr
