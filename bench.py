@@ -57,8 +57,18 @@ def measured_peaks():
 
 
 def kernel_source_hash():
+    """Hash of the sources the two-grid step kernels and their launch
+    configuration are built from: the device, launch and kernel headers, the
+    per-format kernel units, the context setup (launch shape, masks, links)
+    and the C header. The AA, reverse-step, halo and allocation-free units do
+    not enter the step kernels and are left out."""
+    csrc = os.path.join(ROOT, "paper_1112_0850_gb300", "csrc")
+    files = [os.path.join(csrc, n) for n in ("lbm_device.cuh", "lbm_launch.h", "lbm_kernels.cuh", "lbm_capi.cu",
+                                              "lbm_setup.cu")]
+    files += sorted(glob.glob(os.path.join(csrc, "lbm_ops_*.cu")))
+    files.append(os.path.join(ROOT, "include", "lbm_capi.h"))
     h = hashlib.sha256()
-    for p in sorted(glob.glob(os.path.join(ROOT, "paper_1112_0850_gb300", "csrc", "*"))):
+    for p in files:
         with open(p, "rb") as f:
             h.update(os.path.basename(p).encode())
             h.update(f.read())

@@ -75,14 +75,15 @@ __device__ __forceinline__ void pair_check_record(const Dev &d, int c, bool live
 }
 
 // Even step (natural -> swapped): local, every access an aligned pair.
-template <int S, bool FLAGS, int FORCE, bool RECORD>
+// FLAT (both AA kernels): the launch of d.PF (pairs in plane order), else of d.P.
+template <int S, bool FLAGS, int FORCE, bool RECORD, bool FLAT>
 __global__ void __launch_bounds__(256, StepBlocks<S>::value)
     k_aa_even(const Dev d, typename Stor<S>::T *__restrict__ A, typename Stor<S>::R *__restrict__ tape) {
     typedef typename Stor<S>::R R;
     typedef typename Pair2<R>::V V;
     int x0, y, z;
-    if (!pair_cell(d.g, d.P, blockDim.x, blockDim.y, blockIdx.x, blockIdx.y, threadIdx.x, threadIdx.y, x0,
-                   y, z))
+    if (!pair_cell<FLAT>(d.g, FLAT ? d.PF : d.P, blockDim.x, blockDim.y, blockIdx.x, blockIdx.y, threadIdx.x,
+                         threadIdx.y, x0, y, z))
         return;
     const long long qs = d.g.qs;
     const int c = cell_index(d.g, x0, y, z);
@@ -121,15 +122,15 @@ template <int S, bool FLAGS> struct AaOddBlocks {
 // address is a select, so the whole step is one branch-free sequence (a
 // NaN-driven fix-up with separate store paths measured twice as slow here:
 // its code size and divergence made it instruction-bound).
-template <int S, bool FLAGS, int FORCE, bool RECORD>
+template <int S, bool FLAGS, int FORCE, bool RECORD, bool FLAT>
 __global__ void __launch_bounds__(256, AaOddBlocks<S, FLAGS>::value)
     k_aa_odd(const Dev d, typename Stor<S>::T *__restrict__ A, typename Stor<S>::R *__restrict__ tape) {
     typedef typename Stor<S>::T T;
     typedef typename Stor<S>::R R;
     typedef typename Pair2<R>::V V;
     int x0, y, z;
-    if (!pair_cell(d.g, d.P, blockDim.x, blockDim.y, blockIdx.x, blockIdx.y, threadIdx.x, threadIdx.y, x0,
-                   y, z))
+    if (!pair_cell<FLAT>(d.g, FLAT ? d.PF : d.P, blockDim.x, blockDim.y, blockIdx.x, blockIdx.y, threadIdx.x,
+                         threadIdx.y, x0, y, z))
         return;
     const Geom &g = d.g;
     const long long qs = g.qs;
@@ -211,24 +212,34 @@ __global__ void __launch_bounds__(256, AaOddBlocks<S, FLAGS>::value)
     }
 }
 
-template <int S, bool FLAGS, int FORCE>
-static cudaError_t launch_aa3(const Dev &d, void *A, int odd, void *tape) {
+template <int S, bool FLAGS, int FORCE, bool FLAT>
+static cudaError_t launch_aa4(const Dev &d, void *A, int odd, void *tape) {
     typedef typename Stor<S>::T T;
     typedef typename Stor<S>::R R;
     T *a = static_cast<T *>(A);
     R *t = static_cast<R *>(tape);
+    const RowLaunch &P = FLAT ? d.PF : d.P;
+    const dim3 grid(P.nxb * P.nyb, P.nzr), block(P.bx_threads, P.by_threads);
     if (odd) {
         if (tape)
-            k_aa_odd<S, FLAGS, FORCE, true><<<step_grid(d), step_block(d), 0, d.stream>>>(d, a, t);
+            k_aa_odd<S, FLAGS, FORCE, true, FLAT><<<grid, block, 0, d.stream>>>(d, a, t);
         else
-            k_aa_odd<S, FLAGS, FORCE, false><<<step_grid(d), step_block(d), 0, d.stream>>>(d, a, nullptr);
+            k_aa_odd<S, FLAGS, FORCE, false, FLAT><<<grid, block, 0, d.stream>>>(d, a, nullptr);
     } else {
         if (tape)
-            k_aa_even<S, FLAGS, FORCE, true><<<step_grid(d), step_block(d), 0, d.stream>>>(d, a, t);
+            k_aa_even<S, FLAGS, FORCE, true, FLAT><<<grid, block, 0, d.stream>>>(d, a, t);
         else
-            k_aa_even<S, FLAGS, FORCE, false><<<step_grid(d), step_block(d), 0, d.stream>>>(d, a, nullptr);
+            k_aa_even<S, FLAGS, FORCE, false, FLAT><<<grid, block, 0, d.stream>>>(d, a, nullptr);
     }
     return cudaGetLastError();
+}
+
+// The AA kernels run flat only where whole rows would leave lanes idle (with
+// whole-warp rows their flat forms compile to no fewer spills).
+template <int S, bool FLAGS, int FORCE>
+static cudaError_t launch_aa3(const Dev &d, void *A, int odd, void *tape) {
+    return d.flat_step ? launch_aa4<S, FLAGS, FORCE, true>(d, A, odd, tape)
+                       : launch_aa4<S, FLAGS, FORCE, false>(d, A, odd, tape);
 }
 
 template <int S, bool FLAGS>
