@@ -117,13 +117,14 @@ template <class R> struct AdjBlocks {
     static constexpr int value = sizeof(R) == 8 ? 1 : 2;
 };
 
-template <class R, bool FLAGS, bool FORCE>
+// FLAT: the launch of d.PF (pairs in plane order), else of d.P (whole rows).
+template <class R, bool FLAGS, bool FORCE, bool FLAT>
 __global__ void __launch_bounds__(256, AdjBlocks<R>::value)
     k_adj_step(const Dev d, const R *__restrict__ lam_in, R *__restrict__ lam_out, const R *__restrict__ tape,
                R *__restrict__ grad_F) {
     int x0, y, z;
-    if (!pair_cell(d.g, d.P, blockDim.x, blockDim.y, blockIdx.x, blockIdx.y, threadIdx.x, threadIdx.y, x0,
-                   y, z))
+    if (!pair_cell<FLAT>(d.g, FLAT ? d.PF : d.P, blockDim.x, blockDim.y, blockIdx.x, blockIdx.y, threadIdx.x,
+                         threadIdx.y, x0, y, z))
         return;
     const Geom &g = d.g;
     const bool has1 = x0 + 1 < g.nx;
@@ -261,19 +262,25 @@ __global__ void __launch_bounds__(256)
 
 static dim3 grid_of(const Dev &d) { return dim3(d.L.nxb * d.L.nyb, d.g.nz); }
 static dim3 block_of(const Dev &d) { return dim3(d.L.bx_threads, d.L.by_threads); }
-// the reverse step runs on the paired launch of the forward step kernels
-static dim3 pair_grid_of(const Dev &d) { return dim3(d.P.nxb * d.P.nyb, d.P.nzr); }
-static dim3 pair_block_of(const Dev &d) { return dim3(d.P.bx_threads, d.P.by_threads); }
+// The reverse step runs on the paired launch of the forward step kernels:
+// flat where whole rows would leave lanes idle.
+template <class R, bool FLAGS, bool FLAT>
+static cudaError_t launch_adj_step2(const Dev &d, const void *li, void *lo, const void *tape, void *gF) {
+    const RowLaunch &P = FLAT ? d.PF : d.P;
+    const dim3 grid(P.nxb * P.nyb, P.nzr), block(P.bx_threads, P.by_threads);
+    if (d.force_on)
+        k_adj_step<R, FLAGS, true, FLAT><<<grid, block, 0, d.stream>>>(
+            d, static_cast<const R *>(li), static_cast<R *>(lo), static_cast<const R *>(tape), static_cast<R *>(gF));
+    else
+        k_adj_step<R, FLAGS, false, FLAT><<<grid, block, 0, d.stream>>>(
+            d, static_cast<const R *>(li), static_cast<R *>(lo), static_cast<const R *>(tape), static_cast<R *>(gF));
+    return cudaGetLastError();
+}
 
 template <class R, bool FLAGS>
 static cudaError_t launch_adj_step(const Dev &d, const void *li, void *lo, const void *tape, void *gF) {
-    if (d.force_on)
-        k_adj_step<R, FLAGS, true><<<pair_grid_of(d), pair_block_of(d), 0, d.stream>>>(
-            d, static_cast<const R *>(li), static_cast<R *>(lo), static_cast<const R *>(tape), static_cast<R *>(gF));
-    else
-        k_adj_step<R, FLAGS, false><<<pair_grid_of(d), pair_block_of(d), 0, d.stream>>>(
-            d, static_cast<const R *>(li), static_cast<R *>(lo), static_cast<const R *>(tape), static_cast<R *>(gF));
-    return cudaGetLastError();
+    return d.flat_step ? launch_adj_step2<R, FLAGS, true>(d, li, lo, tape, gF)
+                       : launch_adj_step2<R, FLAGS, false>(d, li, lo, tape, gF);
 }
 
 template <class R>
