@@ -669,7 +669,9 @@ lbm_status lbm_step_reduce(lbm_ctx *ctx, int n, double *out) {
         if (s) return s;
     } else {
         Dev d = make_dev(ctx);
-        const size_t nb = (size_t)d.P.nxb * d.P.nyb * d.P.nzr;
+        // one partial per block of either launch mapping of the step
+        const size_t nb_rows = (size_t)d.P.nxb * d.P.nyb * d.P.nzr, nb_flat = (size_t)d.PF.nxb * d.PF.nyb * d.PF.nzr;
+        const size_t nb = nb_rows > nb_flat ? nb_rows : nb_flat;
         if (ctx->step_partials_n < nb) {
             if (ctx->step_partials) {
                 cudaStreamSynchronize(ctx->stream);

@@ -423,14 +423,15 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 // (the reduction of lbm_reduce without a pass of its own): every thread, in
 // the lattice or not, reaches the block reduction; partials[4 b + k] of block
 // b = blockIdx.y * gridDim.x + blockIdx.x, summed in a fixed order.
-template <int S, bool FLAGS, int FORCE>
+template <int S, bool FLAGS, int FORCE, bool FLAT>
 __global__ void __launch_bounds__(256, StepBlocks<S>::value)
     k_step_reduce(const Dev d, const typename Stor<S>::T *__restrict__ src, typename Stor<S>::T *__restrict__ dst,
                   double *__restrict__ partials) {
     if (FLAGS && LinkBounce<S>::value) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     double red[4] = {0.0, 0.0, 0.0, 0.0};
     int x0, y, z;
-    if (pair_cell(d.g, d.P, blockDim.x, blockDim.y, blockIdx.x, blockIdx.y, threadIdx.x, threadIdx.y, x0, y, z))
+    if (pair_cell<FLAT>(d.g, FLAT ? d.PF : d.P, blockDim.x, blockDim.y, blockIdx.x, blockIdx.y, threadIdx.x,
+                        threadIdx.y, x0, y, z))
         step_pair<S, FLAGS, FORCE, false, GlobalRows<S>, true>(d, GlobalRows<S>{src}, src, dst, nullptr, x0, y, z,
                                                               red);
     __shared__ double sm[8][4];  // blocks hold at most 256 threads, whole warps
@@ -986,15 +987,30 @@ cudaError_t Ops<S>::step_reduce(const Dev &d, const void *src, void *dst, double
     if (d.flags && !d.mask) return cudaErrorInvalidValue;
     const T *s = static_cast<const T *>(src);
     T *t = static_cast<T *>(dst);
-    const dim3 grid = step_grid(d), block = step_block(d);
-    if (d.flags) {
-        if (d.Ffield) k_step_reduce<S, true, 2><<<grid, block, 0, d.stream>>>(d, s, t, partials);
-        else if (d.force_on) k_step_reduce<S, true, 1><<<grid, block, 0, d.stream>>>(d, s, t, partials);
-        else k_step_reduce<S, true, 0><<<grid, block, 0, d.stream>>>(d, s, t, partials);
+    // the launch mapping of the plain step (launch_step3)
+    const bool flat = d.flat_step || (d.flags ? flat_preferred<S, true>() : flat_preferred<S, false>());
+    const RowLaunch &P = flat ? d.PF : d.P;
+    const dim3 grid(P.nxb * P.nyb, P.nzr), block(P.bx_threads, P.by_threads);
+    if (flat) {
+        if (d.flags) {
+            if (d.Ffield) k_step_reduce<S, true, 2, true><<<grid, block, 0, d.stream>>>(d, s, t, partials);
+            else if (d.force_on) k_step_reduce<S, true, 1, true><<<grid, block, 0, d.stream>>>(d, s, t, partials);
+            else k_step_reduce<S, true, 0, true><<<grid, block, 0, d.stream>>>(d, s, t, partials);
+        } else {
+            if (d.Ffield) k_step_reduce<S, false, 2, true><<<grid, block, 0, d.stream>>>(d, s, t, partials);
+            else if (d.force_on) k_step_reduce<S, false, 1, true><<<grid, block, 0, d.stream>>>(d, s, t, partials);
+            else k_step_reduce<S, false, 0, true><<<grid, block, 0, d.stream>>>(d, s, t, partials);
+        }
     } else {
-        if (d.Ffield) k_step_reduce<S, false, 2><<<grid, block, 0, d.stream>>>(d, s, t, partials);
-        else if (d.force_on) k_step_reduce<S, false, 1><<<grid, block, 0, d.stream>>>(d, s, t, partials);
-        else k_step_reduce<S, false, 0><<<grid, block, 0, d.stream>>>(d, s, t, partials);
+        if (d.flags) {
+            if (d.Ffield) k_step_reduce<S, true, 2, false><<<grid, block, 0, d.stream>>>(d, s, t, partials);
+            else if (d.force_on) k_step_reduce<S, true, 1, false><<<grid, block, 0, d.stream>>>(d, s, t, partials);
+            else k_step_reduce<S, true, 0, false><<<grid, block, 0, d.stream>>>(d, s, t, partials);
+        } else {
+            if (d.Ffield) k_step_reduce<S, false, 2, false><<<grid, block, 0, d.stream>>>(d, s, t, partials);
+            else if (d.force_on) k_step_reduce<S, false, 1, false><<<grid, block, 0, d.stream>>>(d, s, t, partials);
+            else k_step_reduce<S, false, 0, false><<<grid, block, 0, d.stream>>>(d, s, t, partials);
+        }
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
