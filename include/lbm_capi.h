@@ -229,8 +229,8 @@ lbm_status lbm_reduce_state_noalloc(const void *state, lbm_storage fmt, int nx, 
  * (no pass over the lattice of their own: the reduction fused into the step
  * as an epilogue). out: 4 doubles, host (the call synchronizes) or device
  * (asynchronous). The same totals as lbm_reduce up to the order of the FP64
- * sums; deterministic. With LBM_PATTERN_AA the totals are taken by a
- * reduction pass before the steps. */
+ * sums; deterministic. Both streaming patterns fuse the sum into their
+ * first step. */
 lbm_status lbm_step_reduce(lbm_ctx *ctx, int n, double *out);
 
 /* Copy the current state out as shifted populations s_i = f_i - w_i in format

@@ -76,9 +76,10 @@ __device__ __forceinline__ void pair_check_record(const Dev &d, int c, bool live
 
 // Even step (natural -> swapped): local, every access an aligned pair.
 // FLAT (both AA kernels): the launch of d.PF (pairs in plane order), else of d.P.
-template <int S, bool FLAGS, int FORCE, bool RECORD, bool FLAT>
-__global__ void __launch_bounds__(256, StepBlocks<S>::value)
-    k_aa_even(const Dev d, typename Stor<S>::T *__restrict__ A, typename Stor<S>::R *__restrict__ tape) {
+// RED: also add the pair's pre-collision totals to red[4] (pair_add_totals).
+template <int S, bool FLAGS, int FORCE, bool RECORD, bool FLAT, bool RED>
+__device__ __forceinline__ void aa_even_pair(const Dev &d, typename Stor<S>::T *__restrict__ A,
+                                             typename Stor<S>::R *__restrict__ tape, double *red) {
     typedef typename Stor<S>::R R;
     typedef typename Pair2<R>::V V;
     int x0, y, z;
@@ -99,12 +100,29 @@ __global__ void __launch_bounds__(256, StepBlocks<S>::value)
     Guo2<R> G;
     pair_force<R, FORCE, relax_about_t(S)>(d, c, Fx, Fy, Fz, G);
     const Mom2<R> m = moments2<R, FORCE != 0>(s, Fx, Fy, Fz, d.incomp);
+    if (RED) pair_add_totals<R>(m, live0, live1, d.incomp, red);
     pair_check_record<R, RECORD>(d, c, live0, live1, m, tape);
     collide2<R, FORCE != 0, relax_about_t(S)>(s, m, R(d.omega), R(d.cs), Fx, Fy, Fz, G, d.incomp);
     // a solid lane writes its NaN back (its slots stay marked)
 #pragma unroll
     for (int i = 0; i < Q; ++i)
         Stor<S>::st2(A + (long long)opp(i) * qs + c, !FLAGS || live0 ? s[i].x : nan, !FLAGS || live1 ? s[i].y : nan);
+}
+
+template <int S, bool FLAGS, int FORCE, bool RECORD, bool FLAT>
+__global__ void __launch_bounds__(256, StepBlocks<S>::value)
+    k_aa_even(const Dev d, typename Stor<S>::T *__restrict__ A, typename Stor<S>::R *__restrict__ tape) {
+    aa_even_pair<S, FLAGS, FORCE, RECORD, FLAT, false>(d, A, tape, nullptr);
+}
+
+// The even step with the totals of its pre-collision state summed per block
+// (every thread, in the lattice or not, reaches the block sum).
+template <int S, bool FLAGS, int FORCE, bool FLAT>
+__global__ void __launch_bounds__(256, StepBlocks<S>::value)
+    k_aa_even_reduce(const Dev d, typename Stor<S>::T *__restrict__ A, double *__restrict__ partials) {
+    double red[4] = {0.0, 0.0, 0.0, 0.0};
+    aa_even_pair<S, FLAGS, FORCE, false, FLAT, true>(d, A, nullptr, red);
+    block_partials(red, partials);
 }
 
 // Resident 256-thread blocks per SM the odd step is compiled for. With flags
@@ -122,9 +140,9 @@ template <int S, bool FLAGS> struct AaOddBlocks {
 // address is a select, so the whole step is one branch-free sequence (a
 // NaN-driven fix-up with separate store paths measured twice as slow here:
 // its code size and divergence made it instruction-bound).
-template <int S, bool FLAGS, int FORCE, bool RECORD, bool FLAT>
-__global__ void __launch_bounds__(256, AaOddBlocks<S, FLAGS>::value)
-    k_aa_odd(const Dev d, typename Stor<S>::T *__restrict__ A, typename Stor<S>::R *__restrict__ tape) {
+template <int S, bool FLAGS, int FORCE, bool RECORD, bool FLAT, bool RED>
+__device__ __forceinline__ void aa_odd_pair(const Dev &d, typename Stor<S>::T *__restrict__ A,
+                                            typename Stor<S>::R *__restrict__ tape, double *red) {
     typedef typename Stor<S>::T T;
     typedef typename Stor<S>::R R;
     typedef typename Pair2<R>::V V;
@@ -181,6 +199,7 @@ __global__ void __launch_bounds__(256, AaOddBlocks<S, FLAGS>::value)
     Guo2<R> G;
     pair_force<R, FORCE, relax_about_t(S)>(d, c, Fx, Fy, Fz, G);
     const Mom2<R> m = moments2<R, FORCE != 0>(s, Fx, Fy, Fz, d.incomp);
+    if (RED) pair_add_totals<R>(m, live0, live1, d.incomp, red);
     pair_check_record<R, RECORD>(d, c, live0, live1, m, tape);
     collide2<R, FORCE != 0, relax_about_t(S)>(s, m, R(d.omega), R(d.cs), Fx, Fy, Fz, G, d.incomp);
     // P_i(x) to slot i of x + e_i, or to slot opp(i) of x if x + e_i is solid
@@ -210,6 +229,21 @@ __global__ void __launch_bounds__(256, AaOddBlocks<S, FLAGS>::value)
                 Stor<S>::st(Po + 1, s[i].y - wall_term<R>(d, i));
         }
     }
+}
+
+template <int S, bool FLAGS, int FORCE, bool RECORD, bool FLAT>
+__global__ void __launch_bounds__(256, AaOddBlocks<S, FLAGS>::value)
+    k_aa_odd(const Dev d, typename Stor<S>::T *__restrict__ A, typename Stor<S>::R *__restrict__ tape) {
+    aa_odd_pair<S, FLAGS, FORCE, RECORD, FLAT, false>(d, A, tape, nullptr);
+}
+
+// The odd step with the totals of its pre-collision state summed per block.
+template <int S, bool FLAGS, int FORCE, bool FLAT>
+__global__ void __launch_bounds__(256, AaOddBlocks<S, FLAGS>::value)
+    k_aa_odd_reduce(const Dev d, typename Stor<S>::T *__restrict__ A, double *__restrict__ partials) {
+    double red[4] = {0.0, 0.0, 0.0, 0.0};
+    aa_odd_pair<S, FLAGS, FORCE, false, FLAT, true>(d, A, nullptr, red);
+    block_partials(red, partials);
 }
 
 template <int S, bool FLAGS, int FORCE, bool FLAT>
@@ -247,6 +281,41 @@ static cudaError_t launch_aa2(const Dev &d, void *A, int odd, void *tape) {
     if (d.Ffield) return launch_aa3<S, FLAGS, 2>(d, A, odd, tape);
     if (d.force_on) return launch_aa3<S, FLAGS, 1>(d, A, odd, tape);
     return launch_aa3<S, FLAGS, 0>(d, A, odd, tape);
+}
+
+template <int S, bool FLAGS, int FORCE, bool FLAT>
+static cudaError_t launch_aa_reduce4(const Dev &d, void *A, int odd, double *partials, double *out) {
+    typedef typename Stor<S>::T T;
+    T *a = static_cast<T *>(A);
+    const RowLaunch &P = FLAT ? d.PF : d.P;
+    const dim3 grid(P.nxb * P.nyb, P.nzr), block(P.bx_threads, P.by_threads);
+    if (odd)
+        k_aa_odd_reduce<S, FLAGS, FORCE, FLAT><<<grid, block, 0, d.stream>>>(d, a, partials);
+    else
+        k_aa_even_reduce<S, FLAGS, FORCE, FLAT><<<grid, block, 0, d.stream>>>(d, a, partials);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_reduce_final<<<1, RED_THREADS, 0, d.stream>>>(partials, (int)(grid.x * grid.y), out);
+    return cudaGetLastError();
+}
+
+template <int S, bool FLAGS>
+static cudaError_t launch_aa_reduce2(const Dev &d, void *A, int odd, double *partials, double *out) {
+    if (d.Ffield)
+        return d.flat_step ? launch_aa_reduce4<S, FLAGS, 2, true>(d, A, odd, partials, out)
+                           : launch_aa_reduce4<S, FLAGS, 2, false>(d, A, odd, partials, out);
+    if (d.force_on)
+        return d.flat_step ? launch_aa_reduce4<S, FLAGS, 1, true>(d, A, odd, partials, out)
+                           : launch_aa_reduce4<S, FLAGS, 1, false>(d, A, odd, partials, out);
+    return d.flat_step ? launch_aa_reduce4<S, FLAGS, 0, true>(d, A, odd, partials, out)
+                       : launch_aa_reduce4<S, FLAGS, 0, false>(d, A, odd, partials, out);
+}
+
+template <int S>
+cudaError_t AaOps<S>::step_reduce(const Dev &d, void *A, int odd, double *partials, double *out) {
+    if (d.flags && !d.mask) return cudaErrorInvalidValue;
+    return d.flags ? launch_aa_reduce2<S, true>(d, A, odd, partials, out)
+                   : launch_aa_reduce2<S, false>(d, A, odd, partials, out);
 }
 
 template <int S>

@@ -660,41 +660,35 @@ lbm_status lbm_step_reduce(lbm_ctx *ctx, int n, double *out) {
     if (check_ctx(ctx)) return LBM_ERR_ARG;
     if (n < 1 || !out) return fail(ctx, LBM_ERR_ARG, "n must be >= 1 and out is required");
     cudaError_t e;
-    if (ctx->pattern == LBM_PATTERN_AA) {
-        // (the AA kernels have no fused form: the totals, then the steps)
-        Dev d = make_dev(ctx);
-        e = LBM_DISPATCH(ctx, reduce(d, state_lat(ctx), ctx->red_partials, ctx->red_out));
-        if (e != cudaSuccess) return cuda_fail(ctx, e, "reduce launch");
-        lbm_status s = lbm_step(ctx, n);
-        if (s) return s;
-    } else {
-        Dev d = make_dev(ctx);
-        // one partial per block of either launch mapping of the step
-        const size_t nb_rows = (size_t)d.P.nxb * d.P.nyb * d.P.nzr, nb_flat = (size_t)d.PF.nxb * d.PF.nyb * d.PF.nzr;
-        const size_t nb = nb_rows > nb_flat ? nb_rows : nb_flat;
-        if (ctx->step_partials_n < nb) {
-            if (ctx->step_partials) {
-                cudaStreamSynchronize(ctx->stream);
-                cudaFree(ctx->step_partials);
-            }
-            ctx->step_partials = nullptr;
-            ctx->step_partials_n = 0;
-            e = cudaMalloc((void **)&ctx->step_partials, nb * 4 * sizeof(double));
-            if (e != cudaSuccess) {
-                cudaGetLastError();
-                ctx->step_partials = nullptr;
-                return fail(ctx, LBM_ERR_OOM, "cannot allocate the fused-reduction partials");
-            }
-            ctx->step_partials_n = nb;
+    Dev d = make_dev(ctx);
+    // one partial per block of either launch mapping of the step
+    const size_t nb_rows = (size_t)d.P.nxb * d.P.nyb * d.P.nzr, nb_flat = (size_t)d.PF.nxb * d.PF.nyb * d.PF.nzr;
+    const size_t nb = nb_rows > nb_flat ? nb_rows : nb_flat;
+    if (ctx->step_partials_n < nb) {
+        if (ctx->step_partials) {
+            cudaStreamSynchronize(ctx->stream);
+            cudaFree(ctx->step_partials);
         }
+        ctx->step_partials = nullptr;
+        ctx->step_partials_n = 0;
+        e = cudaMalloc((void **)&ctx->step_partials, nb * 4 * sizeof(double));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            ctx->step_partials = nullptr;
+            return fail(ctx, LBM_ERR_OOM, "cannot allocate the fused-reduction partials");
+        }
+        ctx->step_partials_n = nb;
+    }
+    if (ctx->pattern == LBM_PATTERN_AA)
+        e = LBM_AA_DISPATCH(ctx, step_reduce(d, ctx->lat[0], ctx->cur, ctx->step_partials, ctx->red_out));
+    else
         e = LBM_DISPATCH(ctx, step_reduce(d, ctx->lat[ctx->cur], ctx->lat[ctx->cur ^ 1], ctx->step_partials,
                                           ctx->red_out));
-        if (e != cudaSuccess) return cuda_fail(ctx, e, "fused step-reduce launch");
-        ctx->cur ^= 1;
-        ctx->steps_done++;
-        lbm_status s = lbm_step(ctx, n - 1);
-        if (s) return s;
-    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "fused step-reduce launch");
+    ctx->cur ^= 1;
+    ctx->steps_done++;
+    lbm_status s = lbm_step(ctx, n - 1);
+    if (s) return s;
     const bool dev = is_device_ptr(out);
     e = cudaMemcpyAsync(out, ctx->red_out, 4 * sizeof(double), dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                         ctx->stream);

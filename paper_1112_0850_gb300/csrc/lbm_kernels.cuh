@@ -202,6 +202,52 @@ template <int S> struct SharedRows {
     static __device__ __forceinline__ void ld2(const T *p, R &a, R &b) { Stor<S>::ls2(p, a, b); }
 };
 
+// The pair's mass and momentum j + F/2 (rho u, or u itself in the
+// incompressible model) of the pre-collision state, in FP64, added to red[4].
+template <class R>
+__device__ __forceinline__ void pair_add_totals(const Mom2<R> &m, bool live0, bool live1, bool incomp, double *red) {
+    if (live0) {
+        const double mr = incomp ? 1.0 : (double)m.rho.x;
+        red[0] += (double)m.rho.x;
+        red[1] += mr * (double)m.ux.x;
+        red[2] += mr * (double)m.uy.x;
+        red[3] += mr * (double)m.uz.x;
+    }
+    if (live1) {
+        const double mr = incomp ? 1.0 : (double)m.rho.y;
+        red[0] += (double)m.rho.y;
+        red[1] += mr * (double)m.ux.y;
+        red[2] += mr * (double)m.uy.y;
+        red[3] += mr * (double)m.uz.y;
+    }
+}
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// The block's sum of every thread's red[4], in a fixed order, to
+// partials[4 b + k] of block b = blockIdx.y * gridDim.x + blockIdx.x. Every
+// thread of the block calls it (blocks of whole warps, at most 256 threads).
+__device__ __forceinline__ void block_partials(const double red[4], double *__restrict__ partials) {
+    __shared__ double sm[8][4];
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int nwarps = (blockDim.x * blockDim.y) >> 5;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const double v = warp_sum_d(red[k]);
+        if (lane == 0) sm[wid][k] = v;
+    }
+    __syncthreads();
+    if (tid < 4) {
+        double t = 0.0;
+        for (int w = 0; w < nwarps; ++w) t += sm[w][tid];
+        partials[4 * ((long long)blockIdx.y * gridDim.x + blockIdx.x) + tid] = t;
+    }
+}
+
 // One fused step for the cell pair (x0, x0 + 1) of row (y, z): gather through
 // `rows` (the cell's own opposite populations, for bounce-back, from src),
 // collide, store to dst. RED: also add the pair's mass and momentum j + F/2
@@ -322,23 +368,7 @@ __device__ __forceinline__ void step_pair(const Dev &d, const Rows &rows, const 
     const bool bad0 = live0 && !(m.rho.x > R(0) && m.rho.x < R(1e30));
     const bool bad1 = live1 && !(m.rho.y > R(0) && m.rho.y < R(1e30));
     if (bad0 || bad1) atomicOr(d.status, LBM_STATUS_DIVERGED);
-    if (RED) {
-        // momentum j + F/2: rho u, or u itself in the incompressible model
-        if (live0) {
-            const double mr = d.incomp ? 1.0 : (double)m.rho.x;
-            red[0] += (double)m.rho.x;
-            red[1] += mr * (double)m.ux.x;
-            red[2] += mr * (double)m.uy.x;
-            red[3] += mr * (double)m.uz.x;
-        }
-        if (live1) {
-            const double mr = d.incomp ? 1.0 : (double)m.rho.y;
-            red[0] += (double)m.rho.y;
-            red[1] += mr * (double)m.ux.y;
-            red[2] += mr * (double)m.uy.y;
-            red[3] += mr * (double)m.uz.y;
-        }
-    }
+    if (RED) pair_add_totals<R>(m, live0, live1, d.incomp, red);
     if (RECORD) {
         const long long qs = g.qs;
         st2_real(tape + c, m.rho.x, m.rho.y);
@@ -413,12 +443,6 @@ __global__ void __launch_bounds__(256, StepBlocks<S>::value)
     step_pair<S, FLAGS, FORCE, RECORD>(d, GlobalRows<S>{src}, src, dst, tape, x0, y, z);
 }
 
-__device__ __forceinline__ double warp_sum_d(double v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
 // The step with the mass/momentum totals of its pre-collision state fused in
 // (the reduction of lbm_reduce without a pass of its own): every thread, in
 // the lattice or not, reaches the block reduction; partials[4 b + k] of block
@@ -434,20 +458,7 @@ __global__ void __launch_bounds__(256, StepBlocks<S>::value)
                         threadIdx.y, x0, y, z))
         step_pair<S, FLAGS, FORCE, false, GlobalRows<S>, true>(d, GlobalRows<S>{src}, src, dst, nullptr, x0, y, z,
                                                               red);
-    __shared__ double sm[8][4];  // blocks hold at most 256 threads, whole warps
-    const int tid = threadIdx.y * blockDim.x + threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const int nwarps = (blockDim.x * blockDim.y) >> 5;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const double v = warp_sum_d(red[k]);
-        if (lane == 0) sm[wid][k] = v;
-    }
-    __syncthreads();
-    if (tid < 4) {
-        double t = 0.0;
-        for (int w = 0; w < nwarps; ++w) t += sm[w][tid];
-        partials[4 * ((long long)blockIdx.y * gridDim.x + blockIdx.x) + tid] = t;
-    }
+    block_partials(red, partials);
 }
 
 // ---------------------------------------------------------------------------

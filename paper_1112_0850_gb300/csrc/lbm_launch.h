@@ -101,6 +101,10 @@ template <int S> struct AaOps {
     // the natural layout to the swapped one, else the neighbour (odd) step,
     // which takes it back. tape as in Ops<S>::step.
     static cudaError_t step(const Dev &d, void *A, int odd, void *tape);
+    // The same step, with the mass/momentum totals of the state it starts from
+    // summed by its blocks (partials: 4 doubles per block of the launch) and
+    // finished into out[4] (device), as Ops<S>::step_reduce.
+    static cudaError_t step_reduce(const Dev &d, void *A, int odd, double *partials, double *out);
 };
 
 // Set-up: push masks of every padded cell from the padded flags (device).
