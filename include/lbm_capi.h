@@ -276,6 +276,15 @@ size_t lbm_halo_bytes(const lbm_ctx *ctx);
 lbm_status lbm_halo_pack(lbm_ctx *ctx, int side, void *buf);
 lbm_status lbm_halo_unpack(lbm_ctx *ctx, int side, const void *buf);
 
+/* The totals of lbm_reduce over the fluid cells of planes z0 <= z < z1 only
+ * (0 <= z0 <= z1 <= nz; z0 == z1 gives zeros), in the same fixed FP64 order.
+ * For a slab, the interior planes 1 .. nz - 2 read after an exchange: the
+ * totals of all slabs then add up to those of the unsplit lattice (to the
+ * order of the FP64 sums), the mass/momentum check of a split run, summed
+ * over ranks with an all-reduce. out is a host array; synchronizes. Returns
+ * LBM_ERR_ARG for a null out or planes outside that range. */
+lbm_status lbm_reduce_planes(lbm_ctx *ctx, int z0, int z1, double out[4]);
+
 /* As lbm_step, and also record, for each of the n steps k, the moments the
  * adjoint needs: (rho, u_x, u_y, u_z) of the pre-collision state at step k,
  * u including the F/2 shift. tape: device array of n * tape_bytes_per_step

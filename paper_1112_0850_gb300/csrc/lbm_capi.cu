@@ -644,16 +644,22 @@ lbm_status lbm_macros(lbm_ctx *ctx, void *rho, void *u) {
     return st.finish();
 }
 
-lbm_status lbm_reduce(lbm_ctx *ctx, double out[4]) {
+lbm_status lbm_reduce_planes(lbm_ctx *ctx, int z0, int z1, double out[4]) {
     if (check_ctx(ctx)) return LBM_ERR_ARG;
     if (!out) return fail(ctx, LBM_ERR_ARG, "out is required");
+    if (z0 < 0 || z1 < z0 || z1 > ctx->g.nz) return fail(ctx, LBM_ERR_ARG, "planes must satisfy 0 <= z0 <= z1 <= nz");
     Dev d = make_dev(ctx);
-    cudaError_t e = LBM_DISPATCH(ctx, reduce(d, state_lat(ctx), ctx->red_partials, ctx->red_out));
+    cudaError_t e = LBM_DISPATCH(ctx, reduce(d, state_lat(ctx), z0, z1, ctx->red_partials, ctx->red_out));
     if (e != cudaSuccess) return cuda_fail(ctx, e, "reduce launch");
     e = cudaMemcpyAsync(out, ctx->red_out, 4 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "reduce result copy");
     return LBM_OK;
+}
+
+lbm_status lbm_reduce(lbm_ctx *ctx, double out[4]) {
+    if (check_ctx(ctx)) return LBM_ERR_ARG;
+    return lbm_reduce_planes(ctx, 0, ctx->g.nz, out);
 }
 
 lbm_status lbm_step_reduce(lbm_ctx *ctx, int n, double *out) {

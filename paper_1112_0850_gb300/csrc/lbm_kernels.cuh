@@ -783,16 +783,17 @@ __device__ __forceinline__ double warp_sum(double v) {
 
 template <int S, bool FLAGS, bool FORCE>
 __global__ void __launch_bounds__(RED_THREADS)
-    k_reduce(const Dev d, const typename Stor<S>::T *__restrict__ P, double *__restrict__ partials) {
+    k_reduce(const Dev d, const typename Stor<S>::T *__restrict__ P, int z0, int z1, double *__restrict__ partials) {
     typedef typename Stor<S>::R R;
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
-    const long long N = d.n_cells;
+    // the cells of planes z0 <= z < z1
+    const long long N = (long long)d.g.nx * d.g.ny * (z1 - z0);
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long cc = (long long)blockIdx.x * blockDim.x + threadIdx.x; cc < N; cc += stride) {
         const int x = (int)(cc % d.g.nx);
         const long long r = cc / d.g.nx;
         const int y = (int)(r % d.g.ny);
-        const int z = (int)(r / d.g.ny);
+        const int z = z0 + (int)(r / d.g.ny);
         const int c = cell_index(d.g, x, y, z);
         if (FLAGS && d.flags[c]) continue;
         R s[Q];
@@ -1133,20 +1134,21 @@ cudaError_t Ops<S>::macros(const Dev &d, const void *lat, void *rho, void *u) {
 }
 
 template <int S, bool FLAGS>
-static cudaError_t launch_reduce(const Dev &d, const void *lat, double *partials) {
+static cudaError_t launch_reduce(const Dev &d, const void *lat, int z0, int z1, double *partials) {
     typedef typename Stor<S>::T T;
     if (d.force_on)
-        k_reduce<S, FLAGS, true><<<RED_BLOCKS, RED_THREADS, 0, d.stream>>>(d, static_cast<const T *>(lat),
+        k_reduce<S, FLAGS, true><<<RED_BLOCKS, RED_THREADS, 0, d.stream>>>(d, static_cast<const T *>(lat), z0, z1,
                                                                           partials);
     else
-        k_reduce<S, FLAGS, false><<<RED_BLOCKS, RED_THREADS, 0, d.stream>>>(d, static_cast<const T *>(lat),
+        k_reduce<S, FLAGS, false><<<RED_BLOCKS, RED_THREADS, 0, d.stream>>>(d, static_cast<const T *>(lat), z0, z1,
                                                                            partials);
     return cudaGetLastError();
 }
 
 template <int S>
-cudaError_t Ops<S>::reduce(const Dev &d, const void *lat, double *partials, double *out) {
-    cudaError_t e = d.flags ? launch_reduce<S, true>(d, lat, partials) : launch_reduce<S, false>(d, lat, partials);
+cudaError_t Ops<S>::reduce(const Dev &d, const void *lat, int z0, int z1, double *partials, double *out) {
+    cudaError_t e = d.flags ? launch_reduce<S, true>(d, lat, z0, z1, partials)
+                            : launch_reduce<S, false>(d, lat, z0, z1, partials);
     if (e != cudaSuccess) return e;
     k_reduce_final<<<1, RED_THREADS, 0, d.stream>>>(partials, RED_BLOCKS, out);
     return cudaGetLastError();

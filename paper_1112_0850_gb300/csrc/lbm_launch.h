@@ -84,8 +84,9 @@ template <int S> struct Ops {
     static cudaError_t get_state(const Dev &d, const void *lat, void *dst, int fmt);
     static cudaError_t set_state(const Dev &d, void *lat, const void *src, int fmt);
     static cudaError_t macros(const Dev &d, const void *lat, void *rho, void *u);
-    // partials: RED_BLOCKS * 4 doubles of scratch; out: 4 doubles (device).
-    static cudaError_t reduce(const Dev &d, const void *lat, double *partials, double *out);
+    // Totals over the fluid cells of planes z0 <= z < z1. partials: RED_BLOCKS * 4
+    // doubles of scratch; out: 4 doubles (device).
+    static cudaError_t reduce(const Dev &d, const void *lat, int z0, int z1, double *partials, double *out);
     // One step (as step, no tape) that also sums the totals of reduce for its
     // pre-collision state into out (4 doubles, device); partials: 4 doubles per
     // block of the step grid.

@@ -141,9 +141,16 @@ class Lattice:
         self._call("lbm_macros", self._ptr(rho, self.real, self.shape), self._ptr(u, self.real, (3,) + self.shape))
         return rho, u
 
-    def reduce(self):
+    def reduce(self, z0=None, z1=None):
+        """{sum rho, sum rho u} over the fluid cells, in FP64; with z0, z1 over
+        planes z0 <= z < z1 only (a slab's interior planes: 1, nz - 1)."""
         out = (ctypes.c_double * 4)()
-        self._call("lbm_reduce", out)
+        if z0 is None and z1 is None:
+            self._call("lbm_reduce", out)
+        else:
+            z0 = 0 if z0 is None else int(z0)
+            z1 = self.shape[0] if z1 is None else int(z1)
+            self._call("lbm_reduce_planes", z0, z1, out)
         return np.array(out[:])
 
     def step_reduce(self, n=1, out=None):

@@ -13,6 +13,9 @@ populations between a slab's boundary planes and packed buffers.
 - `exchange_ranks`: the same exchange between processes, one slab per rank,
   over torch.distributed point-to-point calls with bounded waits. It moves
   whatever tensors it is given (packed halos, or whole planes).
+- `SlabSet.totals`, `reduce_ranks`: the FP64 mass and momentum totals of a
+  split lattice, each slab summing its interior planes (lbm_reduce_planes)
+  and the slabs' sums added on the host, or over ranks by an all-reduce.
 """
 import datetime
 
@@ -107,6 +110,17 @@ class SlabSet:
         self.exchange()
         return torch.cat([lat.get_state(fmt)[:, 1:-1] for lat in self.slabs], dim=1)
 
+    def totals(self):
+        """{sum rho, sum rho u_x, sum rho u_y, sum rho u_z} over the fluid
+        cells of the whole lattice: each slab's interior planes summed on the
+        device in FP64 (after an exchange, as the readers need), the slabs'
+        sums added in slab order, so the result is deterministic."""
+        self.exchange()
+        out = np.zeros(4)
+        for lat in self.slabs:
+            out += lat.reduce(1, lat.shape[0] - 1)
+        return out
+
     def status_word(self, clear=False):
         w = 0
         for lat in self.slabs:
@@ -148,4 +162,23 @@ def exchange_ranks(send_down, send_up, recv_below, recv_above, timeout=datetime.
             w.wait(timeout=timeout)
         except RuntimeError as e:
             return EXCHANGE_FAILED, "%s: %s" % (what, str(e).splitlines()[0][:200])
+    return EXCHANGE_OK, ""
+
+
+def reduce_ranks(totals, timeout=datetime.timedelta(seconds=10), group=None):
+    """Sum a rank's FP64 totals (any float64 tensor, e.g. the 4 of
+    `Lattice.reduce(1, nz - 1)` over its slab's interior planes) over all
+    ranks, in place, with an all-reduce whose wait is bounded by `timeout`.
+    Returns (EXCHANGE_OK, "") or, when the wait runs out or a rank has gone,
+    (EXCHANGE_FAILED, why); the tensor's contents are then undefined."""
+    import torch.distributed as dist
+    if totals.dtype != torch.float64:
+        raise TypeError("totals are summed in float64")
+    if dist.get_world_size(group) == 1:
+        return EXCHANGE_OK, ""
+    w = dist.all_reduce(totals, op=dist.ReduceOp.SUM, group=group, async_op=True)
+    try:
+        w.wait(timeout=timeout)
+    except RuntimeError as e:
+        return EXCHANGE_FAILED, "all-reduce of totals: %s" % str(e).splitlines()[0][:200]
     return EXCHANGE_OK, ""

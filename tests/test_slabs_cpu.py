@@ -69,8 +69,9 @@ def test_with_ghosts_wraps_periodically():
     assert slabs.ghost_planes(5, 0, 5) == [4, 0, 1, 2, 3, 4, 0]
 
 
-def _rank_worker(rank, world, port, q, stop_at):
-    """One slab per rank: exchange whole planes, then one oracle step."""
+def _rank_worker(rank, world, port, q, stop_at, skip_reduce):
+    """One slab per rank: exchange whole planes, then one oracle step; at the
+    end the totals of the rank's interior planes, summed over the ranks."""
     import torch
     import torch.distributed as dist
     sys.path.insert(0, ROOT)
@@ -99,20 +100,30 @@ def _rank_worker(rank, world, port, q, stop_at):
         f[:, 0] = below.numpy()
         f[:, -1] = above.numpy()
         f = oracle.run(f, TAU, 1, flags=fl, F=F, threads=1)
-    q.put((rank, status, msg, t_fail, f[:, 1:-1] if status == sl.EXCHANGE_OK else None))
+    tot, rstatus, rmsg = None, sl.EXCHANGE_FAILED, "not reached"
+    if status == sl.EXCHANGE_OK:
+        if rank == 1 and skip_reduce:
+            time.sleep(4.0)  # this rank never joins the all-reduce, then leaves
+        else:
+            tot = torch.from_numpy(np.array(oracle.sums(f[:, 1:-1], flags=fl[1:-1], F=F), dtype=np.float64))
+            t0 = time.time()
+            rstatus, rmsg = sl.reduce_ranks(tot, timeout=datetime.timedelta(seconds=1.5))
+            t_fail = time.time() - t0
+            tot = tot.numpy()
+    q.put((rank, status, msg, t_fail, f[:, 1:-1] if status == sl.EXCHANGE_OK else None, tot, rstatus, rmsg))
     q.close()
     q.join_thread()  # flush the result before leaving
     os._exit(0)  # no collective teardown: a failed rank's peer may be gone
 
 
-def _run_ranks(world, stop_at=-1):
+def _run_ranks(world, stop_at=-1, skip_reduce=False):
     import torch.multiprocessing as mp
     import oracle
     oracle.default()  # build once before the ranks start
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
-    procs = [ctx.Process(target=_rank_worker, args=(r, world, port, q, stop_at)) for r in range(world)]
+    procs = [ctx.Process(target=_rank_worker, args=(r, world, port, q, stop_at, skip_reduce)) for r in range(world)]
     for p in procs:
         p.start()
     res = sorted((q.get(timeout=180) for _ in procs), key=lambda r: r[0])
@@ -131,6 +142,13 @@ def test_oracle_slabs_over_gloo_ranks_equal_unsplit(world):
     joined = np.concatenate([r[4] for r in res], axis=1)
     assert joined.shape == ref.shape
     assert np.array_equal(joined, ref)
+    # mass and momentum: every rank holds the all-reduced sum of the slabs'
+    # interior totals, equal to the unsplit totals up to the order of the sums
+    want = np.array(oracle.sums(ref, flags=flags, F=F))
+    assert all(r[6] == slabs.EXCHANGE_OK for r in res), [r[7] for r in res]
+    for r in res:
+        assert np.allclose(r[5], want, rtol=0, atol=1e-12 * want[0]), (r[5], want)
+    assert all(np.array_equal(r[5], res[0][5]) for r in res)
 
 
 def test_rank_that_stops_sending_fails_the_exchange_in_bounded_time():
@@ -139,3 +157,17 @@ def test_rank_that_stops_sending_fails_the_exchange_in_bounded_time():
     assert r0[1] == slabs.EXCHANGE_FAILED, r0[2]
     assert "rank 1" in r0[2]
     assert r0[3] < 10.0  # the 1.5 s bound, not the 60 s process-group timeout
+
+
+def test_rank_that_skips_the_totals_all_reduce_fails_it_in_bounded_time():
+    res = _run_ranks(2, skip_reduce=True)
+    r0 = res[0]
+    assert r0[1] == slabs.EXCHANGE_OK, r0[2]
+    assert r0[6] == slabs.EXCHANGE_FAILED and "all-reduce" in r0[7], r0[7]
+    assert r0[3] < 10.0  # the 1.5 s bound, not the 60 s process-group timeout
+
+
+def test_reduce_ranks_wants_float64():
+    import torch
+    with pytest.raises(TypeError):
+        slabs.reduce_ranks(torch.zeros(4, dtype=torch.float32))

@@ -34,7 +34,8 @@ def _fields(nx, ny, nz, seed, flags_kind):
     return u0, rho0, flags
 
 
-def _pair(storage, k, nx=21, ny=10, nz=14, flags_kind="channel", force="uniform", u_wall=None, steps=9, seed=5):
+def _pair(storage, k, nx=21, ny=10, nz=14, flags_kind="channel", force="uniform", u_wall=None, steps=9, seed=5,
+          totals=False):
     from paper_1112_0850_gb300.lattice import Lattice
     from paper_1112_0850_gb300.slabs import SlabSet
     ensure_built()
@@ -58,9 +59,10 @@ def _pair(storage, k, nx=21, ny=10, nz=14, flags_kind="channel", force="uniform"
     slabs.step(steps)
     a, b = whole.get_state(), slabs.get_state()
     sa, sb = whole.status_word(), slabs.status_word()
+    ta, tb = (whole.reduce(), slabs.totals()) if totals else (None, None)
     whole.close()
     slabs.close()
-    return a, b, sa, sb
+    return (a, b, sa, sb, ta, tb) if totals else (a, b, sa, sb)
 
 
 @pytest.mark.parametrize("storage", STORAGES)
@@ -152,3 +154,54 @@ def test_halo_argument_errors():
     with pytest.raises(LBMError, match="UNSUPPORTED|pull"):
         aa.halo_pack(0, aa.new_halo())
     aa.close()
+
+
+@pytest.mark.parametrize("storage", STORAGES)
+@pytest.mark.parametrize("k,flags_kind,force", [(2, "channel", "uniform"), (3, "random", "field"),
+                                                (4, None, None)])
+def test_slab_totals_equal_unsplit(storage, k, flags_kind, force):
+    """Mass and momentum of a split run: the slabs' interior-plane totals
+    (lbm_reduce_planes) add up to the unsplit lattice's lbm_reduce totals, up
+    to the order of the FP64 sums (the per-cell moments are the same, as the
+    states are bit for bit equal)."""
+    a, b, _, _, ta, tb = _pair(storage, k, nx=17, ny=9, nz=12, flags_kind=flags_kind, force=force, totals=True)
+    assert torch.equal(a, b)
+    assert np.allclose(tb, ta, rtol=0, atol=1e-12 * ta[0]), (tb, ta)
+
+
+def test_reduce_planes_match_per_plane_macros():
+    """FP64 storage: the totals over planes z0 <= z < z1 equal the FP64 sums of
+    lbm_macros' rho and rho u over those planes, for ranges that cut the
+    lattice anywhere; the ranges of a partition add up to lbm_reduce; an empty
+    range gives zeros."""
+    from paper_1112_0850_gb300.lattice import Lattice
+    ensure_built()
+    nx, ny, nz = 13, 9, 11
+    u0, rho0, flags = _fields(nx, ny, nz, 8, "random")
+    lat = Lattice(nx, ny, nz, 0.61, flags=flags, force=(1e-5, 2e-5, -3e-5), storage="f64")
+    lat.init_equilibrium(torch.as_tensor(u0).cuda(), torch.as_tensor(rho0).cuda())
+    lat.step(5)
+    rho, u = lat.macros()
+    rho, u = rho.cpu().numpy(), u.cpu().numpy()
+    fluid = flags == 0
+    for z0, z1 in [(0, nz), (0, 1), (4, 7), (nz - 1, nz), (1, nz - 1)]:
+        got = lat.reduce(z0, z1)
+        r = np.where(fluid, rho, 0.0)[z0:z1]
+        want = np.array([r.sum()] + [(r * u[a, z0:z1]).sum() for a in range(3)])
+        assert np.allclose(got, want, rtol=0, atol=1e-12 * max(want[0], 1.0)), (z0, z1, got, want)
+    parts = lat.reduce(0, 3) + lat.reduce(3, 8) + lat.reduce(8, nz)
+    full = lat.reduce()
+    assert np.allclose(parts, full, rtol=0, atol=1e-12 * full[0])
+    assert np.array_equal(lat.reduce(5, 5), np.zeros(4))
+    lat.close()
+
+
+def test_reduce_planes_argument_errors():
+    from paper_1112_0850_gb300.capi import LBMError
+    from paper_1112_0850_gb300.lattice import Lattice
+    ensure_built()
+    lat = Lattice(8, 5, 6, 0.6, storage="f32")
+    for z0, z1 in [(-1, 3), (2, 7), (4, 3)]:
+        with pytest.raises(LBMError):
+            lat.reduce(z0, z1)
+    lat.close()
