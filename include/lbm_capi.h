@@ -285,6 +285,35 @@ lbm_status lbm_halo_unpack(lbm_ctx *ctx, int side, const void *buf);
  * LBM_ERR_ARG for a null out or planes outside that range. */
 lbm_status lbm_reduce_planes(lbm_ctx *ctx, int z0, int z1, double out[4]);
 
+/* The halo exchange of the adjoint of a z-slab run. The reverse step
+ * (lbm_adjoint_step) reads lambda_i at x + e_i, so the adjoint populations
+ * cross each face the other way: interior plane 1 reads from ghost plane 0
+ * the five with e_z = -1, and plane nz - 2 reads from plane nz - 1 the five
+ * with e_z = +1. Record the forward one step at a time (lbm_step_record with
+ * n = 1, the forward exchange before each), exchange the forward halos before
+ * lbm_adjoint_seed, and before each lbm_adjoint_step(ctx, 1, tape_k, ...):
+ *   lbm_adjoint_halo_pack(slab k, 0, b)  then lbm_adjoint_halo_unpack(slab k - 1, 1, b)
+ *   lbm_adjoint_halo_pack(slab k, 1, b') then lbm_adjoint_halo_unpack(slab k + 1, 0, b')
+ * and lambda on the interior planes (and the gradients from it) is then bit
+ * for bit that of the unsplit lattice.
+ *
+ * lbm_adjoint_halo_bytes: size of one packed buffer, 5 * ny * pitch elements
+ * of real (0 for an invalid context).
+ * lbm_adjoint_halo_pack: copies from the current adjoint lattice the five
+ * outgoing populations of a boundary plane, side 0: plane 1, e_z = +1; side
+ * 1: plane nz - 2, e_z = -1. Layout [5][ny][pitch], directions in increasing
+ * index order.
+ * lbm_adjoint_halo_unpack: writes such a buffer into a ghost plane, side 0:
+ * plane 0 (the e_z = -1 populations packed by the slab below), side 1: plane
+ * nz - 1 (the e_z = +1 ones packed by the slab above), at fluid cells only
+ * (the reverse step reads a solid neighbour's link from the cell itself).
+ * buf: host or device, owned by the caller, as for lbm_halo_pack. Returns
+ * LBM_ERR_STATE before lbm_adjoint_seed, otherwise the errors of
+ * lbm_halo_pack. Asynchronous on cuda_stream for device buffers. */
+size_t lbm_adjoint_halo_bytes(const lbm_ctx *ctx);
+lbm_status lbm_adjoint_halo_pack(lbm_ctx *ctx, int side, void *buf);
+lbm_status lbm_adjoint_halo_unpack(lbm_ctx *ctx, int side, const void *buf);
+
 /* As lbm_step, and also record, for each of the n steps k, the moments the
  * adjoint needs: (rho, u_x, u_y, u_z) of the pre-collision state at step k,
  * u including the F/2 shift. tape: device array of n * tape_bytes_per_step

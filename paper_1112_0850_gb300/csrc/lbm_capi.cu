@@ -738,30 +738,45 @@ size_t lbm_halo_bytes(const lbm_ctx *ctx) {
     return (size_t)5 * ctx->g.ny * ctx->g.pitch * storage_bytes(ctx->storage);
 }
 
+size_t lbm_adjoint_halo_bytes(const lbm_ctx *ctx) {
+    if (check_ctx(ctx)) return 0;
+    return (size_t)5 * ctx->g.ny * ctx->g.pitch * real_size(ctx->storage);
+}
+
 // Pack copies the boundary interior plane's outgoing populations (side 0:
 // plane 1, e_z = -1; side 1: plane nz - 2, e_z = +1); unpack writes the
 // incoming ones into the ghost plane (side 0: plane 0, e_z = +1; side 1:
-// plane nz - 1, e_z = -1) at fluid cells.
-static lbm_status halo_copy(lbm_ctx *ctx, int side, const void *buf, bool unpack) {
+// plane nz - 1, e_z = -1) at fluid cells. The adjoint populations cross the
+// other way (the reverse step reads lambda_i at x + e_i), so for them every
+// e_z sign flips; they are copied from and into the current adjoint lattice.
+static lbm_status halo_copy(lbm_ctx *ctx, int side, const void *buf, bool unpack, bool adjoint) {
     if (check_ctx(ctx)) return LBM_ERR_ARG;
     if (!buf || (side != 0 && side != 1)) return fail(ctx, LBM_ERR_ARG, "bad halo buffer or side");
     if (ctx->g.nz < 3) return fail(ctx, LBM_ERR_ARG, "a slab needs nz >= 3: two ghost planes and an interior");
     if (ctx->pattern != LBM_PATTERN_PULL) return fail(ctx, LBM_ERR_UNSUPPORTED, "halo copies need the pull pattern");
+    if (adjoint && !ctx->lam_valid) return fail(ctx, LBM_ERR_STATE, "lbm_adjoint_seed must come first");
     Staged st(ctx);
-    const int k = st.add(buf, lbm_halo_bytes(ctx), !unpack);
+    const int k = st.add(buf, adjoint ? lbm_adjoint_halo_bytes(ctx) : lbm_halo_bytes(ctx), !unpack);
     lbm_status s = st.prepare();
     if (s) return s;
     const int z = unpack ? (side == 0 ? 0 : ctx->g.nz - 1) : (side == 0 ? 1 : ctx->g.nz - 2);
-    const int dir = (side == 1) != unpack ? 1 : -1;
-    cudaError_t e = launch_halo(ctx->g, state_lat(ctx), (int)storage_bytes(ctx->storage), st.dev(k), z, dir, unpack,
-                                ctx->flags_d, ctx->num_sms, ctx->stream);
+    const int dir = ((side == 1) != unpack) != adjoint ? 1 : -1;
+    void *lat = adjoint ? ctx->lam[ctx->lcur] : state_lat(ctx);
+    const int elem = (int)(adjoint ? real_size(ctx->storage) : storage_bytes(ctx->storage));
+    cudaError_t e = launch_halo(ctx->g, lat, elem, st.dev(k), z, dir, unpack, ctx->flags_d, ctx->num_sms, ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, unpack ? "halo unpack launch" : "halo pack launch");
     return st.finish();
 }
 
-lbm_status lbm_halo_pack(lbm_ctx *ctx, int side, void *buf) { return halo_copy(ctx, side, buf, false); }
+lbm_status lbm_halo_pack(lbm_ctx *ctx, int side, void *buf) { return halo_copy(ctx, side, buf, false, false); }
 
-lbm_status lbm_halo_unpack(lbm_ctx *ctx, int side, const void *buf) { return halo_copy(ctx, side, buf, true); }
+lbm_status lbm_halo_unpack(lbm_ctx *ctx, int side, const void *buf) { return halo_copy(ctx, side, buf, true, false); }
+
+lbm_status lbm_adjoint_halo_pack(lbm_ctx *ctx, int side, void *buf) { return halo_copy(ctx, side, buf, false, true); }
+
+lbm_status lbm_adjoint_halo_unpack(lbm_ctx *ctx, int side, const void *buf) {
+    return halo_copy(ctx, side, buf, true, true);
+}
 
 static lbm_status ensure_lambda(lbm_ctx *ctx) {
     // the reverse step gathers with the push masks (built at create; kept

@@ -194,6 +194,23 @@ class Lattice:
         assert buf.numel() * buf.element_size() >= capi.lib().lbm_halo_bytes(self.handle)
         self._call("lbm_halo_unpack", int(side), buf.data_ptr())
 
+    def new_adjoint_halo(self):
+        """A device buffer for one packed adjoint halo: [5][ny][pitch] of real."""
+        n = capi.lib().lbm_adjoint_halo_bytes(self.handle) // torch.empty(0, dtype=self.real).element_size()
+        return torch.empty(n, dtype=self.real, device="cuda")
+
+    def adjoint_halo_pack(self, side, buf):
+        """Outgoing adjoint populations of plane 1 (side 0, e_z = +1) or nz - 2 (side 1, e_z = -1)."""
+        assert buf.dtype == self.real and buf.is_contiguous()
+        assert buf.numel() * buf.element_size() >= capi.lib().lbm_adjoint_halo_bytes(self.handle)
+        self._call("lbm_adjoint_halo_pack", int(side), buf.data_ptr())
+
+    def adjoint_halo_unpack(self, side, buf):
+        """Incoming adjoint populations into ghost plane 0 (side 0) or nz - 1 (side 1), fluid cells."""
+        assert buf.dtype == self.real and buf.is_contiguous()
+        assert buf.numel() * buf.element_size() >= capi.lib().lbm_adjoint_halo_bytes(self.handle)
+        self._call("lbm_adjoint_halo_unpack", int(side), buf.data_ptr())
+
     def new_tape(self, n):
         return torch.empty(int(n) * self.info.tape_bytes_per_step, dtype=torch.uint8, device="cuda")
 

@@ -13,6 +13,10 @@ populations between a slab's boundary planes and packed buffers.
 - `exchange_ranks`: the same exchange between processes, one slab per rank,
   over torch.distributed point-to-point calls with bounded waits. It moves
   whatever tensors it is given (packed halos, or whole planes).
+- `SlabSet.step_record`, `adjoint_seed`, `adjoint_step`, `adjoint_init_grad`:
+  the discrete adjoint of a split run. The reverse step reads lambda_i at
+  x + e_i, so its exchange (lbm_adjoint_halo_pack / _unpack) moves the five
+  populations of each face the other way, before every reverse step.
 - `SlabSet.totals`, `reduce_ranks`: the FP64 mass and momentum totals of a
   split lattice, each slab summing its interior planes (lbm_reduce_planes)
   and the slabs' sums added on the host, or over ranks by an all-reduce.
@@ -109,6 +113,70 @@ class SlabSet:
         ghosts are refreshed first."""
         self.exchange()
         return torch.cat([lat.get_state(fmt)[:, 1:-1] for lat in self.slabs], dim=1)
+
+    # -- the adjoint: one step at a time, with an exchange before each -------
+    def new_tapes(self, n):
+        """Per slab, a tape for n recorded steps."""
+        return [lat.new_tape(n) for lat in self.slabs]
+
+    def step_record(self, n, tapes):
+        """n steps, recording each slab's moments for the adjoint."""
+        for k in range(int(n)):
+            self.exchange()
+            for lat, tape in zip(self.slabs, tapes):
+                per = lat.info.tape_bytes_per_step
+                lat.step_record(1, tape[k * per:(k + 1) * per])
+
+    def _split(self, a):
+        """Per slab, the planes z0 - 1 .. z1 of a [..][nz][ny][nx] device tensor
+        (None stays None)."""
+        return [None if a is None else with_ghosts(a, z0, z1) for z0, z1 in self.bounds]
+
+    def adjoint_seed(self, dL_du, dL_drho=None):
+        """Start the adjoint at the current state for dL/du (and dL/drho) of
+        the whole lattice. The seed reads each cell's moments, so the forward
+        halos are exchanged first; the slabs' ghost cells get no seed of their
+        own (their entries are overwritten by each reverse exchange)."""
+        self.exchange()
+        self._lam_ex = [(lat.new_adjoint_halo(), lat.new_adjoint_halo()) for lat in self.slabs]
+        self._grad_F = [lat.zeros(3) for lat in self.slabs]
+        for lat, du, dr, gF in zip(self.slabs, self._split(dL_du), self._split(dL_drho), self._grad_F):
+            du[..., 0, :, :] = 0
+            du[..., -1, :, :] = 0
+            if dr is not None:
+                dr[0] = 0
+                dr[-1] = 0
+            lat.adjoint_seed(du, dr, gF)
+
+    def adjoint_exchange(self):
+        """Fill every ghost plane of the adjoint lattices from the neighbouring
+        slab: the e_z = +1 populations of plane 1 go to the slab below, the
+        e_z = -1 ones of plane nz - 2 to the slab above."""
+        k = len(self.slabs)
+        for lat, (down, up) in zip(self.slabs, self._lam_ex):
+            lat.adjoint_halo_pack(0, down)
+            lat.adjoint_halo_pack(1, up)
+        for j, lat in enumerate(self.slabs):
+            lat.adjoint_halo_unpack(1, self._lam_ex[(j + 1) % k][0])
+            lat.adjoint_halo_unpack(0, self._lam_ex[(j - 1) % k][1])
+
+    def adjoint_step(self, n, tapes):
+        """n reverse steps, from the last recorded step back: each an adjoint
+        exchange, then one reverse step of every slab with its tape."""
+        for k in range(int(n) - 1, -1, -1):
+            self.adjoint_exchange()
+            for lat, tape, gF in zip(self.slabs, tapes, self._grad_F):
+                per = lat.info.tape_bytes_per_step
+                lat.adjoint_step(1, tape[k * per:(k + 1) * per], gF)
+
+    def adjoint_init_grad(self, u0, rho0=None):
+        """dL/du0 [3][nz][ny][nx] and dL/dF [3][nz][ny][nx] of the whole
+        lattice (the interior planes of every slab joined), for the u0 and
+        rho0 given to init_equilibrium."""
+        gu = [lat.adjoint_init_grad(u, r)[0]
+              for lat, u, r in zip(self.slabs, self._split(u0), self._split(rho0))]
+        join = lambda parts: torch.cat([p[:, 1:-1] for p in parts], dim=1)
+        return join(gu), join(self._grad_F)
 
     def totals(self):
         """{sum rho, sum rho u_x, sum rho u_y, sum rho u_z} over the fluid

@@ -205,3 +205,82 @@ def test_reduce_planes_argument_errors():
         with pytest.raises(LBMError):
             lat.reduce(z0, z1)
     lat.close()
+
+
+def _adjoint_pair(storage, k, nx=15, ny=9, nz=12, flags_kind="channel", force="uniform", steps=7, seed=9):
+    """dL/du0 and dL/dF of the unsplit lattice and of k slabs, for the loss
+    sum(g_u . u_T + g_rho rho_T) with random g at the fluid cells."""
+    from paper_1112_0850_gb300.lattice import Lattice
+    from paper_1112_0850_gb300.slabs import SlabSet
+    ensure_built()
+    u0, rho0, flags = _fields(nx, ny, nz, seed, flags_kind)
+    real = REAL[storage]
+    rng = np.random.default_rng(seed + 2)
+    fluid = np.ones((nz, ny, nx)) if flags is None else (flags == 0)
+    g_u = torch.as_tensor(rng.standard_normal((3, nz, ny, nx)) * fluid, dtype=real).cuda()
+    g_rho = torch.as_tensor(rng.standard_normal((nz, ny, nx)) * fluid, dtype=real).cuda()
+    F = (2e-5, -1e-5, 3e-5) if force == "uniform" else None
+    Ff = None
+    if force == "field":
+        Ff = torch.as_tensor(lbm_inputs.force_field((nz, ny, nx), 1e-4, seed + 1), dtype=real).cuda()
+    u0t, rho0t = torch.as_tensor(u0, dtype=real).cuda(), torch.as_tensor(rho0, dtype=real).cuda()
+    tau = 0.57
+    whole = Lattice(nx, ny, nz, tau, flags=flags, force=F, storage=storage)
+    slabs = SlabSet(nx, ny, nz, tau, k, flags=flags, force=F, storage=storage)
+    for lat in (whole, slabs):
+        if Ff is not None:
+            lat.set_force_field(Ff)
+        lat.init_equilibrium(u0t, rho0t)
+    tape = whole.new_tape(steps)
+    whole.step_record(steps, tape)
+    gF = whole.zeros(3)
+    whole.adjoint_seed(g_u, g_rho, gF)
+    whole.adjoint_step(steps, tape, gF)
+    gu = whole.adjoint_init_grad(u0t, rho0t)[0]
+    tapes = slabs.new_tapes(steps)
+    slabs.step_record(steps, tapes)
+    slabs.adjoint_seed(g_u, g_rho)
+    slabs.adjoint_step(steps, tapes)
+    gu_s, gF_s = slabs.adjoint_init_grad(u0t, rho0t)
+    whole.close()
+    slabs.close()
+    return gu, gF, gu_s, gF_s
+
+
+@pytest.mark.parametrize("storage", STORAGES)
+@pytest.mark.parametrize("k,flags_kind,force", [(2, "channel", "uniform"), (3, "random", "field"),
+                                                (4, None, None), (6, "channel", "uniform")])
+def test_slab_adjoint_equals_unsplit(storage, k, flags_kind, force):
+    """The adjoint of a split run, with the reverse exchange (the e_z = +1
+    adjoint populations of plane 1 down, the e_z = -1 ones of plane nz - 2
+    up) before every reverse step, gives the unsplit lattice's dL/du0 and
+    dL/dF bit for bit; six slabs of 12 planes are two interior planes each."""
+    gu, gF, gu_s, gF_s = _adjoint_pair(storage, k, flags_kind=flags_kind, force=force)
+    assert float(gu.abs().max()) > 0
+    assert torch.equal(gu, gu_s)
+    assert torch.equal(gF, gF_s)
+
+
+def test_slab_adjoint_exchange_is_needed():
+    """Without the reverse exchange the boundary planes' gradients differ (the
+    test above is not passing by accident)."""
+    from paper_1112_0850_gb300 import slabs as sl
+    saved = sl.SlabSet.adjoint_exchange
+    sl.SlabSet.adjoint_exchange = lambda self: None
+    try:
+        gu, _, gu_s, _ = _adjoint_pair("f64", 2)
+    finally:
+        sl.SlabSet.adjoint_exchange = saved
+    assert not torch.equal(gu, gu_s)
+
+
+def test_adjoint_halo_needs_a_seed():
+    from paper_1112_0850_gb300.capi import LBMError
+    from paper_1112_0850_gb300.lattice import Lattice
+    ensure_built()
+    lat = Lattice(8, 5, 6, 0.6, storage="f32")
+    buf = lat.new_adjoint_halo()
+    assert buf.numel() == 5 * 5 * lat.info.pitch and buf.dtype == torch.float32
+    with pytest.raises(LBMError, match="STATE|seed"):
+        lat.adjoint_halo_pack(0, buf)
+    lat.close()
