@@ -314,6 +314,24 @@ size_t lbm_adjoint_halo_bytes(const lbm_ctx *ctx);
 lbm_status lbm_adjoint_halo_pack(lbm_ctx *ctx, int side, void *buf);
 lbm_status lbm_adjoint_halo_unpack(lbm_ctx *ctx, int side, const void *buf);
 
+/* One step of the cells of planes z0 <= z < z1 only (0 <= z0 <= z1 <= nz),
+ * read from the current state and written to the next lattice; the current
+ * state stays current until a call with last != 0, which runs what follows
+ * the whole step (the link bounce in 16-bit storage with flags) and makes the
+ * next lattice current. A step taken as several such calls, every plane in
+ * exactly one of them and the last with last != 0, equals lbm_step(ctx, 1)
+ * bit for bit. It lets a slab update its interior planes 2 .. nz - 3, which
+ * read no ghost plane, while its halo exchange runs on another stream (see
+ * lbm_set_stream), and then planes 1 and nz - 2. Returns LBM_ERR_ARG for
+ * planes outside that range, LBM_ERR_UNSUPPORTED with LBM_PATTERN_AA.
+ * Asynchronous on cuda_stream. */
+lbm_status lbm_step_planes(lbm_ctx *ctx, int z0, int z1, int last);
+
+/* Make cuda_stream (a cudaStream_t; NULL = default stream) the stream every
+ * later call of this context enqueues on. Work already enqueued on the
+ * previous stream is not waited for: order the two streams with events. */
+lbm_status lbm_set_stream(lbm_ctx *ctx, void *cuda_stream);
+
 /* As lbm_step, and also record, for each of the n steps k, the moments the
  * adjoint needs: (rho, u_x, u_y, u_z) of the pre-collision state at step k,
  * u including the F/2 shift. tape: device array of n * tape_bytes_per_step

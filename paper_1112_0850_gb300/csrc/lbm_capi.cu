@@ -613,6 +613,40 @@ lbm_status lbm_step(lbm_ctx *ctx, int n) {
     return LBM_OK;
 }
 
+// The rows of launch L that lie in planes z0 <= z < z1 (none: nzr = 0).
+static void clip_planes(RowLaunch &L, int z0, int z1) {
+    const int a = L.z0 > z0 ? L.z0 : z0, b = L.z0 + L.nzr < z1 ? L.z0 + L.nzr : z1;
+    L.z0 = a;
+    L.nzr = b > a ? b - a : 0;
+}
+
+lbm_status lbm_step_planes(lbm_ctx *ctx, int z0, int z1, int last) {
+    if (check_ctx(ctx)) return LBM_ERR_ARG;
+    if (z0 < 0 || z1 < z0 || z1 > ctx->g.nz) return fail(ctx, LBM_ERR_ARG, "planes must satisfy 0 <= z0 <= z1 <= nz");
+    if (ctx->pattern != LBM_PATTERN_PULL) return fail(ctx, LBM_ERR_UNSUPPORTED, "plane steps need the pull pattern");
+    Dev d = make_dev(ctx);
+    cudaError_t e = cudaSuccess;
+    Dev part = d;
+    clip_planes(part.P, z0, z1);
+    clip_planes(part.PF, z0, z1);
+    part.link_max = 0;  // the link bounce follows the whole step, below
+    if (part.P.nzr > 0 && part.PF.nzr > 0) e = step_from(ctx, part, ctx->cur, nullptr);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "stream-collide (planes) launch");
+    if (last) {
+        e = LBM_DISPATCH(ctx, bounce(d, ctx->lat[ctx->cur ^ 1]));
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "bounce launch");
+        ctx->cur ^= 1;
+        ctx->steps_done++;
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_set_stream(lbm_ctx *ctx, void *cuda_stream) {
+    if (check_ctx(ctx)) return LBM_ERR_ARG;
+    ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+    return LBM_OK;
+}
+
 lbm_status lbm_step_record(lbm_ctx *ctx, int n, void *tape) {
     if (check_ctx(ctx)) return LBM_ERR_ARG;
     if (n < 0) return fail(ctx, LBM_ERR_ARG, "n must be >= 0");

@@ -994,6 +994,15 @@ cudaError_t Ops<S>::step(const Dev &d, const void *src, void *dst, void *tape) {
 }
 
 template <int S>
+cudaError_t Ops<S>::bounce(const Dev &d, void *dst) {
+    if (!d.flags || !LinkBounce<S>::value || d.link_max == 0) return cudaSuccess;
+    const int per_block = 256 * LINKS_PER_THREAD;
+    k_bounce<S><<<dim3((d.link_max + per_block - 1) / per_block, Q - 1), 256, 0, d.stream>>>(
+        d, static_cast<typename Stor<S>::T *>(dst));
+    return cudaGetLastError();
+}
+
+template <int S>
 cudaError_t Ops<S>::step_reduce(const Dev &d, const void *src, void *dst, double *partials, double *out) {
     typedef typename Stor<S>::T T;
     if (d.flags && !d.mask) return cudaErrorInvalidValue;

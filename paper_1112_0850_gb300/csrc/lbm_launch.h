@@ -84,6 +84,9 @@ template <int S> struct Ops {
     static cudaError_t get_state(const Dev &d, const void *lat, void *dst, int fmt);
     static cudaError_t set_state(const Dev &d, void *lat, const void *src, int fmt);
     static cudaError_t macros(const Dev &d, const void *lat, void *rho, void *u);
+    // The link bounce of a step alone (link form with flags; no-op otherwise):
+    // the solid slots of dst the next step gathers.
+    static cudaError_t bounce(const Dev &d, void *dst);
     // Totals over the fluid cells of planes z0 <= z < z1. partials: RED_BLOCKS * 4
     // doubles of scratch; out: 4 doubles (device).
     static cudaError_t reduce(const Dev &d, const void *lat, int z0, int z1, double *partials, double *out);

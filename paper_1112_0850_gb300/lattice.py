@@ -141,6 +141,17 @@ class Lattice:
         self._call("lbm_macros", self._ptr(rho, self.real, self.shape), self._ptr(u, self.real, (3,) + self.shape))
         return rho, u
 
+    def step_planes(self, z0, z1, last):
+        """One step of planes z0 <= z < z1 only; last=True completes the step
+        (every plane in exactly one call per step)."""
+        self._call("lbm_step_planes", int(z0), int(z1), 1 if last else 0)
+
+    def set_stream(self, stream):
+        """Enqueue every later call on `stream` (a torch.cuda.Stream); order it
+        against the previous stream with events."""
+        self._call("lbm_set_stream", ctypes.c_void_p(stream.cuda_stream))
+        self.stream = stream
+
     def reduce(self, z0=None, z1=None):
         """{sum rho, sum rho u} over the fluid cells, in FP64; with z0, z1 over
         planes z0 <= z < z1 only (a slab's interior planes: 1, nz - 1)."""

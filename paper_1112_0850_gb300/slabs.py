@@ -57,12 +57,17 @@ class SlabSet:
 
     Slab j is a `Lattice` of nz_j + 2 planes: the interior planes of
     `split_planes(nz, k)[j]` between two ghost planes, created with the flags
-    of those planes. `step` exchanges the halos, then steps every slab once.
-    Keyword arguments go to `Lattice` (storage, model, ...; pull pattern)."""
+    of those planes. `step` exchanges the halos, then steps every slab once;
+    with overlap=True the exchange runs on a second stream while each slab
+    updates its interior planes 2 .. nz - 3 (which read no ghost plane), and
+    planes 1 and nz - 2 follow it (lbm_step_planes). Keyword arguments go to
+    `Lattice` (storage, model, ...; pull pattern)."""
 
-    def __init__(self, nx, ny, nz, tau, k, flags=None, force=None, **kw):
+    def __init__(self, nx, ny, nz, tau, k, flags=None, force=None, overlap=False, **kw):
         from .lattice import Lattice
         self.shape = (nz, ny, nx)
+        self.overlap = bool(overlap)
+        self._side = None
         self.bounds = split_planes(nz, k)
         self.slabs = []
         try:
@@ -101,10 +106,44 @@ class SlabSet:
             lat.halo_unpack(1, self.down[(j + 1) % k])
 
     def step(self, n=1):
+        if self.overlap:
+            return self._step_overlapped(n)
         for _ in range(int(n)):
             self.exchange()
             for lat in self.slabs:
                 lat.step(1)
+
+    def _step_overlapped(self, n):
+        main = self.stream
+        if self._side is None:
+            self._side = torch.cuda.Stream(device=main.device)
+            self._ready, self._halo_done = torch.cuda.Event(), torch.cuda.Event()
+        side = self._side
+        for _ in range(int(n)):
+            self._ready.record(main)  # the current state is complete
+            for lat in self.slabs:
+                nzl = lat.shape[0]
+                if nzl - 2 > 2:
+                    lat.step_planes(2, nzl - 2, False)
+            # the exchange reads planes 1 and nz - 2 of the current state and
+            # writes its ghost planes, neither of which the interior writes
+            side.wait_event(self._ready)
+            for lat in self.slabs:
+                lat.set_stream(side)
+            try:
+                self.exchange()
+            finally:
+                for lat in self.slabs:
+                    lat.set_stream(main)
+            self._halo_done.record(side)
+            main.wait_event(self._halo_done)
+            for lat in self.slabs:
+                nzl = lat.shape[0]
+                if nzl - 2 > 1:
+                    lat.step_planes(1, 2, False)
+                    lat.step_planes(nzl - 2, nzl - 1, True)
+                else:  # one interior plane
+                    lat.step_planes(1, 2, True)
 
     def get_state(self, fmt=None):
         """The interior planes of all slabs joined: [19][nz][ny][nx]. The

@@ -35,7 +35,7 @@ def _fields(nx, ny, nz, seed, flags_kind):
 
 
 def _pair(storage, k, nx=21, ny=10, nz=14, flags_kind="channel", force="uniform", u_wall=None, steps=9, seed=5,
-          totals=False):
+          totals=False, overlap=False):
     from paper_1112_0850_gb300.lattice import Lattice
     from paper_1112_0850_gb300.slabs import SlabSet
     ensure_built()
@@ -47,7 +47,7 @@ def _pair(storage, k, nx=21, ny=10, nz=14, flags_kind="channel", force="uniform"
         Ff = torch.as_tensor(lbm_inputs.force_field((nz, ny, nx), 1e-4, seed + 1), dtype=real).cuda()
     tau = 0.56
     whole = Lattice(nx, ny, nz, tau, flags=flags, force=F, storage=storage)
-    slabs = SlabSet(nx, ny, nz, tau, k, flags=flags, force=F, storage=storage)
+    slabs = SlabSet(nx, ny, nz, tau, k, flags=flags, force=F, storage=storage, overlap=overlap)
     u0t, rho0t = torch.as_tensor(u0, dtype=real).cuda(), torch.as_tensor(rho0, dtype=real).cuda()
     for lat in (whole, slabs):
         if Ff is not None:
@@ -284,3 +284,60 @@ def test_adjoint_halo_needs_a_seed():
     with pytest.raises(LBMError, match="STATE|seed"):
         lat.adjoint_halo_pack(0, buf)
     lat.close()
+
+
+@pytest.mark.parametrize("storage", STORAGES)
+@pytest.mark.parametrize("k,nz,flags_kind,force", [(2, 14, "channel", "uniform"), (3, 11, "random", "field"),
+                                                   (4, 12, None, None), (6, 12, "channel", "uniform"),
+                                                   (5, 5, "channel", "uniform")])
+def test_slabs_overlapped_exchange_equal_unsplit(storage, k, nz, flags_kind, force):
+    """The exchange on a second stream while the interior planes update, then
+    planes 1 and nz - 2: still the unsplit lattice bit for bit, down to slabs
+    of two and of one interior plane."""
+    a, b, sa, sb = _pair(storage, k, nx=17, ny=9, nz=nz, flags_kind=flags_kind, force=force, overlap=True)
+    assert torch.equal(a, b), (storage, k)
+    assert sa == sb == 0
+
+
+@pytest.mark.parametrize("storage", STORAGES)
+@pytest.mark.parametrize("flags_kind", ["channel", "random", None])
+def test_step_planes_equal_step(storage, flags_kind):
+    """A step taken as plane windows (any order, an empty window, windows
+    outside the fluid box of a walled channel) equals lbm_step bit for bit."""
+    from paper_1112_0850_gb300.lattice import Lattice
+    ensure_built()
+    nx, ny, nz = 19, 10, 13
+    u0, rho0, flags = _fields(nx, ny, nz, 4, flags_kind)
+    if flags is not None:
+        flags[:2] = 1  # two solid planes: a window there is empty after clipping to the fluid box
+    u0 = u0 * (flags == 0) if flags is not None else u0
+    real = REAL[storage]
+    F = (1e-5, -2e-5, 3e-5)
+    lats = [Lattice(nx, ny, nz, 0.58, flags=flags, force=F, storage=storage) for _ in range(2)]
+    for lat in lats:
+        lat.init_equilibrium(torch.as_tensor(u0, dtype=real).cuda(), torch.as_tensor(rho0, dtype=real).cuda())
+    windows = [[(0, 2), (7, 13), (2, 5), (5, 5), (5, 7)], [(0, 13)], [(12, 13), (0, 12)]]
+    for step in range(6):
+        lats[0].step(1)
+        w = windows[step % len(windows)]
+        for j, (z0, z1) in enumerate(w):
+            lats[1].step_planes(z0, z1, j == len(w) - 1)
+    a, b = lats[0].get_state(), lats[1].get_state()
+    assert torch.equal(a, b)
+    for lat in lats:
+        lat.close()
+
+
+def test_step_planes_argument_errors():
+    from paper_1112_0850_gb300.capi import LBMError
+    from paper_1112_0850_gb300.lattice import Lattice
+    ensure_built()
+    lat = Lattice(8, 5, 6, 0.6, storage="f32")
+    for z0, z1 in [(-1, 3), (2, 7), (4, 3)]:
+        with pytest.raises(LBMError):
+            lat.step_planes(z0, z1, True)
+    lat.close()
+    aa = Lattice(8, 5, 6, 0.6, storage="f32", pattern="aa")
+    with pytest.raises(LBMError, match="UNSUPPORTED|pull"):
+        aa.step_planes(0, 6, True)
+    aa.close()
