@@ -322,10 +322,15 @@ lbm_status lbm_adjoint_halo_unpack(lbm_ctx *ctx, int side, const void *buf);
  * exactly one of them and the last with last != 0, equals lbm_step(ctx, 1)
  * bit for bit. It lets a slab update its interior planes 2 .. nz - 3, which
  * read no ghost plane, while its halo exchange runs on another stream (see
- * lbm_set_stream), and then planes 1 and nz - 2. Returns LBM_ERR_ARG for
- * planes outside that range, LBM_ERR_UNSUPPORTED with LBM_PATTERN_AA.
- * Asynchronous on cuda_stream. */
-lbm_status lbm_step_planes(lbm_ctx *ctx, int z0, int z1, int last);
+ * lbm_set_stream), and then planes 1 and nz - 2; a slab's ghost planes need
+ * no update, as the next exchange refills what its interior reads there.
+ * out nullable: 4 doubles that receive the totals of lbm_reduce_planes(z0,
+ * z1) for the current state, summed inside this call's step as
+ * lbm_step_reduce does (the same totals up to the order of the FP64 sums):
+ * host (the call synchronizes) or device (asynchronous). Returns LBM_ERR_ARG
+ * for planes outside that range, LBM_ERR_UNSUPPORTED with LBM_PATTERN_AA.
+ * Asynchronous on cuda_stream unless out is a host array. */
+lbm_status lbm_step_planes(lbm_ctx *ctx, int z0, int z1, int last, double *out);
 
 /* Make cuda_stream (a cudaStream_t; NULL = default stream) the stream every
  * later call of this context enqueues on. Work already enqueued on the

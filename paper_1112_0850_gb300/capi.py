@@ -66,7 +66,7 @@ PROTOTYPES = {
     "lbm_halo_pack": (_st, [_vp, _i, _vp]),
     "lbm_halo_unpack": (_st, [_vp, _i, _vp]),
     "lbm_reduce_planes": (_st, [_vp, _i, _i, _vp]),
-    "lbm_step_planes": (_st, [_vp, _i, _i, _i]),
+    "lbm_step_planes": (_st, [_vp, _i, _i, _i, _vp]),
     "lbm_set_stream": (_st, [_vp, _vp]),
     "lbm_adjoint_halo_bytes": (ctypes.c_size_t, [_vp]),
     "lbm_adjoint_halo_pack": (_st, [_vp, _i, _vp]),

@@ -613,34 +613,6 @@ lbm_status lbm_step(lbm_ctx *ctx, int n) {
     return LBM_OK;
 }
 
-// The rows of launch L that lie in planes z0 <= z < z1 (none: nzr = 0).
-static void clip_planes(RowLaunch &L, int z0, int z1) {
-    const int a = L.z0 > z0 ? L.z0 : z0, b = L.z0 + L.nzr < z1 ? L.z0 + L.nzr : z1;
-    L.z0 = a;
-    L.nzr = b > a ? b - a : 0;
-}
-
-lbm_status lbm_step_planes(lbm_ctx *ctx, int z0, int z1, int last) {
-    if (check_ctx(ctx)) return LBM_ERR_ARG;
-    if (z0 < 0 || z1 < z0 || z1 > ctx->g.nz) return fail(ctx, LBM_ERR_ARG, "planes must satisfy 0 <= z0 <= z1 <= nz");
-    if (ctx->pattern != LBM_PATTERN_PULL) return fail(ctx, LBM_ERR_UNSUPPORTED, "plane steps need the pull pattern");
-    Dev d = make_dev(ctx);
-    cudaError_t e = cudaSuccess;
-    Dev part = d;
-    clip_planes(part.P, z0, z1);
-    clip_planes(part.PF, z0, z1);
-    part.link_max = 0;  // the link bounce follows the whole step, below
-    if (part.P.nzr > 0 && part.PF.nzr > 0) e = step_from(ctx, part, ctx->cur, nullptr);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "stream-collide (planes) launch");
-    if (last) {
-        e = LBM_DISPATCH(ctx, bounce(d, ctx->lat[ctx->cur ^ 1]));
-        if (e != cudaSuccess) return cuda_fail(ctx, e, "bounce launch");
-        ctx->cur ^= 1;
-        ctx->steps_done++;
-    }
-    return LBM_OK;
-}
-
 lbm_status lbm_set_stream(lbm_ctx *ctx, void *cuda_stream) {
     if (check_ctx(ctx)) return LBM_ERR_ARG;
     ctx->stream = static_cast<cudaStream_t>(cuda_stream);
@@ -696,29 +668,45 @@ lbm_status lbm_reduce(lbm_ctx *ctx, double out[4]) {
     return lbm_reduce_planes(ctx, 0, ctx->g.nz, out);
 }
 
+// Scratch of the fused step-reduce: one partial per block of either launch
+// mapping of the whole step (a plane window's launch has fewer blocks).
+static lbm_status ensure_step_partials(lbm_ctx *ctx, const Dev &d) {
+    const size_t nb_rows = (size_t)d.P.nxb * d.P.nyb * d.P.nzr, nb_flat = (size_t)d.PF.nxb * d.PF.nyb * d.PF.nzr;
+    const size_t nb = nb_rows > nb_flat ? nb_rows : nb_flat;
+    if (ctx->step_partials_n >= nb) return LBM_OK;
+    if (ctx->step_partials) {
+        cudaStreamSynchronize(ctx->stream);
+        cudaFree(ctx->step_partials);
+    }
+    ctx->step_partials = nullptr;
+    ctx->step_partials_n = 0;
+    cudaError_t e = cudaMalloc((void **)&ctx->step_partials, nb * 4 * sizeof(double));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        ctx->step_partials = nullptr;
+        return fail(ctx, LBM_ERR_OOM, "cannot allocate the fused-reduction partials");
+    }
+    ctx->step_partials_n = nb;
+    return LBM_OK;
+}
+
+// The 4 totals in red_out to out: device (asynchronous) or host (synchronizes).
+static lbm_status copy_totals(lbm_ctx *ctx, double *out) {
+    const bool dev = is_device_ptr(out);
+    cudaError_t e = cudaMemcpyAsync(out, ctx->red_out, 4 * sizeof(double),
+                                    dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess && !dev) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "totals copy");
+    return LBM_OK;
+}
+
 lbm_status lbm_step_reduce(lbm_ctx *ctx, int n, double *out) {
     if (check_ctx(ctx)) return LBM_ERR_ARG;
     if (n < 1 || !out) return fail(ctx, LBM_ERR_ARG, "n must be >= 1 and out is required");
     cudaError_t e;
     Dev d = make_dev(ctx);
-    // one partial per block of either launch mapping of the step
-    const size_t nb_rows = (size_t)d.P.nxb * d.P.nyb * d.P.nzr, nb_flat = (size_t)d.PF.nxb * d.PF.nyb * d.PF.nzr;
-    const size_t nb = nb_rows > nb_flat ? nb_rows : nb_flat;
-    if (ctx->step_partials_n < nb) {
-        if (ctx->step_partials) {
-            cudaStreamSynchronize(ctx->stream);
-            cudaFree(ctx->step_partials);
-        }
-        ctx->step_partials = nullptr;
-        ctx->step_partials_n = 0;
-        e = cudaMalloc((void **)&ctx->step_partials, nb * 4 * sizeof(double));
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            ctx->step_partials = nullptr;
-            return fail(ctx, LBM_ERR_OOM, "cannot allocate the fused-reduction partials");
-        }
-        ctx->step_partials_n = nb;
-    }
+    lbm_status s0 = ensure_step_partials(ctx, d);
+    if (s0) return s0;
     if (ctx->pattern == LBM_PATTERN_AA)
         e = LBM_AA_DISPATCH(ctx, step_reduce(d, ctx->lat[0], ctx->cur, ctx->step_partials, ctx->red_out));
     else
@@ -729,12 +717,46 @@ lbm_status lbm_step_reduce(lbm_ctx *ctx, int n, double *out) {
     ctx->steps_done++;
     lbm_status s = lbm_step(ctx, n - 1);
     if (s) return s;
-    const bool dev = is_device_ptr(out);
-    e = cudaMemcpyAsync(out, ctx->red_out, 4 * sizeof(double), dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
-                        ctx->stream);
-    if (e == cudaSuccess && !dev) e = cudaStreamSynchronize(ctx->stream);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "totals copy");
-    return LBM_OK;
+    return copy_totals(ctx, out);
+}
+
+// The rows of launch L that lie in planes z0 <= z < z1 (none: nzr = 0).
+static void clip_planes(RowLaunch &L, int z0, int z1) {
+    const int a = L.z0 > z0 ? L.z0 : z0, b = L.z0 + L.nzr < z1 ? L.z0 + L.nzr : z1;
+    L.z0 = a;
+    L.nzr = b > a ? b - a : 0;
+}
+
+lbm_status lbm_step_planes(lbm_ctx *ctx, int z0, int z1, int last, double *out) {
+    if (check_ctx(ctx)) return LBM_ERR_ARG;
+    if (z0 < 0 || z1 < z0 || z1 > ctx->g.nz) return fail(ctx, LBM_ERR_ARG, "planes must satisfy 0 <= z0 <= z1 <= nz");
+    if (ctx->pattern != LBM_PATTERN_PULL) return fail(ctx, LBM_ERR_UNSUPPORTED, "plane steps need the pull pattern");
+    Dev d = make_dev(ctx);
+    Dev part = d;
+    clip_planes(part.P, z0, z1);
+    clip_planes(part.PF, z0, z1);
+    part.link_max = 0;  // the link bounce follows the whole step, below
+    const bool any = part.P.nzr > 0 && part.PF.nzr > 0;
+    cudaError_t e = cudaSuccess;
+    if (out) {
+        lbm_status s = ensure_step_partials(ctx, d);
+        if (s) return s;
+        if (any)
+            e = LBM_DISPATCH(ctx, step_reduce(part, ctx->lat[ctx->cur], ctx->lat[ctx->cur ^ 1], ctx->step_partials,
+                                              ctx->red_out));
+        else
+            e = cudaMemsetAsync(ctx->red_out, 0, 4 * sizeof(double), ctx->stream);
+    } else if (any) {
+        e = step_from(ctx, part, ctx->cur, nullptr);
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "stream-collide (planes) launch");
+    if (last) {
+        e = LBM_DISPATCH(ctx, bounce(d, ctx->lat[ctx->cur ^ 1]));
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "bounce launch");
+        ctx->cur ^= 1;
+        ctx->steps_done++;
+    }
+    return out ? copy_totals(ctx, out) : LBM_OK;
 }
 
 lbm_status lbm_get_state(lbm_ctx *ctx, void *dst, lbm_storage fmt) {

@@ -141,10 +141,21 @@ class Lattice:
         self._call("lbm_macros", self._ptr(rho, self.real, self.shape), self._ptr(u, self.real, (3,) + self.shape))
         return rho, u
 
-    def step_planes(self, z0, z1, last):
+    def step_planes(self, z0, z1, last, totals=False, out=None):
         """One step of planes z0 <= z < z1 only; last=True completes the step
-        (every plane in exactly one call per step)."""
-        self._call("lbm_step_planes", int(z0), int(z1), 1 if last else 0)
+        (every plane in exactly one call per step). With totals=True (host
+        numpy result) or a device float64 tensor `out` (asynchronous), also
+        the totals of reduce(z0, z1) for the current state, summed inside the
+        step."""
+        if out is not None:
+            assert out.is_cuda and out.dtype == torch.float64 and out.numel() >= 4
+            self._call("lbm_step_planes", int(z0), int(z1), 1 if last else 0, ctypes.c_void_p(out.data_ptr()))
+            return out
+        if totals:
+            res = (ctypes.c_double * 4)()
+            self._call("lbm_step_planes", int(z0), int(z1), 1 if last else 0, res)
+            return np.array(res[:])
+        self._call("lbm_step_planes", int(z0), int(z1), 1 if last else 0, None)
 
     def set_stream(self, stream):
         """Enqueue every later call on `stream` (a torch.cuda.Stream); order it

@@ -17,9 +17,10 @@ populations between a slab's boundary planes and packed buffers.
   the discrete adjoint of a split run. The reverse step reads lambda_i at
   x + e_i, so its exchange (lbm_adjoint_halo_pack / _unpack) moves the five
   populations of each face the other way, before every reverse step.
-- `SlabSet.totals`, `reduce_ranks`: the FP64 mass and momentum totals of a
-  split lattice, each slab summing its interior planes (lbm_reduce_planes)
-  and the slabs' sums added on the host, or over ranks by an all-reduce.
+- `SlabSet.totals`, `SlabSet.step_reduce`, `reduce_ranks`: the FP64 mass and
+  momentum totals of a split lattice, each slab summing its interior planes
+  (lbm_reduce_planes, or inside the step with lbm_step_planes) and the slabs'
+  sums added on the host, or over ranks by an all-reduce.
 """
 import datetime
 
@@ -216,6 +217,20 @@ class SlabSet:
               for lat, u, r in zip(self.slabs, self._split(u0), self._split(rho0))]
         join = lambda parts: torch.cat([p[:, 1:-1] for p in parts], dim=1)
         return join(gu), join(self._grad_F)
+
+    def step_reduce(self, n=1):
+        """The totals of `totals()` for the current state, then n >= 1 steps:
+        after an exchange, each slab's first step covers its interior planes
+        only and sums their totals inside the step (lbm_step_planes with out);
+        the slabs' sums are added on the host in slab order."""
+        if int(n) < 1:
+            raise ValueError("n must be >= 1")
+        self.exchange()
+        out = np.zeros(4)
+        for lat in self.slabs:
+            out += lat.step_planes(1, lat.shape[0] - 1, True, totals=True)
+        self.step(int(n) - 1)
+        return out
 
     def totals(self):
         """{sum rho, sum rho u_x, sum rho u_y, sum rho u_z} over the fluid

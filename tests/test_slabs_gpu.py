@@ -341,3 +341,65 @@ def test_step_planes_argument_errors():
     with pytest.raises(LBMError, match="UNSUPPORTED|pull"):
         aa.step_planes(0, 6, True)
     aa.close()
+
+
+@pytest.mark.parametrize("storage", STORAGES)
+@pytest.mark.parametrize("flags_kind", ["channel", None])
+def test_step_planes_fused_totals(storage, flags_kind):
+    """Totals summed inside a plane window's step equal lbm_reduce_planes over
+    the same planes taken before it (to the order of the FP64 sums), on the
+    host and into a device array; an empty window gives zeros; the stepped
+    state still equals lbm_step's bit for bit."""
+    from paper_1112_0850_gb300.lattice import Lattice
+    ensure_built()
+    nx, ny, nz = 17, 9, 12
+    u0, rho0, flags = _fields(nx, ny, nz, 6, flags_kind)
+    real = REAL[storage]
+    lats = [Lattice(nx, ny, nz, 0.6, flags=flags, force=(2e-5, 0.0, -1e-5), storage=storage) for _ in range(2)]
+    for lat in lats:
+        lat.init_equilibrium(torch.as_tensor(u0, dtype=real).cuda(), torch.as_tensor(rho0, dtype=real).cuda())
+    dev_out = torch.zeros(4, dtype=torch.float64, device="cuda")
+    for step, windows in enumerate([[(0, 5), (5, 12)], [(3, 3), (0, 3), (3, 12)], [(1, 11), (0, 1), (11, 12)]]):
+        lats[0].step(1)
+        for j, (z0, z1) in enumerate(windows):
+            want = lats[1].reduce(z0, z1)
+            last = j == len(windows) - 1
+            if j % 2:
+                got = lats[1].step_planes(z0, z1, last, out=dev_out).cpu().numpy()
+            else:
+                got = lats[1].step_planes(z0, z1, last, totals=True)
+            if z0 == z1:
+                assert np.array_equal(got, np.zeros(4))
+            else:
+                assert np.allclose(got, want, rtol=0, atol=1e-12 * max(want[0], 1.0)), (step, z0, z1, got, want)
+    assert torch.equal(lats[0].get_state(), lats[1].get_state())
+    for lat in lats:
+        lat.close()
+
+
+@pytest.mark.parametrize("storage", STORAGES)
+@pytest.mark.parametrize("k", [2, 3])
+def test_slab_step_reduce_equals_unsplit(storage, k):
+    """SlabSet.step_reduce: the totals of the split lattice summed inside the
+    first step (interior planes only) equal the unsplit lbm_step_reduce
+    totals, and the states after the steps are equal bit for bit."""
+    from paper_1112_0850_gb300.lattice import Lattice
+    from paper_1112_0850_gb300.slabs import SlabSet
+    ensure_built()
+    nx, ny, nz = 17, 9, 12
+    u0, rho0, flags = _fields(nx, ny, nz, 7, "channel")
+    real = REAL[storage]
+    F = (2e-5, -1e-5, 3e-5)
+    whole = Lattice(nx, ny, nz, 0.57, flags=flags, force=F, storage=storage)
+    slabs = SlabSet(nx, ny, nz, 0.57, k, flags=flags, force=F, storage=storage)
+    u0t, rho0t = torch.as_tensor(u0, dtype=real).cuda(), torch.as_tensor(rho0, dtype=real).cuda()
+    for lat in (whole, slabs):
+        lat.init_equilibrium(u0t, rho0t)
+    whole.step(3)
+    slabs.step(3)
+    ta = whole.step_reduce(4)
+    tb = slabs.step_reduce(4)
+    assert np.allclose(tb, ta, rtol=0, atol=1e-12 * ta[0]), (tb, ta)
+    assert torch.equal(whole.get_state(), slabs.get_state())
+    whole.close()
+    slabs.close()
