@@ -43,6 +43,20 @@ def ghost_planes(nz, z0, z1):
     return [(z0 - 1) % nz] + list(range(z0, z1)) + [z1 % nz]
 
 
+def overlap_windows(nz):
+    """The plane windows of one overlapped step of a slab of nz planes (ghosts
+    0 and nz - 1): (interior, boundary). The interior windows read no ghost
+    plane (planes 2 .. nz - 3 gather from planes 1 .. nz - 2), so they run
+    while the exchange fills the ghosts; the boundary windows (planes 1 and
+    nz - 2) follow it, the last of them completing the step. Together they
+    cover planes 1 .. nz - 2 once each."""
+    if nz < 3:
+        raise ValueError("a slab needs nz >= 3")
+    interior = [(2, nz - 2)] if nz - 2 > 2 else []
+    boundary = [(1, 2), (nz - 2, nz - 1)] if nz - 2 > 1 else [(1, 2)]
+    return interior, boundary
+
+
 def with_ghosts(a, z0, z1, axis=-3):
     """Planes z0 - 1 .. z1 of field `a` along `axis` (z of [..][nz][ny][nx]),
     periodic; numpy array or torch tensor, returned contiguous."""
@@ -123,9 +137,8 @@ class SlabSet:
         for _ in range(int(n)):
             self._ready.record(main)  # the current state is complete
             for lat in self.slabs:
-                nzl = lat.shape[0]
-                if nzl - 2 > 2:
-                    lat.step_planes(2, nzl - 2, False)
+                for z0, z1 in overlap_windows(lat.shape[0])[0]:
+                    lat.step_planes(z0, z1, False)
             # the exchange reads planes 1 and nz - 2 of the current state and
             # writes its ghost planes, neither of which the interior writes
             side.wait_event(self._ready)
@@ -139,12 +152,9 @@ class SlabSet:
             self._halo_done.record(side)
             main.wait_event(self._halo_done)
             for lat in self.slabs:
-                nzl = lat.shape[0]
-                if nzl - 2 > 1:
-                    lat.step_planes(1, 2, False)
-                    lat.step_planes(nzl - 2, nzl - 1, True)
-                else:  # one interior plane
-                    lat.step_planes(1, 2, True)
+                boundary = overlap_windows(lat.shape[0])[1]
+                for j, (z0, z1) in enumerate(boundary):
+                    lat.step_planes(z0, z1, j == len(boundary) - 1)
 
     def get_state(self, fmt=None):
         """The interior planes of all slabs joined: [19][nz][ny][nx]. The

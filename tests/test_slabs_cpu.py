@@ -69,6 +69,24 @@ def test_with_ghosts_wraps_periodically():
     assert slabs.ghost_planes(5, 0, 5) == [4, 0, 1, 2, 3, 4, 0]
 
 
+@pytest.mark.parametrize("nz", [3, 4, 5, 6, 7, 12, 258])
+def test_overlap_windows_cover_interior_once_and_spare_the_ghosts(nz):
+    interior, boundary = slabs.overlap_windows(nz)
+    planes = [z for z0, z1 in interior + boundary for z in range(z0, z1)]
+    assert sorted(planes) == list(range(1, nz - 1))  # every interior plane once, no ghost
+    for z0, z1 in interior:
+        # pull: plane z reads planes z - 1 .. z + 1, none of them a ghost
+        assert z0 - 1 >= 1 and z1 <= nz - 2
+    for z0, z1 in boundary:
+        assert z1 - z0 == 1 and z0 in (1, nz - 2)
+    assert boundary  # the step completes after the exchange
+
+
+def test_overlap_windows_need_a_slab():
+    with pytest.raises(ValueError):
+        slabs.overlap_windows(2)
+
+
 def _rank_worker(rank, world, port, q, stop_at, skip_reduce):
     """One slab per rank: exchange whole planes, then one oracle step; at the
     end the totals of the rank's interior planes, summed over the ranks."""
