@@ -189,3 +189,64 @@ def test_reduce_ranks_wants_float64():
     import torch
     with pytest.raises(TypeError):
         slabs.reduce_ranks(torch.zeros(4, dtype=torch.float32))
+
+
+class _FakeLattice:
+    """Stands in for Lattice in SlabSet's host wiring: a pack writes (slab,
+    side, kind) into the buffer, an unpack records what it received."""
+    count = 0
+
+    def __init__(self, nx, ny, nz, tau, flags=None, force=None, **kw):
+        import torch
+        self.id = _FakeLattice.count
+        _FakeLattice.count += 1
+        self.shape = (nz, ny, nx)
+        self.stream = None
+        self.got = {}
+        self._t = torch
+
+    def new_halo(self):
+        return self._t.zeros(3)
+
+    new_adjoint_halo = new_halo
+
+    def _pack(self, kind, side, buf):
+        buf[:] = self._t.tensor([self.id, side, kind], dtype=buf.dtype)
+
+    def halo_pack(self, side, buf):
+        self._pack(0, side, buf)
+
+    def adjoint_halo_pack(self, side, buf):
+        self._pack(1, side, buf)
+
+    def halo_unpack(self, side, buf):
+        self.got[("f", side)] = tuple(int(v) for v in buf)
+
+    def adjoint_halo_unpack(self, side, buf):
+        self.got[("a", side)] = tuple(int(v) for v in buf)
+
+    def close(self):
+        pass
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 5])
+def test_slab_exchange_wiring(monkeypatch, k):
+    """Forward: ghost plane 0 of slab j gets the plane nz - 2 pack (side 1) of
+    slab j - 1, ghost plane nz - 1 the plane 1 pack (side 0) of slab j + 1.
+    Adjoint, the reverse: ghost plane nz - 1 gets slab j + 1's side-0 pack
+    (its e_z = +1 populations of plane 1), ghost plane 0 slab j - 1's side-1
+    pack. Periodic in z."""
+    from paper_1112_0850_gb300 import lattice
+    monkeypatch.setattr(lattice, "Lattice", _FakeLattice)
+    _FakeLattice.count = 0
+    s = slabs.SlabSet(4, 3, 4 * k, 0.6, k)
+    s._lam_ex = [(lat.new_adjoint_halo(), lat.new_adjoint_halo()) for lat in s.slabs]
+    s.exchange()
+    s.adjoint_exchange()
+    for j, lat in enumerate(s.slabs):
+        below, above = (j - 1) % k, (j + 1) % k
+        assert lat.got[("f", 0)] == (below, 1, 0)
+        assert lat.got[("f", 1)] == (above, 0, 0)
+        assert lat.got[("a", 1)] == (above, 0, 1)
+        assert lat.got[("a", 0)] == (below, 1, 1)
+    s.close()
