@@ -21,7 +21,7 @@ import numpy as np
 from . import build as _build
 
 Q = 19
-FMT = {None: 0, "f64": 0, "f32": 1, "f16": 2, "bf16": 3}
+FMT = {None: 0, "f64": 0, "f32": 1, "f16": 2, "bf16": 3, "f16m": 4, "bf16m": 5}
 MODEL = {None: 0, "qian": 0, "incompressible": 1}
 
 class Oracle:
@@ -43,6 +43,10 @@ class Oracle:
         L.oracle_round.argtypes = [ctypes.c_double, ci]
         L.oracle_round.restype = ctypes.c_double
         L.oracle_init.argtypes = [ci] * 3 + [vp, vp, vp, vp, ci, ci]
+        L.oracle_init.restype = ci
+        L.oracle_split_round.argtypes = [dp, ci]
+        L.oracle_store.argtypes = [ci] * 3 + [vp, vp, ci]
+        L.oracle_store.restype = ci
         L.oracle_run.argtypes = [ci] * 3 + [ctypes.c_double, vp, vp, ci, vp, vp, ci, ci, ci, ci]
         L.oracle_run.restype = ci
         L.oracle_macros.argtypes = [ci] * 3 + [vp, vp, ci, vp, vp, vp, ci]
@@ -89,6 +93,27 @@ class Oracle:
         """Round one FP64 value to 'f32' | 'f16' | 'bf16' (ties to even)."""
         return self.lib.oracle_round(float(v), FMT[fmt])
 
+    def split_round(self, P, fmt):
+        """One cell's 19 values through the moment-split format 'f16m' | 'bf16m':
+        J = sum P_i e_i and g_i = (P_i - w_i) - 3 w_i e_i.J~ rounded, rebuilt
+        as w_i + 3 w_i e_i.J~ + g~_i. Returns the rebuilt values."""
+        out = np.array(P, dtype=np.float64, copy=True)
+        assert out.shape == (Q,)
+        self.lib.oracle_split_round(_dp(out), FMT[fmt])
+        return out
+
+    def store_state(self, f, flags=None, fmt=None):
+        """State f [19][nz][ny][nx] as storage format fmt holds it once written
+        (elementwise rounding of f - w, or the moment-split storage of the
+        values each cell holds for its neighbours to pull); returns a new array."""
+        f = np.array(f, dtype=np.float64, order="C", copy=True)
+        shape = f.shape[1:]
+        nz, ny, nx = shape
+        fl = _flags(flags, shape)
+        if self.lib.oracle_store(nx, ny, nz, _vp(fl), _vp(f), FMT[fmt]) != 0:
+            raise MemoryError("oracle_store could not allocate its scratch")
+        return f
+
     def init_equilibrium(self, u0, rho0=None, flags=None, fmt=None, model=None):
         """f^0 = f_eq(rho0, u0) per fluid cell; u0 [3][nz][ny][nx]; returns f [19][nz][ny][nx]."""
         u0 = _f64(u0)
@@ -97,7 +122,8 @@ class Oracle:
         fl = _flags(flags, shape)
         r0 = None if rho0 is None else _f64(rho0)
         f = np.zeros((Q,) + shape)
-        self.lib.oracle_init(nx, ny, nz, _vp(fl), _vp(r0), _vp(u0), _vp(f), FMT[fmt], MODEL[model])
+        if self.lib.oracle_init(nx, ny, nz, _vp(fl), _vp(r0), _vp(u0), _vp(f), FMT[fmt], MODEL[model]) != 0:
+            raise MemoryError("oracle_init could not allocate its scratch")
         return f
 
     def run(self, f, tau, steps, flags=None, F=None, fmt=None, threads=None, u_wall=None, model=None):
@@ -180,6 +206,14 @@ def round_storage_value(v, fmt):
     return default().round_storage_value(v, fmt)
 
 
+def split_round(P, fmt):
+    return default().split_round(P, fmt)
+
+
+def store_state(f, flags=None, fmt=None):
+    return default().store_state(f, flags, fmt)
+
+
 def init_equilibrium(u0, rho0=None, flags=None, fmt=None, model=None):
     return default().init_equilibrium(u0, rho0, flags, fmt, model)
 
@@ -232,4 +266,4 @@ def _force(F, shape):
 
 
 __all__ = ["Q", "Oracle", "default", "load", "lattice", "equilibrium", "moments", "collide_cell", "round_storage_value",
-           "init_equilibrium", "run", "macros", "sums", "max_threads"]
+           "split_round", "store_state", "init_equilibrium", "run", "macros", "sums", "max_threads"]

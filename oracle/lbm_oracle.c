@@ -39,6 +39,18 @@
  * shifted deviation s_i = f_i - w_i of every fluid entry is rounded to the
  * nearest value of a narrower IEEE format (ties to even), written from the
  * format's definition (sign, exponent range, mantissa width).
+ *
+ * Moment-split storage (fmt 4: binary16, fmt 5: bfloat16; a storage format of
+ * this library, not of the paper): the 19 post-collision values P_i of a cell
+ * are kept as their momentum J = sum_i P_i e_i and the remainders
+ * g_i = (P_i - w_i) - 3 w_i (e_i . J~), where J~ is J rounded to the element
+ * format; g_i is rounded too, and a reader rebuilds
+ * P~_i = w_i + 3 w_i (e_i . J~) + g~_i. The rebuilt value is off by the
+ * rounding of g_i alone, which is small next to the deviation itself in a
+ * flow whose populations are near their linear equilibrium part. The rounding
+ * is applied where a cell's values are written: to the post-collision values
+ * of every fluid cell before they stream, and to the initial state grouped as
+ * the values each cell holds for its neighbours to pull.
  */
 #include <math.h>
 #include <stdint.h>
@@ -211,20 +223,42 @@ static double round_format(double v, int mant, int emin, double maxval)
     return r;
 }
 
-/* fmt: 1 = IEEE binary32, 2 = IEEE binary16, 3 = bfloat16. */
+/* fmt: 1 = IEEE binary32, 2 = IEEE binary16, 3 = bfloat16; the moment-split
+ * formats 4 and 5 round their elements as binary16 and bfloat16. */
 double oracle_round(double v, int fmt)
 {
     switch (fmt) {
     case 1: return round_format(v, 23, -126, 3.4028234663852886e38);
-    case 2: return round_format(v, 10, -14, 65504.0);
-    case 3: return round_format(v, 7, -126, 3.3895313892515355e38);
+    case 2: case 4: return round_format(v, 10, -14, 65504.0);
+    case 3: case 5: return round_format(v, 7, -126, 3.3895313892515355e38);
     default: return v;
     }
 }
 
+static int is_split(int fmt) { return fmt == 4 || fmt == 5; }
+
+/* The 19 values P[i] one cell stores, through the moment-split format fmt:
+ * J = sum_i P_i e_i rounded, g_i = (P_i - w_i) - 3 w_i (e_i . J~) rounded,
+ * P_i <- w_i + (3 w_i (e_i . J~) + g~_i). */
+void oracle_split_round(double *P, int fmt)
+{
+    double J[3] = {0.0, 0.0, 0.0};
+    for (int i = 0; i < Q; ++i)
+        for (int a = 0; a < 3; ++a) J[a] += P[i] * E[i][a];
+    for (int a = 0; a < 3; ++a) J[a] = oracle_round(J[a], fmt);
+    for (int i = 0; i < Q; ++i) {
+        double w = weight(i);
+        double base = 3.0 * w * (E[i][0] * J[0] + E[i][1] * J[1] + E[i][2] * J[2]);
+        double g = oracle_round((P[i] - w) - base, fmt);
+        P[i] = w + (base + g);
+    }
+}
+
+/* Storage rounding of the elementwise formats (1-3): every fluid entry's
+ * deviation s_i = f_i - w_i, after each stream step and at init. */
 static void round_storage(double *f, const uint8_t *flags, int64_t N, int fmt)
 {
-    if (!fmt) return;
+    if (!fmt || is_split(fmt)) return;
     for (int i = 0; i < Q; ++i) {
         double w = weight(i);
         for (int64_t c = 0; c < N; ++c)
@@ -232,11 +266,60 @@ static void round_storage(double *f, const uint8_t *flags, int64_t N, int fmt)
     }
 }
 
+/* A pre-collision state f (push form) as it is held in moment-split storage
+ * by cells that each store the values their neighbours pull: fluid cell x
+ * holds P_i(x) = f_i(x + e_i) when x + e_i is fluid, else f_opp(i)(x) (the
+ * halfway bounce-back of x's own population). Each fluid cell's 19 values go
+ * through oracle_split_round, and f is rebuilt from them: f_i(y) = P_i(y - e_i)
+ * when y - e_i is fluid, else P_opp(i)(y). Returns -1 if scratch allocation
+ * failed. */
+static int store_split(int nx, int ny, int nz, const uint8_t *flags, double *f, int fmt)
+{
+    int64_t N = (int64_t)nx * ny * nz;
+    double *P = (double *)malloc(sizeof(double) * Q * N);
+    if (!P) return -1;
+    for (int z = 0; z < nz; ++z)
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                int64_t c = cell(x, y, z, nx, ny);
+                if (!is_fluid(flags, c)) continue;
+                double v[Q];
+                for (int i = 0; i < Q; ++i) {
+                    int64_t d = cell(wrap(x + E[i][0], nx), wrap(y + E[i][1], ny), wrap(z + E[i][2], nz), nx, ny);
+                    v[i] = is_fluid(flags, d) ? f[i * N + d] : f[opposite(i) * N + c];
+                }
+                oracle_split_round(v, fmt);
+                for (int i = 0; i < Q; ++i) P[i * N + c] = v[i];
+            }
+    for (int z = 0; z < nz; ++z)
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                int64_t c = cell(x, y, z, nx, ny);
+                if (!is_fluid(flags, c)) continue;
+                for (int i = 0; i < Q; ++i) {
+                    int64_t s = cell(wrap(x - E[i][0], nx), wrap(y - E[i][1], ny), wrap(z - E[i][2], nz), nx, ny);
+                    f[i * N + c] = is_fluid(flags, s) ? P[i * N + s] : P[opposite(i) * N + c];
+                }
+            }
+    free(P);
+    return 0;
+}
+
+/* A state f written to storage format fmt (as lbm_set_state would hold it):
+ * the elementwise rounding of formats 1-3, or the moment-split storage of
+ * formats 4 and 5. Returns 0, or -1 if scratch allocation failed. */
+int oracle_store(int nx, int ny, int nz, const uint8_t *flags, double *f, int fmt)
+{
+    if (is_split(fmt)) return store_split(nx, ny, nz, flags, f, fmt);
+    round_storage(f, flags, (int64_t)nx * ny * nz, fmt);
+    return 0;
+}
+
 /* f[i][c] = f_eq_i(rho0(c), u0(c)) at fluid cells, 0 at solid cells, with the
  * equilibrium of `model`. rho0 may be NULL (rho0 = 1). Optional storage
- * rounding as in oracle_run. */
-void oracle_init(int nx, int ny, int nz, const uint8_t *flags, const double *rho0,
-                 const double *u0 /* [3][N] */, double *f /* [19][N] */, int fmt, int model)
+ * rounding as in oracle_store. Returns 0, or -1 if scratch allocation failed. */
+int oracle_init(int nx, int ny, int nz, const uint8_t *flags, const double *rho0,
+                const double *u0 /* [3][N] */, double *f /* [19][N] */, int fmt, int model)
 {
     int64_t N = (int64_t)nx * ny * nz;
     for (int64_t c = 0; c < N; ++c) {
@@ -253,14 +336,14 @@ void oracle_init(int nx, int ny, int nz, const uint8_t *flags, const double *rho
         }
         for (int i = 0; i < Q; ++i) f[i * N + c] = feq[i];
     }
-    round_storage(f, flags, N, fmt);
+    return oracle_store(nx, ny, nz, flags, f, fmt);
 }
 
 /* One collide-and-push step from cur to nxt (Sec. 2 steps 1-3 plus the
  * bounce-back rule). Every fluid entry of nxt is written exactly once. */
 static void step_once(int nx, int ny, int nz, double tau, const uint8_t *flags,
                       const double *F, int F_per_cell, const double *u_wall, const double *cur,
-                      double *nxt, int nthreads, int model)
+                      double *nxt, int nthreads, int model, int fmt)
 {
     int64_t N = (int64_t)nx * ny * nz;
     memset(nxt, 0, sizeof(double) * Q * N);
@@ -276,6 +359,7 @@ static void step_once(int nx, int ny, int nz, double tau, const uint8_t *flags,
                 for (int i = 0; i < Q; ++i) f[i] = cur[i * N + c];
                 force_at(F, F_per_cell, c, N, Fc);
                 oracle_collide_cell_model(model, f, tau, Fc, fs);
+                if (is_split(fmt)) oracle_split_round(fs, fmt); /* stored where computed */
                 for (int i = 0; i < Q; ++i) {
                     int xd = wrap(x + E[i][0], nx), yd = wrap(y + E[i][1], ny),
                         zd = wrap(z + E[i][2], nz);
@@ -308,7 +392,7 @@ int oracle_run(int nx, int ny, int nz, double tau, const uint8_t *flags, const d
     if (nthreads < 1) nthreads = 1;
     double *a = f, *b = tmp;
     for (int s = 0; s < nsteps; ++s) {
-        step_once(nx, ny, nz, tau, flags, F, F_per_cell, u_wall, a, b, nthreads, model);
+        step_once(nx, ny, nz, tau, flags, F, F_per_cell, u_wall, a, b, nthreads, model, fmt);
         round_storage(b, flags, N, fmt);
         double *t = a; a = b; b = t;
     }

@@ -357,6 +357,121 @@ def check_shifted_storage_emulation(orc):
     assert np.abs(dev - dev.astype(np.float16).astype(np.float64)).max() < 1e-16
 
 
+def _split_cell(e, w, J, g):
+    """Values P_i = w_i + 3 w_i (e_i . J) + g_i of one cell."""
+    return w + 3.0 * w * (e @ np.asarray(J, dtype=np.float64)) + np.asarray(g, dtype=np.float64)
+
+
+def _even_remainder(opp, seed, scale):
+    """Dyadic remainders with g_i = g_opp(i) (no momentum), few bits each."""
+    rng = np.random.default_rng(seed)
+    g = rng.integers(-31, 32, size=19).astype(np.float64) * scale
+    return 0.5 * (g + g[opp])
+
+
+def check_split_exact_when_representable(orc):
+    """Moment-split storage keeps a cell's values P_i as J = sum P_i e_i and
+    g_i = (P_i - w_i) - 3 w_i e_i.J~, both in the element format. When J and g
+    are values of the format (and g carries no momentum, so that J is the
+    vector's momentum), nothing is lost: the rebuilt values equal P to FP64
+    round-off, although the deviations P_i - w_i themselves are not values of
+    the format (the elementwise formats change them)."""
+    e, w, opp = orc.lattice()
+    e = e.astype(np.float64)
+    for fmt, el in (("f16m", "f16"), ("bf16m", "bf16")):
+        for seed, J in ((1, (3 * 2.0 ** -7, -5 * 2.0 ** -8, 2.0 ** -6)), (2, (-2.0 ** -5, 0.0, 7 * 2.0 ** -9))):
+            g = _even_remainder(opp, seed, 2.0 ** -14)
+            P = _split_cell(e, w, J, g)
+            assert np.abs(orc.split_round(P, fmt) - P).max() < 1e-16, fmt
+            Pel = w + np.array([orc.round_storage_value(v, el) for v in P - w])
+            assert np.abs(Pel - P).max() > 1e-7, fmt
+
+
+def check_split_error_is_remainder_rounding(orc):
+    """In moment-split storage a value is off by the rounding of its remainder
+    g_i alone: at most half a unit in the last place of |g_i| (binary16 with
+    its subnormal step 2^-24, bfloat16 with 8 significant bits). For a cell near
+    equilibrium at |u| ~ 0.02 that is far below the rounding of the whole
+    deviation, which the elementwise formats pay."""
+    e, w, opp = orc.lattice()
+    e = e.astype(np.float64)
+    rng = np.random.default_rng(21)
+    for fmt, el, mant, emin in (("f16m", "f16", 10, -14), ("bf16m", "bf16", 7, -126)):
+        sq_split = sq_elem = 0.0
+        for _ in range(20):
+            u = 0.02 * rng.standard_normal(3)
+            rho = 1.0 + 1e-3 * rng.standard_normal()
+            P = orc.equilibrium(rho, u) + 1e-5 * rng.standard_normal(19)
+            Pt = orc.split_round(P, fmt)
+            Jt = np.array([orc.round_storage_value(v, el) for v in e.T @ P])
+            g = (P - w) - 3.0 * w * (e @ Jt)
+            ulp = 2.0 ** (np.maximum(np.floor(np.log2(np.maximum(np.abs(g), 1e-300))), emin) - mant)
+            assert np.all(np.abs(Pt - P) <= 0.5 * ulp * (1 + 1e-9) + 1e-16), fmt
+            Pel = w + np.array([orc.round_storage_value(v, el) for v in P - w])
+            sq_split += np.sum((Pt - P) ** 2)
+            sq_elem += np.sum((Pel - P) ** 2)
+        # RMS over the cells: about 0.07 (binary16) and 0.11 (bfloat16)
+        assert np.sqrt(sq_split / sq_elem) < 0.2, (fmt, np.sqrt(sq_split / sq_elem))
+
+
+def check_split_store_round_trip(orc):
+    """A state whose every cell holds representable split values for its
+    neighbours to pull (P_i(x) = f_i(x + e_i), or f_opp(i)(x) next to a solid)
+    comes back unchanged from moment-split storage, with and without walls."""
+    ei, w, opp = orc.lattice()
+    e = ei.astype(np.float64)
+    nz, ny, nx = 4, 5, 6
+    for flags in (None, lbm_inputs.random_flags(nx, ny, nz, 0.2, 23)):
+        solid = np.zeros((nz, ny, nx), bool) if flags is None else flags != 0
+        rng = np.random.default_rng(24)
+        P = np.zeros((19, nz, ny, nx))
+        for z in range(nz):
+            for y in range(ny):
+                for x in range(nx):
+                    J = rng.integers(-15, 16, size=3) * 2.0 ** -9
+                    P[:, z, y, x] = _split_cell(e, w, J, _even_remainder(opp, 100 + x + 7 * y + 53 * z, 2.0 ** -15))
+        f = np.zeros_like(P)
+        for z in range(nz):
+            for y in range(ny):
+                for x in range(nx):
+                    if solid[z, y, x]:
+                        continue
+                    for i in range(19):
+                        sx, sy, sz = (x - ei[i, 0]) % nx, (y - ei[i, 1]) % ny, (z - ei[i, 2]) % nz
+                        f[i, z, y, x] = P[opp[i], z, y, x] if solid[sz, sy, sx] else P[i, sz, sy, sx]
+        for fmt in ("f16m", "bf16m"):
+            assert np.abs(orc.store_state(f, flags=flags, fmt=fmt) - f).max() < 1e-16, fmt
+
+
+def check_split_step_rounds_where_computed(orc):
+    """One step in moment-split storage is the unrounded step with each fluid
+    cell's post-collision values passed through the split rounding before they
+    stream (brute force over a small box with walls and a uniform force)."""
+    ei, w, opp = orc.lattice()
+    nz, ny, nx = 3, 4, 5
+    flags = lbm_inputs.random_flags(nx, ny, nz, 0.2, 31)
+    solid = flags != 0
+    rng = np.random.default_rng(32)
+    F = np.array([2e-4, -1e-4, 3e-4])
+    f = orc.init_equilibrium(0.03 * rng.standard_normal((3, nz, ny, nx)), flags=flags)
+    for fmt in ("f16m", "bf16m"):
+        want = np.zeros_like(f)
+        for z in range(nz):
+            for y in range(ny):
+                for x in range(nx):
+                    if solid[z, y, x]:
+                        continue
+                    fs = orc.split_round(orc.collide_cell(f[:, z, y, x], 0.6, F), fmt)
+                    for i in range(19):
+                        dx, dy, dz = (x + ei[i, 0]) % nx, (y + ei[i, 1]) % ny, (z + ei[i, 2]) % nz
+                        if solid[dz, dy, dx]:
+                            want[opp[i], z, y, x] = fs[i]
+                        else:
+                            want[i, dz, dy, dx] = fs[i]
+        got = orc.run(f, 0.6, 1, flags=flags, F=F, fmt=fmt)
+        assert np.abs(got - want).max() < 1e-16, fmt
+
+
 def check_couette_moving_wall(orc):
     """Plane Couette flow between a fixed wall (y = 0) and a wall moving with U
     along x (y = ny - 1, flag 2): halfway bounce-back with the moving-wall term
@@ -531,6 +646,10 @@ ALL_ORACLE_CHECKS = [
     check_diagonal_shear_wave,
     check_init_moments,
     check_shifted_storage_emulation,
+    check_split_exact_when_representable,
+    check_split_error_is_remainder_rounding,
+    check_split_store_round_trip,
+    check_split_step_rounds_where_computed,
     check_poiseuille,
     check_couette_moving_wall,
     check_moving_walls_keep_matching_flow,

@@ -53,6 +53,14 @@ MUTANTS = [
      "            if (model == 7)\n                oracle_equilibrium_incompressible"),
     ("inc_step_ignores_model", "oracle_collide_cell_model(model, f, tau, Fc, fs);", "oracle_collide_cell_model(0, f, tau, Fc, fs);"),
     ("inc_sums_rho_weighted", "model == 1 ? uc[a] : r * uc[a]", "r * uc[a]"),
+    ("split_whole_deviation", "double g = oracle_round((P[i] - w) - base, fmt);",
+     "double g = oracle_round(P[i] - w, fmt) - base;"),
+    ("split_base_sign", "double base = 3.0 * w * (E[i][0]", "double base = -3.0 * w * (E[i][0]"),
+    ("split_store_no_bounce", "v[i] = is_fluid(flags, d) ? f[i * N + d] : f[opposite(i) * N + c];",
+     "v[i] = f[i * N + d];"),
+    ("split_rebuild_own_slot", "f[i * N + c] = is_fluid(flags, s) ? P[i * N + s] : P[opposite(i) * N + c];",
+     "f[i * N + c] = is_fluid(flags, s) ? P[i * N + s] : P[i * N + c];"),
+    ("split_step_unrounded", "if (is_split(fmt)) oracle_split_round(fs, fmt);", "if (0) oracle_split_round(fs, fmt);"),
 ]
 
 
