@@ -37,6 +37,10 @@
  *     interface. On error, lbm_last_error() describes the failure.
  *   - Kernel-side failures (a non-finite or non-positive density) set bits of
  *     a device status word which lbm_status_word() reads; they never trap.
+ *     The calls that synchronize the context's stream on their own
+ *     (lbm_synchronize, lbm_reduce, lbm_reduce_planes) return
+ *     LBM_ERR_DIVERGED while the divergence bit is set; lbm_init_equilibrium
+ *     and lbm_set_state clear the word, as they start a new run.
  */
 #ifndef LBM_CAPI_H
 #define LBM_CAPI_H
@@ -58,24 +62,46 @@ typedef enum {
     LBM_ERR_OOM = 2,         /* device allocation failed or size would not fit */
     LBM_ERR_CUDA = 3,        /* a CUDA runtime call failed */
     LBM_ERR_STATE = 4,       /* call out of order (e.g. adjoint step before seed) */
-    LBM_ERR_DIVERGED = 5,    /* a kernel saw a non-finite or non-positive density */
-    LBM_ERR_INDEX = 6,       /* an index check failed (checked builds only) */
+    LBM_ERR_DIVERGED = 5,    /* a kernel saw a non-finite or non-positive density: returned by
+                                the calls that synchronize (lbm_synchronize, lbm_reduce,
+                                lbm_reduce_planes) when the status word's divergence bit is
+                                set; the results those calls return are still written */
+                             /* (6 is not used) */
     LBM_ERR_UNSUPPORTED = 7  /* combination the library does not support */
 } lbm_status;
 
 /* Population storage formats. S = shifted: the stored value is f_i - w_i
  * (density deviation around rest, rho0 = 1); collision arithmetic is FP64 for
- * LBM_F64 and FP32 for the three others. Narrow formats round to nearest even. */
+ * LBM_F64 and FP32 for the others. Narrow formats round to nearest even.
+ *
+ * M = moment split (this library's format; the paper stores SP or DP only,
+ * Sec. 7): each cell keeps, for the 19 post-collision values P_i it holds,
+ * their momentum J = sum_i P_i e_i and the remainders
+ * g_i = (P_i - w_i) - 3 w_i (e_i . J), every one of them a 16-bit value (J
+ * rounded first, and used rounded in g). A reader rebuilds
+ * P_i = w_i + 3 w_i (e_i . J) + g_i in FP32, so a value is off by the rounding
+ * of its remainder only, not of the whole deviation: the remainder is what the
+ * linear equilibrium part leaves over (quadratic and non-equilibrium parts),
+ * an order of magnitude or more smaller in flows at low Mach number. Per cell
+ * and lattice: 19 remainders plus J in an 8-byte word (three values and an
+ * unused one), 46 bytes, so 92 B per lattice update. The M formats run the
+ * two-grid pull update only (no LBM_PATTERN_AA, no row staging, no halo
+ * copies: those return LBM_ERR_UNSUPPORTED). Their canonical state arrays
+ * (lbm_get_state, lbm_set_state) hold plain shifted deviations in the 16-bit
+ * element type of the format. */
 typedef enum {
     LBM_F64 = 0,   /* double, 304 B per lattice update  */
     LBM_F32 = 1,   /* float,  152 B per lattice update  */
     LBM_F16S = 2,  /* IEEE binary16, 76 B per lattice update */
-    LBM_BF16S = 3  /* bfloat16,      76 B per lattice update */
+    LBM_BF16S = 3, /* bfloat16,      76 B per lattice update */
+    LBM_F16M = 4,  /* IEEE binary16 moment split, 92 B per lattice update */
+    LBM_BF16M = 5  /* bfloat16 moment split,      92 B per lattice update */
 } lbm_storage;
 
-/* Bits of the device status word. */
+/* Bits of the device status word (bit 0x2 is not used). Kernels set them and
+ * never trap; lbm_status_word() reads and clears them, and the synchronizing
+ * calls report the divergence bit as LBM_ERR_DIVERGED. */
 #define LBM_STATUS_DIVERGED 0x1u /* some fluid cell had rho <= 0 or non-finite rho */
-#define LBM_STATUS_INDEX    0x2u /* a checked build caught an out-of-range index */
 #define LBM_STATUS_TIMEOUT  0x4u /* a kernel gave up waiting (about 1 s) for its asynchronous copies */
 
 /* Streaming pattern: how the fused update moves populations through memory. */
@@ -114,7 +140,8 @@ typedef struct {
 
 typedef struct {
     int nx, ny, nz;
-    int pitch;                  /* padded row length in elements (rows start 128-byte aligned) */
+    int pitch;                  /* padded row length in elements: nx rounded up to a whole pair
+                                   of cells, or to lbm_options.row_align bytes when set */
     lbm_storage storage;
     int real_size;              /* bytes of "real": 8 (LBM_F64) or 4 */
     double tau;
@@ -127,8 +154,9 @@ typedef struct {
     lbm_model model;            /* equilibrium */
 } lbm_info;
 
-/* Fill *opt with defaults (LBM_F32, default stream, 128-byte rows, LBM_PATTERN_PULL,
- * LBM_MODEL_QIAN). */
+/* Fill *opt with defaults (LBM_F32, default stream, rows padded only to a
+ * pair of cells (row_align 0), LBM_PATTERN_PULL, LBM_MODEL_QIAN, no row
+ * staging). */
 lbm_status lbm_options_default(lbm_options *opt);
 
 /* Create a context for an nx * ny * nz periodic lattice (Sec. 2: the uniform
@@ -188,7 +216,9 @@ lbm_status lbm_macros(lbm_ctx *ctx, void *rho, void *u);
 
 /* Totals over fluid cells of the current state, accumulated in FP64 in a
  * fixed order (deterministic): out = {sum rho, sum rho u_x, sum rho u_y,
- * sum rho u_z} with rho u = j + F/2. out is a host array; synchronizes. */
+ * sum rho u_z} with rho u = j + F/2. out is a host array; synchronizes.
+ * Returns LBM_ERR_DIVERGED (out still written) if the status word's
+ * divergence bit is set. */
 lbm_status lbm_reduce(lbm_ctx *ctx, double out[4]);
 
 /* Largest lattice, in cells (nx * ny * nz), that lbm_reduce_state_noalloc
@@ -213,9 +243,13 @@ lbm_status lbm_reduce(lbm_ctx *ctx, double out[4]);
  * the library keeps until the process exits; each call overwrites the slots it
  * uses, so nothing has to be cleared. All calls share that one array: calls
  * whose kernels can overlap on the GPU (different streams, or different host
- * threads without ordering) race and may return wrong totals. The first call
- * on each device looks up the array's device address (cudaGetSymbolAddress
- * with that device current); make that first call before any stream capture.
+ * threads without ordering) race and may return wrong totals. Every call made
+ * outside a stream capture looks up the array's device address
+ * (cudaGetSymbolAddress with the calling thread's current device), so a
+ * device reset in between leaves nothing stale; a call made while cuda_stream
+ * is being captured reuses the address of the last call outside a capture on
+ * that device, so make one call on each device before any stream capture (and
+ * one again after a cudaDeviceReset).
  * Asynchronous on cuda_stream. Returns LBM_ERR_ARG for a null state or out, a
  * bad format or size, and when nx * ny * nz exceeds LBM_NOALLOC_MAX_CELLS;
  * LBM_ERR_CUDA if the address look-up or a launch fails. It calls no
@@ -282,7 +316,8 @@ lbm_status lbm_halo_unpack(lbm_ctx *ctx, int side, const void *buf);
  * totals of all slabs then add up to those of the unsplit lattice (to the
  * order of the FP64 sums), the mass/momentum check of a split run, summed
  * over ranks with an all-reduce. out is a host array; synchronizes. Returns
- * LBM_ERR_ARG for a null out or planes outside that range. */
+ * LBM_ERR_ARG for a null out or planes outside that range, LBM_ERR_DIVERGED
+ * (out still written) if the status word's divergence bit is set. */
 lbm_status lbm_reduce_planes(lbm_ctx *ctx, int z0, int z1, double out[4]);
 
 /* The halo exchange of the adjoint of a z-slab run. The reverse step
@@ -368,7 +403,10 @@ lbm_status lbm_adjoint_init_grad(lbm_ctx *ctx, const void *rho0, const void *u0,
 /* Read (and clear, if clear != 0) the device status word; synchronizes. */
 lbm_status lbm_status_word(lbm_ctx *ctx, uint32_t *out, int clear);
 
-/* Block the host until all work enqueued on the context's stream is done. */
+/* Block the host until all work enqueued on the context's stream is done.
+ * Returns LBM_ERR_DIVERGED if the status word's divergence bit is set (the
+ * bit stays set until lbm_status_word clears it or a new initial state is
+ * loaded), so a caller that synchronizes learns of a diverged run there. */
 lbm_status lbm_synchronize(lbm_ctx *ctx);
 
 /* Message of the last failed call on this context (empty if none). */

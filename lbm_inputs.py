@@ -133,6 +133,21 @@ def solenoidal_velocity(n, amp, seed, kmax=4):
     return u * (amp / speed)
 
 
+def smooth_velocity(shape, amp, seed, kmax=2):
+    """Random smooth velocity field on a periodic box of any shape [nz][ny][nx]:
+    i.i.d. normal Fourier coefficients for every integer wave vector with
+    0 < |k| <= kmax (each axis counted in its own box length), back-transformed
+    and scaled so max |u| = amp. Returns u [3][nz][ny][nx]."""
+    rng = np.random.default_rng(seed)
+    nz, ny, nx = shape
+    kz, ky, kx = np.meshgrid(np.fft.fftfreq(nz, d=1.0 / nz), np.fft.fftfreq(ny, d=1.0 / ny),
+                             np.fft.fftfreq(nx, d=1.0 / nx), indexing="ij")
+    band = (kx ** 2 + ky ** 2 + kz ** 2 > 0) & (kx ** 2 + ky ** 2 + kz ** 2 <= kmax ** 2)
+    u = np.stack([np.fft.ifftn(np.where(band, np.fft.fftn(rng.standard_normal(shape)), 0.0)).real
+                  for _ in range(3)])
+    return u * (amp / np.sqrt((u ** 2).sum(0)).max())
+
+
 def force_field(shape, sigma, seed):
     """F[3][nz][ny][nx] with i.i.d. N(0, sigma^2) components."""
     rng = np.random.default_rng(seed)

@@ -11,12 +11,13 @@ import os
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "liblbm_gb300.so")
 
-LBM_F64, LBM_F32, LBM_F16S, LBM_BF16S = 0, 1, 2, 3
-STORAGE = {"f64": LBM_F64, "f32": LBM_F32, "f16s": LBM_F16S, "bf16s": LBM_BF16S}
+LBM_F64, LBM_F32, LBM_F16S, LBM_BF16S, LBM_F16M, LBM_BF16M = 0, 1, 2, 3, 4, 5
+STORAGE = {"f64": LBM_F64, "f32": LBM_F32, "f16s": LBM_F16S, "bf16s": LBM_BF16S, "f16m": LBM_F16M,
+           "bf16m": LBM_BF16M}
 STORAGE_NAME = {v: k for k, v in STORAGE.items()}
-STORAGE_BYTES = {LBM_F64: 8, LBM_F32: 4, LBM_F16S: 2, LBM_BF16S: 2}
+# bytes of one stored population value (a remainder, for the moment-split formats)
+STORAGE_BYTES = {LBM_F64: 8, LBM_F32: 4, LBM_F16S: 2, LBM_BF16S: 2, LBM_F16M: 2, LBM_BF16M: 2}
 STATUS_DIVERGED = 0x1
-STATUS_INDEX = 0x2
 STATUS_TIMEOUT = 0x4
 NOALLOC_MAX_CELLS = 268435456
 Q = 19

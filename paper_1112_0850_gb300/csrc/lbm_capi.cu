@@ -55,8 +55,8 @@ struct lbm_ctx {
 
 namespace {
 
-const char *status_names[] = {"LBM_OK",    "LBM_ERR_ARG",      "LBM_ERR_OOM",   "LBM_ERR_CUDA",
-                              "LBM_ERR_STATE", "LBM_ERR_DIVERGED", "LBM_ERR_INDEX", "LBM_ERR_UNSUPPORTED"};
+const char *status_names[] = {"LBM_OK",        "LBM_ERR_ARG",      "LBM_ERR_OOM",     "LBM_ERR_CUDA",
+                              "LBM_ERR_STATE", "LBM_ERR_DIVERGED", "unknown status", "LBM_ERR_UNSUPPORTED"};
 
 lbm_status fail(lbm_ctx *ctx, lbm_status s, const std::string &msg) {
     if (ctx) ctx->err = msg;
@@ -67,9 +67,22 @@ lbm_status cuda_fail(lbm_ctx *ctx, cudaError_t e, const char *what) {
     return fail(ctx, LBM_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
+// The status word v, read after a synchronization: LBM_ERR_DIVERGED while
+// its divergence bit is set.
+lbm_status diverged(lbm_ctx *ctx, unsigned v) {
+    if (v & LBM_STATUS_DIVERGED) {
+        char msg[160];
+        snprintf(msg, sizeof msg,
+                 "a fluid cell reached a non-finite or non-positive density (status word 0x%x); "
+                 "lbm_status_word clears it", v);
+        return fail(ctx, LBM_ERR_DIVERGED, msg);
+    }
+    return LBM_OK;
+}
+
 size_t real_size(lbm_storage s) { return s == LBM_F64 ? 8 : 4; }
 
-bool valid_storage(int s) { return s >= LBM_F64 && s <= LBM_BF16S; }
+bool valid_storage(int s) { return s >= LBM_F64 && s <= LBM_BF16M; }
 
 // Elements per padded row so that each row starts on a row_align-byte
 // boundary (0 = a whole pair of cells); -1 if row_align is not allowed.
@@ -133,6 +146,7 @@ Dev make_dev(const lbm_ctx *ctx) {
     d.incomp = ctx->model == LBM_MODEL_INCOMPRESSIBLE;
     d.row_staging = ctx->stage_rows;
     d.num_sms = ctx->num_sms;
+    d.jo = split_j_offset(ctx->g.qs);
     return d;
 }
 
@@ -211,10 +225,12 @@ struct Staged {
 };
 
 #define LBM_DISPATCH(ctx, call)                                             \
-    ((ctx)->storage == LBM_F64    ? Ops<LBM_F64>::call                      \
-     : (ctx)->storage == LBM_F32  ? Ops<LBM_F32>::call                      \
-     : (ctx)->storage == LBM_F16S ? Ops<LBM_F16S>::call                     \
-                                  : Ops<LBM_BF16S>::call)
+    ((ctx)->storage == LBM_F64     ? Ops<LBM_F64>::call                     \
+     : (ctx)->storage == LBM_F32   ? Ops<LBM_F32>::call                     \
+     : (ctx)->storage == LBM_F16S  ? Ops<LBM_F16S>::call                    \
+     : (ctx)->storage == LBM_BF16S ? Ops<LBM_BF16S>::call                   \
+     : (ctx)->storage == LBM_F16M  ? Ops<LBM_F16M>::call                    \
+                                   : Ops<LBM_BF16M>::call)
 #define LBM_AA_DISPATCH(ctx, call)                                          \
     ((ctx)->storage == LBM_F64    ? AaOps<LBM_F64>::call                    \
      : (ctx)->storage == LBM_F32  ? AaOps<LBM_F32>::call                    \
@@ -287,6 +303,7 @@ lbm_status lbm_create(lbm_ctx **out, int nx, int ny, int nz, double tau, const u
         (o.model != LBM_MODEL_QIAN && o.model != LBM_MODEL_INCOMPRESSIBLE))
         return LBM_ERR_ARG;
     const bool aa = o.pattern == LBM_PATTERN_AA;
+    if (is_split(o.storage) && (aa || o.stage_rows)) return LBM_ERR_UNSUPPORTED;
     const int pitch = pitch_for(nx, o.storage, o.row_align);
     if (pitch < 0) return LBM_ERR_ARG;
     const long long qs = (long long)nz * ny * pitch;
@@ -342,7 +359,7 @@ lbm_status lbm_create(lbm_ctx **out, int nx, int ny, int nz, double tau, const u
         return LBM_ERR_CUDA;
     }
 
-    const size_t lat_bytes = (size_t)Q * (size_t)qs * storage_bytes(o.storage);
+    const size_t lat_bytes = lattice_bytes_of(o.storage, qs);
     size_t free_b = 0, total_b = 0;
     e = cudaMemGetInfo(&free_b, &total_b);
     if (e != cudaSuccess) {
@@ -481,7 +498,7 @@ lbm_status lbm_get_info(const lbm_ctx *ctx, lbm_info *info) {
     info->tau = ctx->tau;
     info->n_cells = (int64_t)ctx->g.nx * ctx->g.ny * ctx->g.nz;
     info->n_fluid = ctx->n_fluid;
-    info->lattice_bytes = (size_t)Q * (size_t)ctx->g.qs * storage_bytes(ctx->storage);
+    info->lattice_bytes = lattice_bytes_of(ctx->storage, ctx->g.qs);
     info->tape_bytes_per_step = 4 * (size_t)ctx->g.qs * real_size(ctx->storage);
     info->steps_done = ctx->steps_done;
     info->pattern = ctx->pattern;
@@ -555,6 +572,8 @@ lbm_status lbm_init_equilibrium(lbm_ctx *ctx, const void *rho, const void *u) {
     Dev d = make_dev(ctx);
     cudaError_t e = LBM_DISPATCH(ctx, init_eq(d, state_lat(ctx), ir >= 0 ? st.dev(ir) : nullptr, st.dev(iu)));
     if (e != cudaSuccess) return cuda_fail(ctx, e, "init_equilibrium launch");
+    e = cudaMemsetAsync(ctx->status_d, 0, sizeof(unsigned), ctx->stream);  // a new run
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "status word reset");
     ctx->steps_done = 0;
     ctx->lam_valid = false;
     return LBM_OK;
@@ -657,10 +676,12 @@ lbm_status lbm_reduce_planes(lbm_ctx *ctx, int z0, int z1, double out[4]) {
     Dev d = make_dev(ctx);
     cudaError_t e = LBM_DISPATCH(ctx, reduce(d, state_lat(ctx), z0, z1, ctx->red_partials, ctx->red_out));
     if (e != cudaSuccess) return cuda_fail(ctx, e, "reduce launch");
+    unsigned v = 0;
     e = cudaMemcpyAsync(out, ctx->red_out, 4 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&v, ctx->status_d, sizeof(unsigned), cudaMemcpyDeviceToHost, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "reduce result copy");
-    return LBM_OK;
+    return diverged(ctx, v);
 }
 
 lbm_status lbm_reduce(lbm_ctx *ctx, double out[4]) {
@@ -785,6 +806,8 @@ lbm_status lbm_set_state(lbm_ctx *ctx, const void *src, lbm_storage fmt) {
     Dev d = make_dev(ctx);
     cudaError_t e = LBM_DISPATCH(ctx, set_state(d, state_lat(ctx), st.dev(k), (int)fmt));
     if (e != cudaSuccess) return cuda_fail(ctx, e, "set_state launch");
+    e = cudaMemsetAsync(ctx->status_d, 0, sizeof(unsigned), ctx->stream);  // a new run
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "status word reset");
     ctx->steps_done = 0;
     return LBM_OK;
 }
@@ -810,6 +833,8 @@ static lbm_status halo_copy(lbm_ctx *ctx, int side, const void *buf, bool unpack
     if (!buf || (side != 0 && side != 1)) return fail(ctx, LBM_ERR_ARG, "bad halo buffer or side");
     if (ctx->g.nz < 3) return fail(ctx, LBM_ERR_ARG, "a slab needs nz >= 3: two ghost planes and an interior");
     if (ctx->pattern != LBM_PATTERN_PULL) return fail(ctx, LBM_ERR_UNSUPPORTED, "halo copies need the pull pattern");
+    if (is_split(ctx->storage))
+        return fail(ctx, LBM_ERR_UNSUPPORTED, "halo copies do not carry the momentum words of moment-split storage");
     if (adjoint && !ctx->lam_valid) return fail(ctx, LBM_ERR_STATE, "lbm_adjoint_seed must come first");
     Staged st(ctx);
     const int k = st.add(buf, adjoint ? lbm_adjoint_halo_bytes(ctx) : lbm_halo_bytes(ctx), !unpack);
@@ -934,9 +959,11 @@ lbm_status lbm_status_word(lbm_ctx *ctx, uint32_t *out, int clear) {
 
 lbm_status lbm_synchronize(lbm_ctx *ctx) {
     if (check_ctx(ctx)) return LBM_ERR_ARG;
-    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    unsigned v = 0;
+    cudaError_t e = cudaMemcpyAsync(&v, ctx->status_d, sizeof(unsigned), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "synchronize");
-    return LBM_OK;
+    return diverged(ctx, v);
 }
 
 const char *lbm_last_error(const lbm_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }

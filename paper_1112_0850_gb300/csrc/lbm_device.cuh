@@ -163,6 +163,44 @@ template <> struct Stor<LBM_BF16S> {
     }
 };
 
+// The moment-split formats store their 19 remainders as the 16-bit format
+// of the same name does; their per-cell momentum words are handled by SplitJ.
+LBM_HD constexpr bool is_split(int s) { return s == LBM_F16M || s == LBM_BF16M; }
+template <> struct Stor<LBM_F16M> : Stor<LBM_F16S> {};
+template <> struct Stor<LBM_BF16M> : Stor<LBM_BF16S> {};
+
+// Momentum J of a cell in a moment-split lattice: one 8-byte word per cell,
+// (J_x, J_y) in its first 32-bit half and (J_z, 0) in its second, each a
+// 16-bit value of the format (rounded to nearest even). lo/hi give the value
+// in the low/high 16 bits of a 32-bit half as float (exact).
+template <int S> struct SplitJ;
+template <> struct SplitJ<LBM_F16M> {
+    static __device__ __forceinline__ unsigned pack(float a, float b) {
+        union {
+            unsigned u;
+            __half2 h;
+        } v;
+        v.h = __floats2half2_rn(a, b);
+        return v.u;
+    }
+    static __device__ __forceinline__ float lo(unsigned w) {
+        return __half2float(__ushort_as_half((unsigned short)(w & 0xffffu)));
+    }
+    static __device__ __forceinline__ float hi(unsigned w) { return __half2float(__ushort_as_half((unsigned short)(w >> 16))); }
+};
+template <> struct SplitJ<LBM_BF16M> {
+    static __device__ __forceinline__ unsigned pack(float a, float b) {
+        union {
+            unsigned u;
+            __nv_bfloat162 h;
+        } v;
+        v.h = __floats2bfloat162_rn(a, b);
+        return v.u;
+    }
+    static __device__ __forceinline__ float lo(unsigned w) { return __uint_as_float(w << 16); }
+    static __device__ __forceinline__ float hi(unsigned w) { return __uint_as_float(w & 0xffff0000u); }
+};
+
 // Two 32-bit words of a small array read every step (the push masks of a
 // cell pair, 4 B a cell; a bounce-back link), loaded with an L2 evict-last
 // policy: while the lattices stream through L2 every step, these arrays stay
@@ -194,7 +232,18 @@ __device__ __forceinline__ void st2_real(double *p, double a, double b) {
     __stcs(reinterpret_cast<double2 *>(p), make_double2(a, b));
 }
 
+// Bytes of one stored population value (a remainder, for the split formats).
 inline size_t storage_bytes(lbm_storage s) { return s == LBM_F64 ? 8 : (s == LBM_F32 ? 4 : 2); }
+
+// Element offset of the momentum words in a moment-split lattice: after the
+// 19 remainder arrays, rounded up to a 16-byte boundary (8 elements).
+LBM_HD long long split_j_offset(long long qs) { return (19 * qs + 7) / 8 * 8; }
+
+// Bytes of one padded lattice of qs cells in storage s.
+inline size_t lattice_bytes_of(lbm_storage s, long long qs) {
+    if (is_split(s)) return (size_t)split_j_offset(qs) * 2 + (size_t)qs * 8;
+    return (size_t)19 * (size_t)qs * storage_bytes(s);
+}
 
 // ---------------------------------------------------------------------------
 // Geometry of the padded structure-of-arrays store: population i of cell

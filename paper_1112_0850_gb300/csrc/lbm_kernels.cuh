@@ -40,6 +40,94 @@ template <> struct IOFmt<LBM_BF16S> {
     static __device__ __forceinline__ void put(T *p, double v) { *p = __double2bfloat16(v); }
 };
 
+// Canonical state arrays of a moment-split context hold plain shifted
+// deviations in the format's 16-bit element type.
+template <> struct IOFmt<LBM_F16M> : IOFmt<LBM_F16S> {};
+template <> struct IOFmt<LBM_BF16M> : IOFmt<LBM_BF16S> {};
+
+// ---------------------------------------------------------------------------
+// Moment-split storage (LBM_F16M, LBM_BF16M): a cell holds, for its 19
+// post-collision values P_i, the momentum word J (SplitJ) and the remainders
+// g_i = s_i - K_i (e_i . J) (s_i = P_i - w_i, J as stored), rebuilt as
+// s_i = K_i (e_i . J) + g_i with one fused multiply-add. K_i = 3 w_i, taken as
+// the momentum-exact pair of OddK (2 K_axis + 8 K_diag = 1 exactly, so the
+// base parts carry J itself). Writing e_i = sigma e'_i with the first non-zero
+// component of e'_i equal to +1, K_i (e_i . J) = (sigma K_i)(e'_i . J): e'_i . J
+// is one component or one sum / difference (edot_first), the same value in the
+// packed step kernel and the per-cell readers.
+LBM_HD constexpr bool first_positive(int i) {
+    return ex(i) > 0 || (ex(i) == 0 && (ey(i) > 0 || (ey(i) == 0 && ez(i) > 0)));
+}
+// e'_i: the member of the pair (i, opp(i)) whose first non-zero component is +1.
+LBM_HD constexpr int split_first(int i) { return first_positive(i) ? i : opp(i); }
+// sigma K_i (0 for the rest population).
+LBM_HD constexpr float split_k(int i) {
+    return i == 0 ? 0.0f : (first_positive(i) ? 1.0f : -1.0f) * (i <= 6 ? OddK<float>::AXIS : OddK<float>::DIAG);
+}
+
+// e'_i . J of one cell's momentum word (scalar; the association of edot_first).
+template <int S> __device__ __forceinline__ float split_edot(int i, uint2 w) {
+    const float jx = SplitJ<S>::lo(w.x), jy = SplitJ<S>::hi(w.x), jz = SplitJ<S>::lo(w.y);
+    if (ex(i)) {
+        if (ey(i)) return ey(i) > 0 ? __fadd_rn(jx, jy) : __fsub_rn(jx, jy);
+        if (ez(i)) return ez(i) > 0 ? __fadd_rn(jx, jz) : __fsub_rn(jx, jz);
+        return jx;
+    }
+    if (ey(i)) {
+        if (ez(i)) return ez(i) > 0 ? __fadd_rn(jy, jz) : __fsub_rn(jy, jz);
+        return jy;
+    }
+    return jz;
+}
+
+// Momentum words of a moment-split lattice P (one uint2 per padded cell).
+template <class T> __device__ __forceinline__ const uint2 *split_words(const Dev &d, const T *P) {
+    return reinterpret_cast<const uint2 *>(P + d.jo);
+}
+template <class T> __device__ __forceinline__ uint2 *split_words(const Dev &d, T *P) {
+    return reinterpret_cast<uint2 *>(P + d.jo);
+}
+
+// Round to the 16-bit format (nearest even) from float or double.
+template <int S> __device__ __forceinline__ unsigned split_pack(float a, float b) { return SplitJ<S>::pack(a, b); }
+template <int S> __device__ __forceinline__ unsigned split_pack(double a, double b) {
+    union {
+        unsigned short h[2];
+        unsigned u;
+    } v;
+    if (S == LBM_F16M) {
+        v.h[0] = __half_as_ushort(__double2half(a));
+        v.h[1] = __half_as_ushort(__double2half(b));
+    } else {
+        v.h[0] = __bfloat16_as_ushort(__double2bfloat16(a));
+        v.h[1] = __bfloat16_as_ushort(__double2bfloat16(b));
+    }
+    return v.u;
+}
+
+// Write one cell's 19 shifted values v (float or double) at cell c of a
+// moment-split lattice: J = sum_i v_i e_i rounded to the format, then the
+// remainders g_i = v_i - K_i (e_i . J) rounded.
+template <int S, class V>
+__device__ __forceinline__ void split_store(const Dev &d, typename Stor<S>::T *P, int c, const V v[Q]) {
+    V jx = V(0), jy = V(0), jz = V(0);
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+        if (ex(i)) jx += ex(i) > 0 ? v[i] : -v[i];
+        if (ey(i)) jy += ey(i) > 0 ? v[i] : -v[i];
+        if (ez(i)) jz += ez(i) > 0 ? v[i] : -v[i];
+    }
+    const unsigned wx = split_pack<S>(jx, jy), wy = split_pack<S>(jz, V(0));
+    const uint2 w = make_uint2(wx, wy);
+    IOFmt<S>::put(P + c, (double)v[0]);
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+        const V g = fma(V(-split_k(i)), V(split_edot<S>(split_first(i), w)), v[i]);
+        IOFmt<S>::put(P + (long long)i * d.g.qs + c, (double)g);
+    }
+    split_words(d, P)[c] = w;
+}
+
 __device__ __forceinline__ bool is_solid(const uint8_t *flags, int c) { return flags && flags[c]; }
 
 // Moving-wall term of a population bounced into direction i: 6 w_i (e_i . u_w).
@@ -69,6 +157,26 @@ template <int S, bool FLAGS>
 __device__ __forceinline__ void gather(const Dev &d, const typename Stor<S>::T *P, int x, int y, int z,
                                        int c, typename Stor<S>::R s[Q]) {
     const long long qs = d.g.qs;
+    if constexpr (is_split(S)) {
+        // rebuild each value from its source cell's momentum word; a bounced
+        // one is the cell's own opposite value, rebuilt from its own word
+        const uint2 *J = split_words(d, P);
+        s[0] = Stor<S>::ld(P + c);
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+            const int src = pull_src(d.g, x, y, z, i);
+            const uint8_t f = FLAGS ? d.flags[src] : 0;
+            if (!f) {
+                s[i] = __fmaf_rn(split_k(i), split_edot<S>(split_first(i), __ldg(J + src)),
+                                 Stor<S>::ld(P + (long long)i * qs + src));
+            } else {
+                s[i] = __fmaf_rn(split_k(opp(i)), split_edot<S>(split_first(i), __ldg(J + c)),
+                                 Stor<S>::ld(P + (long long)opp(i) * qs + c));
+                if (f == 2 && d.moving_on) s[i] += wall_term<typename Stor<S>::R>(d, i);
+            }
+        }
+        return;
+    }
     if (d.layout == LAYOUT_AA_NAT) {
 #pragma unroll
         for (int i = 0; i < Q; ++i) s[i] = Stor<S>::ld(P + (long long)i * qs + c);
@@ -134,7 +242,7 @@ template <int S> __device__ __forceinline__ bool nan_marked(const Dev &d) {
 // FP64 arithmetic 1 (<= 255 registers), FP32 storage 3 (<= 80), 16-bit
 // storage 4 (<= 64: fewer bytes per thread, so more threads in flight).
 template <int S> struct StepBlocks {
-    static constexpr int value = S == LBM_F64 ? 1 : (S == LBM_F32 ? 3 : 4);
+    static constexpr int value = S == LBM_F64 ? 1 : ((S == LBM_F32 || is_split(S)) ? 3 : 4);
 };
 template <int S> struct Bounce {
     static constexpr int mode = bounce_mode(S);
@@ -419,6 +527,167 @@ __device__ __forceinline__ void step_pair(const Dev &d, const Rows &rows, const 
     }
 }
 
+// The fused step of step_pair for the moment-split formats: the gather
+// rebuilds each value from its source cell's remainder and momentum word, the
+// bounce-back reload (the mask-guided form) rebuilds the cell's own opposite
+// values from its own word, and the store writes the pair's momentum word,
+// J = j + F (the momentum of the post-collision values: the Guo collision
+// adds F), rounded, then the remainders against it.
+template <int S, bool FLAGS, int FORCE, bool RECORD, bool RED = false>
+__device__ __forceinline__ void step_pair_split(const Dev &d, const typename Stor<S>::T *__restrict__ src,
+                                                typename Stor<S>::T *__restrict__ dst, float *__restrict__ tape,
+                                                int x0, int y, int z, double *red = nullptr) {
+    typedef typename Stor<S>::T T;
+    typedef float R;
+    typedef float2 V;  // lane x: cell x0, lane y: cell x0 + 1
+    const Geom &g = d.g;
+    const bool has1 = x0 + 1 < g.nx;
+    const int c = cell_index(g, x0, y, z);
+    uint32_t m0 = 0u, m1 = 0u;
+    bool live0 = true, live1 = has1;
+    if (FLAGS) {
+        const uint2 mm = ld_resident2(d.mask + c);
+        m0 = mm.x;
+        m1 = mm.y;
+        live0 = !(m0 & SOLID_BIT);
+        live1 = has1 && !(m1 & SOLID_BIT);
+    }
+    const int xa = wrap1(x0 - 1, g.nx);              // e_x = +1, cell x0
+    const int xb = wrap1(x0 + 1, g.nx);              // e_x = -1, cell x0
+    const int xc = has1 ? wrap1(x0 + 2, g.nx) : x0;  // e_x = -1, cell x0 + 1 (e_x = +1 pulls from x0)
+    // the cell after the pair: x0 + 2, or, for the lone last cell of an odd
+    // row, its own e_x = -1 source xb (the row's first cell)
+    const int xn = has1 ? xc : xb;
+    // Momentum words of the nine source rows (y - e_y, z - e_z), r = 3 (e_y + 1)
+    // + e_z + 1: the pair (x0, x0 + 1) of each, and cells xa and xn of the five
+    // rows that directions with e_x = +-1 pull from (those with e_y e_z = 0).
+    const uint2 *Js = split_words(d, src);
+    uint4 jq[9];
+    uint2 ja[9], jc[9];
+#pragma unroll
+    for (int r = 0; r < 9; ++r) {
+        const int dy = r / 3 - 1, dz = r % 3 - 1;
+        const int rb = (wrap1(z - dz, g.nz) * g.ny + wrap1(y - dy, g.ny)) * g.pitch;
+        jq[r] = __ldg(reinterpret_cast<const uint4 *>(Js + rb + x0));
+        if (dy == 0 || dz == 0) {
+            ja[r] = __ldg(Js + rb + xa);
+            jc[r] = __ldg(Js + rb + xn);
+        }
+    }
+    V s[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const T *Pi = src + (long long)i * g.qs + (wrap1(z - ez(i), g.nz) * g.ny + wrap1(y - ey(i), g.ny)) * g.pitch;
+        V gi;
+        if (ex(i) == 0) {
+            Stor<S>::ld2(Pi + x0, gi.x, gi.y);
+        } else {
+            gi.x = Stor<S>::ld(Pi + (ex(i) > 0 ? xa : xb));
+            gi.y = Stor<S>::ld(Pi + (ex(i) > 0 ? x0 : xc));
+        }
+        if (i == 0) {
+            s[0] = gi;
+            continue;
+        }
+        const int r = (ey(i) + 1) * 3 + ez(i) + 1;
+        uint2 wa, wb;  // the momentum words of the two source cells
+        if (ex(i) == 0) {
+            wa = make_uint2(jq[r].x, jq[r].y);
+            wb = make_uint2(jq[r].z, jq[r].w);
+        } else if (ex(i) > 0) {
+            wa = ja[r];
+            wb = make_uint2(jq[r].x, jq[r].y);
+        } else {  // sources xb, xc: x0 + 1 and x0 + 2, or the row's first cell for a lone last cell
+            wa = has1 ? make_uint2(jq[r].z, jq[r].w) : jc[r];
+            wb = jc[r];
+        }
+        const V jx = make_float2(SplitJ<S>::lo(wa.x), SplitJ<S>::lo(wb.x));
+        const V jy = make_float2(SplitJ<S>::hi(wa.x), SplitJ<S>::hi(wb.x));
+        const V jz = make_float2(SplitJ<S>::lo(wa.y), SplitJ<S>::lo(wb.y));
+        s[i] = vfma(vsplat(split_k(i)), edot_first(split_first(i), jx, jy, jz), gi);
+    }
+    if (FLAGS && ((m0 | m1) & 0x7fffeu)) {
+        // a pair next to a solid: its bounced values are the cell's own
+        // opposite ones, rebuilt from its own momentum word (row r = 4) and
+        // selected over the gathered (unread) ones. Branch-free: predicated
+        // loads and selects, so a warp with bounces anywhere runs one pass.
+        const V ox = make_float2(SplitJ<S>::lo(jq[4].x), SplitJ<S>::lo(jq[4].z));
+        const V oy = make_float2(SplitJ<S>::hi(jq[4].x), SplitJ<S>::hi(jq[4].z));
+        const V oz = make_float2(SplitJ<S>::lo(jq[4].y), SplitJ<S>::lo(jq[4].w));
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+            const T *Po = src + (long long)opp(i) * g.qs + c;
+            const bool b0 = (m0 >> opp(i)) & 1u, b1 = (m1 >> opp(i)) & 1u;
+            V go = vsplat(R(0));
+            if (b0) go.x = Stor<S>::ld(Po);
+            if (b1) go.y = Stor<S>::ld(Po + 1);
+            const V r = vfma(vsplat(split_k(opp(i))), edot_first(split_first(i), ox, oy, oz), go);
+            s[i].x = b0 ? r.x : s[i].x;
+            s[i].y = b1 ? r.y : s[i].y;
+        }
+    }
+    if (FLAGS && d.moving_on && ((m0 | m1) & MOVING_BIT)) {
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+            if (((m0 >> opp(i)) & 1u) && d.flags[pull_src(g, x0, y, z, i)] == 2) s[i].x += wall_term<R>(d, i);
+            if (((m1 >> opp(i)) & 1u) && d.flags[pull_src(g, x0 + 1, y, z, i)] == 2) s[i].y += wall_term<R>(d, i);
+        }
+    }
+    V Fx = vsplat(R(0)), Fy = vsplat(R(0)), Fz = vsplat(R(0));
+    Guo2<R> G;
+    if (FORCE == 1) {
+        Fx = vsplat(R(d.F[0]));
+        Fy = vsplat(R(d.F[1]));
+        Fz = vsplat(R(d.F[2]));
+        G = uniform_guo<R, false>(d);
+    } else if (FORCE == 2) {
+        const R *F = static_cast<const R *>(d.Ffield);
+        ld2_real(F + c, Fx.x, Fx.y);
+        ld2_real(F + g.qs + c, Fy.x, Fy.y);
+        ld2_real(F + 2 * g.qs + c, Fz.x, Fz.y);
+        G = guo2<R>(R(1) - R(0.5) * R(d.omega), Fx, Fy, Fz);
+    }
+    const Mom2<R> m = moments2<R, FORCE != 0>(s, Fx, Fy, Fz, d.incomp);
+    const bool bad0 = live0 && !(m.rho.x > R(0) && m.rho.x < R(1e30));
+    const bool bad1 = live1 && !(m.rho.y > R(0) && m.rho.y < R(1e30));
+    if (bad0 || bad1) atomicOr(d.status, LBM_STATUS_DIVERGED);
+    if (RED) pair_add_totals<R>(m, live0, live1, d.incomp, red);
+    if (RECORD) {
+        const long long qs = g.qs;
+        st2_real(tape + c, m.rho.x, m.rho.y);
+        st2_real(tape + qs + c, m.ux.x, m.ux.y);
+        st2_real(tape + 2 * qs + c, m.uy.x, m.uy.y);
+        st2_real(tape + 3 * qs + c, m.uz.x, m.uz.y);
+    }
+    collide2<R, FORCE != 0, false>(s, m, R(d.omega), R(d.cs), Fx, Fy, Fz, G, d.incomp);
+    // the pair's momentum word, then the remainders against the rounded J
+    V Jx = m.jx, Jy = m.jy, Jz = m.jz;
+    if (FORCE) {
+        const V h = vsplat(R(0.5));
+        Jx = vfma(h, Fx, Jx);
+        Jy = vfma(h, Fy, Jy);
+        Jz = vfma(h, Fz, Jz);
+    }
+    const unsigned w0x = SplitJ<S>::pack(Jx.x, Jy.x), w0y = SplitJ<S>::pack(Jz.x, R(0));
+    const unsigned w1x = SplitJ<S>::pack(Jx.y, Jy.y), w1y = SplitJ<S>::pack(Jz.y, R(0));
+    const V tx = make_float2(SplitJ<S>::lo(w0x), SplitJ<S>::lo(w1x));
+    const V ty = make_float2(SplitJ<S>::hi(w0x), SplitJ<S>::hi(w1x));
+    const V tz = make_float2(SplitJ<S>::lo(w0y), SplitJ<S>::lo(w1y));
+#pragma unroll
+    for (int p = 0; p < NPAIR; ++p) {
+        const int i = pair_first(p), io = opp(i);
+        const V e = edot_first(i, tx, ty, tz);
+        s[i] = vfma(vsplat(-split_k(i)), e, s[i]);
+        s[io] = vfma(vsplat(-split_k(io)), e, s[io]);
+    }
+    // Pairs are stored whole, a solid cell included (its values are never
+    // read: the mask-guided reload rebuilds bounced values from the fluid
+    // cell's own slots), so 32-byte sectors are written complete.
+#pragma unroll
+    for (int i = 0; i < Q; ++i) Stor<S>::st2(dst + (long long)i * g.qs + c, s[i].x, s[i].y);
+    *reinterpret_cast<uint4 *>(split_words(d, dst) + c) = make_uint4(w0x, w0y, w1x, w1y);
+}
+
 // Launch the step kernel of the link form as a programmatic dependent of the
 // previous step's bounce kernel: its blocks are scheduled as the bounce
 // kernel drains, and wait for it before their first load.
@@ -440,7 +709,10 @@ __global__ void __launch_bounds__(256, StepBlocks<S>::value)
     if (!pair_cell<FLAT>(d.g, FLAT ? d.PF : d.P, blockDim.x, blockDim.y, blockIdx.x, blockIdx.y, threadIdx.x,
                          threadIdx.y, x0, y, z))
         return;
-    step_pair<S, FLAGS, FORCE, RECORD>(d, GlobalRows<S>{src}, src, dst, tape, x0, y, z);
+    if constexpr (is_split(S))
+        step_pair_split<S, FLAGS, FORCE, RECORD>(d, src, dst, tape, x0, y, z);
+    else
+        step_pair<S, FLAGS, FORCE, RECORD>(d, GlobalRows<S>{src}, src, dst, tape, x0, y, z);
 }
 
 // The step with the mass/momentum totals of its pre-collision state fused in
@@ -455,9 +727,13 @@ __global__ void __launch_bounds__(256, StepBlocks<S>::value)
     double red[4] = {0.0, 0.0, 0.0, 0.0};
     int x0, y, z;
     if (pair_cell<FLAT>(d.g, FLAT ? d.PF : d.P, blockDim.x, blockDim.y, blockIdx.x, blockIdx.y, threadIdx.x,
-                        threadIdx.y, x0, y, z))
-        step_pair<S, FLAGS, FORCE, false, GlobalRows<S>, true>(d, GlobalRows<S>{src}, src, dst, nullptr, x0, y, z,
-                                                              red);
+                        threadIdx.y, x0, y, z)) {
+        if constexpr (is_split(S))
+            step_pair_split<S, FLAGS, FORCE, false, true>(d, src, dst, nullptr, x0, y, z, red);
+        else
+            step_pair<S, FLAGS, FORCE, false, GlobalRows<S>, true>(d, GlobalRows<S>{src}, src, dst, nullptr, x0, y,
+                                                                  z, red);
+    }
     block_partials(red, partials);
 }
 
@@ -656,6 +932,25 @@ __global__ void __launch_bounds__(256)
         return;
     }
     const long long N = d.n_cells, cc = canon_index(d.g, x, y, z);
+    if constexpr (is_split(S)) {  // the 19 values this cell holds, written as J and remainders
+        R v[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const int t = push_dst(d.g, x, y, z, i);
+            int k = i;
+            long long ct = canon_neighbor(d.g, x, y, z, i);
+            const bool bounce = FLAGS && d.flags[t];
+            if (bounce) {
+                k = opp(i);
+                ct = cc;
+            }
+            const R r1 = rho0 ? rho0[ct] - R(1) : R(0);
+            v[i] = feq_shifted<R>(k, r1, u0[ct], u0[N + ct], u0[2 * N + ct], d.incomp);
+            if (bounce && d.flags[t] == 2 && d.moving_on) v[i] += wall_term<R>(d, i);
+        }
+        split_store<S>(d, P, c, v);
+        return;
+    }
     if (d.layout == LAYOUT_AA_NAT) {  // AA natural layout: f^0_i(x) at the cell itself
         const R r1 = rho0 ? rho0[cc] - R(1) : R(0);
 #pragma unroll
@@ -723,6 +1018,19 @@ __global__ void __launch_bounds__(256)
         return;
     }
     const long long N = d.n_cells, cc = canon_index(d.g, x, y, z);
+    if constexpr (is_split(S)) {  // the 19 values this cell holds, written as J and remainders
+        double v[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const int t = push_dst(d.g, x, y, z, i);
+            long long off = (long long)i * N + canon_neighbor(d.g, x, y, z, i);
+            const bool bounce = FLAGS && d.flags[t];
+            if (bounce) off = (long long)opp(i) * N + cc;
+            v[i] = IOFmt<D>::get(in + off) + (bounce && d.flags[t] == 2 && d.moving_on ? d.wc[i] : 0.0);
+        }
+        split_store<S>(d, P, c, v);
+        return;
+    }
     if (d.layout == LAYOUT_AA_NAT) {  // AA natural layout: s_i(x) at the cell itself
 #pragma unroll
         for (int i = 0; i < Q; ++i) IOFmt<S>::put(P + (long long)i * d.g.qs + c, IOFmt<D>::get(in + i * N + cc));
@@ -909,7 +1217,7 @@ static cudaError_t launch_step3f(const Dev &d, const void *src, void *dst, void 
 // box +3%). The 16-bit link form with flags keeps whole rows there (the flat
 // form spilled more: -4.5%); so does FP64.
 template <int S, bool FLAGS> constexpr bool flat_preferred() {
-    return S == LBM_F32 || (S != LBM_F64 && !FLAGS);
+    return S == LBM_F32 || is_split(S) || (S != LBM_F64 && !FLAGS);
 }
 
 template <int S, bool FLAGS, int FORCE>
@@ -955,9 +1263,11 @@ static cudaError_t launch_step_tma4(const Dev &d, const void *src, void *dst, vo
 
 template <int S, bool FLAGS, int FORCE>
 static cudaError_t launch_step3_any(const Dev &d, const void *src, void *dst, void *tape) {
-    if (tma_eligible<S>(d))
-        return tape ? launch_step_tma4<S, FLAGS, FORCE, true>(d, src, dst, tape)
-                    : launch_step_tma4<S, FLAGS, FORCE, false>(d, src, dst, tape);
+    if constexpr (!is_split(S)) {  // (the moment-split formats have no staged form)
+        if (tma_eligible<S>(d))
+            return tape ? launch_step_tma4<S, FLAGS, FORCE, true>(d, src, dst, tape)
+                        : launch_step_tma4<S, FLAGS, FORCE, false>(d, src, dst, tape);
+    }
     return launch_step3<S, FLAGS, FORCE>(d, src, dst, tape);
 }
 
@@ -1107,8 +1417,8 @@ cudaError_t Ops<S>::get_state(const Dev &d, const void *lat, void *dst, int fmt)
     switch (fmt) {
     case LBM_F64: return launch_get<S, LBM_F64>(d, lat, dst);
     case LBM_F32: return launch_get<S, LBM_F32>(d, lat, dst);
-    case LBM_F16S: return launch_get<S, LBM_F16S>(d, lat, dst);
-    case LBM_BF16S: return launch_get<S, LBM_BF16S>(d, lat, dst);
+    case LBM_F16S: case LBM_F16M: return launch_get<S, LBM_F16S>(d, lat, dst);
+    case LBM_BF16S: case LBM_BF16M: return launch_get<S, LBM_BF16S>(d, lat, dst);
     }
     return cudaErrorInvalidValue;
 }
@@ -1118,8 +1428,8 @@ cudaError_t Ops<S>::set_state(const Dev &d, void *lat, const void *src, int fmt)
     switch (fmt) {
     case LBM_F64: return launch_set<S, LBM_F64>(d, lat, src);
     case LBM_F32: return launch_set<S, LBM_F32>(d, lat, src);
-    case LBM_F16S: return launch_set<S, LBM_F16S>(d, lat, src);
-    case LBM_BF16S: return launch_set<S, LBM_BF16S>(d, lat, src);
+    case LBM_F16S: case LBM_F16M: return launch_set<S, LBM_F16S>(d, lat, src);
+    case LBM_BF16S: case LBM_BF16M: return launch_set<S, LBM_BF16S>(d, lat, src);
     }
     return cudaErrorInvalidValue;
 }

@@ -47,15 +47,18 @@ struct Dev {
     bool incomp;           // incompressible equilibrium (He & Luo) instead of Qian's
     bool row_staging;      // use the TMA row-staged step kernel where it applies
     int num_sms;           // multiprocessors of the device (grid of persistent kernels)
+    long long jo;          // moment-split formats: element offset of the momentum words in a lattice
 };
 
 // Bounce-back form per storage format (see k_step), the measured fastest on
 // the walled channel: FP64 load side, FP32 mask-guided reload, 16-bit link
 // kernel (BB_NANS, NaN marks with a rho-gated fix-up, is kept as the
-// measured alternative).
+// measured alternative). The moment-split formats take the mask-guided
+// reload: a bounced value is rebuilt from the cell's own momentum, which a
+// copy into a solid slot could not carry.
 enum { BB_LOAD = 0, BB_LINKS = 1, BB_NANS = 2, BB_MFIX = 3 };
 __host__ __device__ constexpr int bounce_mode(int s) {
-    return s == LBM_F64 ? BB_LOAD : (s == LBM_F32 ? BB_MFIX : BB_LINKS);
+    return s == LBM_F64 ? BB_LOAD : ((s == LBM_F32 || is_split(s)) ? BB_MFIX : BB_LINKS);
 }
 // The form in which a solid cell's slot holds the value bounced into it, so
 // the gather needs no flags (links).

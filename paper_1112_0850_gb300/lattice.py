@@ -17,8 +17,12 @@ def _real_dtype(storage):
     return torch.float64 if storage == capi.LBM_F64 else torch.float32
 
 
+# element type of the canonical state arrays of each format (the moment-split
+# formats exchange plain shifted deviations in their 16-bit element type)
 _FMT_DTYPE = {capi.LBM_F64: torch.float64, capi.LBM_F32: torch.float32, capi.LBM_F16S: torch.float16,
-              capi.LBM_BF16S: torch.bfloat16}
+              capi.LBM_BF16S: torch.bfloat16, capi.LBM_F16M: torch.float16, capi.LBM_BF16M: torch.bfloat16}
+_DTYPE_FMT = {torch.float64: capi.LBM_F64, torch.float32: capi.LBM_F32, torch.float16: capi.LBM_F16S,
+              torch.bfloat16: capi.LBM_BF16S}
 
 
 def _storage_code(s):
@@ -30,7 +34,8 @@ class Lattice:
 
     flags: optional uint8 array [nz][ny][nx] (0 fluid, 2 moving wall, other nonzero solid);
     force: optional uniform body force (3,); storage: "f64" | "f32" | "f16s" |
-    "bf16s". Work is enqueued on `stream` (default: torch's current stream at
+    "bf16s" | "f16m" | "bf16m" (16-bit moment split: momentum plus remainders).
+    Work is enqueued on `stream` (default: torch's current stream at
     construction). row_align: bytes each padded row starts on (0 = pairs only,
     128 = the paper's padding).
     pattern: "pull" (two lattices) or "aa" (one lattice updated in place).
@@ -195,7 +200,7 @@ class Lattice:
         return out
 
     def set_state(self, state):
-        fmt = {v: k for k, v in _FMT_DTYPE.items()}[state.dtype]
+        fmt = _DTYPE_FMT[state.dtype]
         self._call("lbm_set_state", self._ptr(state, state.dtype, (capi.Q,) + self.shape), fmt)
 
     def new_halo(self):

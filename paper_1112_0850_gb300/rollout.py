@@ -10,6 +10,8 @@ state every `ckpt_every` steps (in format `ckpt_fmt`), the backward pass
 restores each checkpoint, recomputes its segment while recording the moments
 the adjoint needs (lbm_step_record), and then runs the segment's adjoint
 steps in reverse. Memory: one checkpoint per segment plus one segment's tape.
+Checkpoints default to the lattice's own storage format; a moment-split
+lattice (whose canonical state has no exact 16-bit form) keeps FP32 ones.
 """
 import torch
 
@@ -20,8 +22,8 @@ class LBMRollout(torch.autograd.Function):
     @staticmethod
     def forward(ctx, u0, F, lattice, steps, ckpt_every, ckpt_fmt=None):
         lat = lattice
-        fmt = lat.storage if ckpt_fmt is None else (capi.STORAGE[ckpt_fmt] if isinstance(ckpt_fmt, str)
-                                                    else int(ckpt_fmt))
+        own = capi.LBM_F32 if lat.storage in (capi.LBM_F16M, capi.LBM_BF16M) else lat.storage
+        fmt = own if ckpt_fmt is None else (capi.STORAGE[ckpt_fmt] if isinstance(ckpt_fmt, str) else int(ckpt_fmt))
         u0 = u0.detach().contiguous()
         F = F.detach().contiguous()
         lat.set_force_field(F)
@@ -34,7 +36,7 @@ class LBMRollout(torch.autograd.Function):
             ckpts.append((lat.get_state(fmt), n))
             lat.step(n)
             done += n
-        final = lat.get_state(lat.storage)
+        final = lat.get_state(own)
         _, u = lat.macros(with_rho=False)
         ctx.lat = lat
         ctx.ckpts = ckpts

@@ -11,13 +11,16 @@ from paper_1112_0850_gb300.lattice import Lattice
 # stated by the method's accuracy targets: FP64 storage 1e-12, FP32 1e-5,
 # 16-bit shifted storage 1e-3. bfloat16 keeps 8 significant bits: one
 # rounding of a deviation w_i (3 e.u) ~ 3e-3 costs ~2^-9 of it per step, and
-# over 20-100 steps that leaves 2e-3 to 6e-3 relative error in u, so bf16
-# storage misses the 1e-3 target; it is held to 1e-2 here and its measured
-# error is reported (binary16, 11 significant bits, meets 1e-3).
-TOL_U = {"f64": 1e-12, "f32": 1e-5, "f16s": 1e-3, "bf16s": 1e-2}
+# over the parity runs (20-100 steps) that leaves 2.2e-3 to 5.3e-3 relative
+# error in u, the same in the oracle's own emulation of the rounding (the
+# format's floor). BF16 shifted storage therefore misses the 1e-3 target; it is
+# held to that measured floor plus a margin (the moment-split bfloat16 format,
+# tests/test_split_gpu.py, is the one that meets it on smooth flows).
+TOL_U = {"f64": 1e-12, "f32": 1e-5, "f16s": 1e-3, "bf16s": 7e-3}
 STORAGES = ["f64", "f32", "f16s", "bf16s"]
-REAL = {"f64": torch.float64, "f32": torch.float32, "f16s": torch.float32, "bf16s": torch.float32}
-EMUL = {"f64": None, "f32": "f32", "f16s": "f16", "bf16s": "bf16"}
+REAL = {"f64": torch.float64, "f32": torch.float32, "f16s": torch.float32, "bf16s": torch.float32,
+        "f16m": torch.float32, "bf16m": torch.float32}
+EMUL = {"f64": None, "f32": "f32", "f16s": "f16", "bf16s": "bf16", "f16m": "f16m", "bf16m": "bf16m"}
 
 _built = False
 

@@ -74,9 +74,11 @@ def test_fp32_adjoint_matches_reference(storage):
     _, gu, gF = _gpu_grad(storage, flags, u0, F, ut, T, 0.6, 4)
     _, gur, gFr = oadj.gradients(u0, F, 0.6, T, ut, flags)
     m = fluid_mask(flags, u0.shape[1:])
+    eu, eF = rel_l2(gu, gur, m), rel_l2(gF, gFr, m)
+    print("%s adjoint vs FP64 reference: dL/du0 %.3e, dL/dF %.3e" % (storage, eu, eF))
     tol = 1e-4 if storage == "f32" else 2e-2
-    assert rel_l2(gu, gur, m) <= tol
-    assert rel_l2(gF, gFr, m) <= tol
+    assert eu <= tol
+    assert eF <= tol
 
 
 def test_checkpoint_interval_does_not_change_gradient():

@@ -57,7 +57,7 @@ SIZES = [(1, 1, 1), (1, 3, 2), (3, 1, 1), (2, 2, 2), (5, 4, 3), (8, 6, 5), (31, 
 
 
 @pytest.mark.parametrize("align", ["default", "128"])
-@pytest.mark.parametrize("fmt", [0, 1, 2, 3])
+@pytest.mark.parametrize("fmt", [0, 1, 2, 3, 4, 5])
 @pytest.mark.parametrize("size", SIZES, ids=lambda s: "x".join(map(str, s)))
 def test_launch_indices_in_bounds(lib, size, fmt, align):
     nx, ny, nz = size

@@ -1,9 +1,9 @@
 """The workload configurations at their stated sizes, end to end on the GPU.
 
 - Taylor-Green vortex, periodic 512^3, U0 = 0.02, tau = 0.52, 200 steps:
-  velocity and density of FP32 and 16-bit shifted storage against an FP64
-  run of the same kernels (the FP64 path is itself held to 1e-12 against the
-  oracle, here on a 64^3 Taylor-Green box).
+  velocity and density of FP32, 16-bit shifted and 16-bit moment-split
+  storage against an FP64 run of the same kernels (the FP64 path is itself
+  held to 1e-12 against the oracle, here on a 64^3 Taylor-Green box).
 - Adjoint, periodic 128^3, random solenoidal u0 (max 0.01), per-cell force
   N(0, 1e-6), 500 steps, checkpoints every 50: the FP32 gradient against the
   FP64 gradient of the same kernels, and a descent step lowers the loss.
@@ -61,7 +61,7 @@ def test_taylor_green_512_storage_accuracy():
     u0f, rho0f = u0.astype(np.float32), rho0.astype(np.float32)
     del u0, rho0
     errs = {}
-    for storage in ("f32", "f16s", "bf16s"):
+    for storage in ("f32", "f16s", "bf16s", "f16m", "bf16m"):
         lat = _lattice(n, n, n, tau, storage=storage)
         lat.init_equilibrium(torch.from_numpy(u0f), torch.from_numpy(rho0f))
         lat.step(T)
@@ -81,10 +81,18 @@ def test_taylor_green_512_storage_accuracy():
     # relaxes about T = s_eq + S/omega with a momentum-exact odd part, which
     # keeps such biases out (measured 1.0e-6; 1.5e-5 with the omega-folded form).
     assert errs["f32"][0] <= 1e-5
-    assert errs["f16s"][0] <= 1e-3
-    # BF16 keeps 8 significant bits of deviations of ~3e-3: storing the initial
-    # state alone costs ~9e-4 of the velocity, and 200 steps give 2.6e-3.
-    assert errs["bf16s"][0] <= 1e-2
+    assert errs["f16s"][0] <= 1e-3  # measured 3.1e-4
+    # Moment-split storage rounds only the remainder the linear equilibrium
+    # part leaves over (quadratic and non-equilibrium parts, ~1e-4 here): the
+    # 1e-3 target in both 16-bit formats (the oracle's emulation of the format
+    # gives 1.3e-4 for bfloat16 and 3.7e-5 for binary16 on a 64^3 box).
+    assert errs["f16m"][0] <= 1e-3
+    assert errs["bf16m"][0] <= 1e-3
+    # BF16 shifted storage keeps 8 significant bits of deviations of ~3e-3:
+    # storing the initial state alone costs ~9e-4 of the velocity, and 200
+    # steps give 2.6e-3 (measured), so it misses the 1e-3 target; held to its
+    # measured error plus a margin.
+    assert errs["bf16s"][0] <= 3.5e-3
 
 
 def _adjoint_grads(storage, n, T, K, tau, u0, F, ut, flags=None, ckpt_fmt=None):
@@ -163,4 +171,6 @@ def test_porous_channel_fp16_bf16_checkpoints_gradient():
     err = (torch.linalg.vector_norm((gF16 - gF32)[:, m]) / torch.linalg.vector_norm(gF32[:, m])).item()
     print("porous channel 384x256x256, 2000 steps: rel error of dL/dF, FP16 storage + BF16 checkpoints vs "
           "all-FP32: %.3e" % err)
-    assert np.isfinite(err) and err <= 0.1
+    # measured 1.6e-2 (storage rounding of the FP16 forward and the BF16
+    # checkpoints, carried through 2000 steps)
+    assert np.isfinite(err) and err <= 3e-2
