@@ -26,7 +26,9 @@ static __device__ __align__(256) double g_noalloc_partials[NA_MAX_BLOCKS * 4];
 
 constexpr int NA_MAX_DEVICES = 64;
 std::mutex g_noalloc_mu;
-void *g_noalloc_addr[NA_MAX_DEVICES];  // device address of g_noalloc_partials, per device
+// device address of g_noalloc_partials per device, as last looked up outside
+// a stream capture (used by calls made during one)
+void *g_noalloc_addr[NA_MAX_DEVICES];
 
 // Block b sums cells [b * 16384, (b + 1) * 16384): thread t takes cells
 // b * 16384 + t + 256 k, k = 0..63 (coalesced), adds rho = 1 + sum s_i and
@@ -73,15 +75,25 @@ __global__ void __launch_bounds__(NA_THREADS)
     }
 }
 
-// Device address of the scratch array on the current device, looked up once
-// per device (cudaGetSymbolAddress with that device current).
-cudaError_t noalloc_scratch(double **out) {
+// Device address of the scratch array on the current device
+// (cudaGetSymbolAddress with that device current). It is looked up afresh on
+// every call made outside a stream capture, so a device reset (which unloads
+// the module and may place the array elsewhere when it is loaded again) never
+// leaves a stale address behind; a call made while `st` is being captured
+// uses the address of the last call outside a capture on this device (the
+// first call on a device therefore belongs before any capture).
+cudaError_t noalloc_scratch(cudaStream_t st, double **out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= NA_MAX_DEVICES) return cudaErrorInvalidDevice;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) {
+        cudaGetLastError();  // (the legacy stream while another stream captures): take it as captured
+        cap = cudaStreamCaptureStatusActive;
+    }
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_addr[dev]) {
+    if (cap == cudaStreamCaptureStatusNone || !g_noalloc_addr[dev]) {
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_noalloc_partials);
         if (e != cudaSuccess) return e;
@@ -113,14 +125,14 @@ extern "C" lbm_status lbm_reduce_state_noalloc(const void *state, lbm_storage fm
     if (!state || !out || nx < 1 || ny < 1 || nz < 1 || fmt < LBM_F64 || fmt > LBM_BF16S) return LBM_ERR_ARG;
     const long long N = (long long)nx * ny * nz;
     if (N > NA_MAX_CELLS) return LBM_ERR_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     double *scratch = nullptr;
-    cudaError_t e = noalloc_scratch(&scratch);
+    cudaError_t e = noalloc_scratch(st, &scratch);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return LBM_ERR_CUDA;
     }
     const double F[3] = {force ? force[0] : 0.0, force ? force[1] : 0.0, force ? force[2] : 0.0};
-    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     switch (fmt) {
     case LBM_F64: e = launch_sum<LBM_F64>(state, N, flags, F, scratch, out, st); break;
     case LBM_F32: e = launch_sum<LBM_F32>(state, N, flags, F, scratch, out, st); break;
