@@ -76,7 +76,9 @@ def test_fp32_adjoint_matches_reference(storage):
     m = fluid_mask(flags, u0.shape[1:])
     eu, eF = rel_l2(gu, gur, m), rel_l2(gF, gFr, m)
     print("%s adjoint vs FP64 reference: dL/du0 %.3e, dL/dF %.3e" % (storage, eu, eF))
-    tol = 1e-4 if storage == "f32" else 2e-2
+    # measured 2.5e-7 / 1.6e-7 (FP32) and 8.6e-5 / 4.9e-5 (FP16 storage);
+    # held to about three times that
+    tol = 7.5e-7 if storage == "f32" else 2.5e-4
     assert eu <= tol
     assert eF <= tol
 
