@@ -10,10 +10,13 @@ flush is needed between steps.
 
 Prints one JSON line: value = million fluid-cell updates per second (MFLUPS,
 the paper's metric), the roofline of the step kernel against measured HBM
-bandwidth, the FP64 oracle timed on the host cores, an end-to-end figure
-through host buffers, the other storage formats and the adjoint/forward
-step-time ratio on the same workload, the 512^3 Taylor-Green box in every
-format and pattern, and the cost of a z-slab halo exchange on that box.
+bandwidth, the FP64 oracle timed on the host cores beside the host copy
+bandwidth, an end-to-end figure through host buffers, the other storage
+formats and the adjoint/forward step-time ratio on the same workload, the
+512^3 Taylor-Green box in every format and pattern, and the cost of a z-slab
+halo exchange on that box. The K timed steps run as 5 back-to-back
+sub-regions (median and spread of the step time beside the whole-region
+value); every other leg is timed as 5 repetitions of at least 10 ms each.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -42,7 +45,9 @@ METRIC = "D3Q19 MLUPS & % of HBM roofline per precision; adjoint/forward step-ti
 NX, NY, NZ, TAU, GX, SOLID = 256, 128, 128, 0.55, 1e-6, 0.10
 WORKLOAD = ("D3Q19 BGK channel 256x128x128 (x periodic), walls y=0/127 z=0/127 + seeded spheres r 3-6 "
             "(10% solid), halfway bounce-back, g_x=1e-6, tau=0.55")
-PDF_BYTES = {"f64": 304, "f32": 152, "f16s": 76, "bf16s": 76}
+# algorithmic bytes per fluid-cell update: 19 loads + 19 stores of the stored
+# value; the moment-split formats also read and write one 8-byte momentum word
+PDF_BYTES = {"f64": 304, "f32": 152, "f16s": 76, "bf16s": 76, "f16m": 92, "bf16m": 92}
 FLAG_BYTES = 1
 STEP_KERNEL = "k_step"
 
@@ -291,6 +296,62 @@ def time_steps(torch, lat, steps, warmup):
     return e0.elapsed_time(e1) / 1e3
 
 
+REPS = 5          # repetitions of every timed region (median and spread reported)
+MIN_REP_S = 0.01  # device time of one repetition of a leg, at least (so >= 50 ms a leg)
+
+
+def time_reps(torch, stream, run, reps=REPS):
+    """Enqueue run() `reps` times back to back on `stream`, with a CUDA event
+    between repetitions; return the device seconds of each repetition."""
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(reps + 1)]
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    for k in range(reps):
+        run()
+        ev[k + 1].record(stream)
+    torch.cuda.synchronize()
+    return [ev[k].elapsed_time(ev[k + 1]) / 1e3 for k in range(reps)]
+
+
+def spread(per_step):
+    """Median, min, max and relative spread of per-step times (seconds)."""
+    v = sorted(per_step)
+    med = v[len(v) // 2]
+    return {"median_ms": med * 1e3, "min_ms": v[0] * 1e3, "max_ms": v[-1] * 1e3,
+            "spread": (v[-1] - v[0]) / med, "reps": len(v)}
+
+
+def leg(torch, lat, warmup=3):
+    """Time a lattice's steps: REPS repetitions of k steps each, k chosen so a
+    repetition takes at least MIN_REP_S of device time (one untimed repetition
+    first, which also captures the step graph where k >= 32). Returns
+    (median seconds per step, spread record)."""
+    lat.step(warmup)
+    t1 = time_steps(torch, lat, 2, 0) / 2
+    k = max(2, int(np.ceil(MIN_REP_S / max(t1, 1e-9))))
+    lat.step(k)
+    ts = time_reps(torch, lat.stream, lambda: lat.step(k))
+    rec = spread([t / k for t in ts])
+    rec["steps_per_rep"] = k
+    return rec["median_ms"] / 1e3, rec
+
+
+def host_copy_gbs(cores, nbytes=1 << 30, reps=5):
+    """Host copy bandwidth (STREAM copy: bytes read + bytes written per second)
+    with torch's multithreaded CPU copy over `cores` threads, best of reps."""
+    import torch
+    torch.set_num_threads(cores)
+    a = torch.ones(nbytes // 8, dtype=torch.float64)
+    b = torch.empty_like(a)
+    b.copy_(a)
+    best = float("inf")
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        b.copy_(a)
+        best = min(best, time.perf_counter() - t0)
+    return 2 * nbytes / best / 1e9
+
+
 def sweep():
     """Throughput against domain size (periodic n^3 boxes, the paper's domain
     sweeps, Sec. 7) and the effect of padding rows to 128 bytes (Sec. 6): MLUPS
@@ -306,18 +367,18 @@ def sweep():
         rng = np.random.default_rng(1)
         u = torch.tensor(0.01 * rng.standard_normal((3, n, n, n)), dtype=lat.real).cuda()
         lat.init_equilibrium(u)
-        k = int(min(2000, max(10, 4e9 / n ** 3)))
-        t = time_steps(torch, lat, k, 5) / k
+        t, rec = leg(torch, lat, 5)
         pitch = lat.info.pitch
         lat.close()
         gbs = n ** 3 * PDF_BYTES[storage] / t / 1e9
-        return {"n": n, "storage": storage, "pitch": pitch, "steps": k, "mlups": n ** 3 / t / 1e6, "gbs": gbs,
-                "frac": gbs / peak}
+        return {"n": n, "storage": storage, "pitch": pitch, "mlups": n ** 3 / t / 1e6, "gbs": gbs,
+                "frac": gbs / peak, "timing": rec}
 
     sizes = [16, 24, 32, 48, 64, 96, 128, 160, 200, 256, 320, 384, 448, 512]
-    out = {"sweep": [run(n, s) for s in ("f32", "f16s") for n in sizes],
-           "padding": [run(n, s, ra) for s in ("f32", "f16s") for n in (200, 250)
-                       for ra in (0, 128)],
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        res = [run(n, s) for s in ("f32", "f16s", "bf16m") for n in sizes]
+        pad = [run(n, s, ra) for s in ("f32", "f16s") for n in (200, 250) for ra in (0, 128)]
+    out = {"sweep": res, "padding": pad, "clocks": clk.summary(),
            "note": "periodic boxes, random velocities (0.01), tau 0.6; small boxes fit in the 129 MB L2, so "
                    "their fraction of HBM copy bandwidth can exceed 1; padding: row_align 128 = the paper's "
                    "128-byte rows, 0 = rows padded only to a pair of cells (the default)"}
@@ -333,7 +394,7 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip other precisions, adjoint ratio, CPU baseline")
     ap.add_argument("--case", default="channel", choices=["channel", "taylor-green"],
                     help="headline workload: the walled channel (default) or a periodic Taylor-Green box")
-    ap.add_argument("--storage", default="f32", choices=["f64", "f32", "f16s", "bf16s"])
+    ap.add_argument("--storage", default="f32", choices=["f64", "f32", "f16s", "bf16s", "f16m", "bf16m"])
     ap.add_argument("--n", type=int, default=512, help="Taylor-Green box edge")
     ap.add_argument("--pattern", default="pull", choices=["pull", "aa"],
                     help="two lattices (pull) or one lattice updated in place (AA pattern)")
@@ -410,24 +471,26 @@ def main():
         flag_bytes = 0
     n_fluid = lat.n_fluid
 
-    # ---- headline: FP32 steps, device-resident --------------------------------------------
+    # ---- headline: K steps, device-resident ------------------------------------------
+    # The K timed steps run as REPS back-to-back sub-regions with a CUDA event
+    # between them: `value` is K steps over the whole region, and the
+    # sub-regions give the median and spread of the step time.
     lat.step(args.warmup)
     torch.cuda.synchronize()
     barrier()
+    chunks = [args.steps // REPS + (1 if k < args.steps % REPS else 0) for k in range(REPS)]
+    chunks = [c for c in chunks if c > 0]
     with ClockSampler(torch.cuda.current_device()) as clk:
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(lat.stream)
-        lat.step(args.steps)
-        e1.record(lat.stream)
-        torch.cuda.synchronize()
+        it = iter(chunks)
+        ts = time_reps(torch, lat.stream, lambda: lat.step(next(it)), reps=len(chunks))
     barrier()
-    dt_local = e0.elapsed_time(e1) / 1e3
+    dt_local = sum(ts)
     dt = max_over_ranks(dt_local, world, "cuda")
     clocks = clk.summary()
     status = lat.status_word()
     value = aggregate_mflups(n_fluid * args.steps, world, dt)
     per_launch = dt_local / args.steps
+    head_spread = spread([t / c for t, c in zip(ts, chunks)])
     peak, peak_kind = measured_peaks()
     alg_bytes = n_fluid * PDF_BYTES[storage] + n_cells * flag_bytes
     achieved = alg_bytes / per_launch / 1e9
@@ -438,14 +501,15 @@ def main():
     e2e = None
     if not args.no_extras and args.case == "channel" and storage == "f32":
         # ---- other storage formats on the same workload -------------------------------------
-        per_prec = {"f32": {"mflups": n_fluid / per_launch / 1e6, "gbs": achieved, "frac": achieved / peak}}
-        ks = max(10, args.steps // 5)
-        for s in ("f64", "f16s", "bf16s"):
+        per_prec = {"f32": {"mflups": n_fluid / per_launch / 1e6, "gbs": achieved, "frac": achieved / peak,
+                            "bytes_per_lup": PDF_BYTES["f32"], "timing": head_spread}}
+        for s in ("f64", "f16s", "bf16s", "f16m", "bf16m"):
             l2 = Lattice(NX, NY, NZ, TAU, flags=flags, force=F, storage=s)
             l2.init_equilibrium(l2.zeros(3))
-            t = time_steps(torch, l2, ks, args.warmup) / ks
+            t, rec = leg(torch, l2, args.warmup)
             gbs = (n_fluid * PDF_BYTES[s] + n_cells * FLAG_BYTES) / t / 1e9
-            per_prec[s] = {"mflups": n_fluid / t / 1e6, "gbs": gbs, "frac": gbs / peak}
+            per_prec[s] = {"mflups": n_fluid / t / 1e6, "gbs": gbs, "frac": gbs / peak, "bytes_per_lup": PDF_BYTES[s],
+                           "timing": rec}
             l2.close()
         extras["per_precision"] = per_prec
         # ---- the 512^3 periodic Taylor-Green box, every storage format -----------------
@@ -453,16 +517,16 @@ def main():
         n = 512
         rho_tg, u_tg = lbm_inputs.taylor_green(n, 0.02, dtype=np.float32)
         rho_tg, u_tg = torch.from_numpy(rho_tg).cuda(), torch.from_numpy(u_tg).cuda()
-        for s in ("f32", "f16s", "bf16s", "f64"):
+        for s in ("f32", "f16s", "bf16s", "f16m", "bf16m", "f64"):
             l2 = Lattice(n, n, n, 0.52, storage=s)
             if s == "f64":
                 l2.init_equilibrium(u_tg.double(), rho_tg.double())
             else:
                 l2.init_equilibrium(u_tg, rho_tg)
-            kk = 10 if s == "f64" else 40
-            t = time_steps(torch, l2, kk, 3) / kk
+            t, rec = leg(torch, l2)
             gbs = n ** 3 * PDF_BYTES[s] / t / 1e9
-            tg[s] = {"mlups": n ** 3 / t / 1e6, "gbs": gbs, "frac": gbs / peak, "ms_per_step": t * 1e3}
+            tg[s] = {"mlups": n ** 3 / t / 1e6, "gbs": gbs, "frac": gbs / peak, "ms_per_step": t * 1e3,
+                     "bytes_per_lup": PDF_BYTES[s], "timing": rec}
             l2.close()
         extras["taylor_green_512"] = tg
         # ---- the AA pattern (one lattice, in place) on both workloads ------------------
@@ -470,64 +534,68 @@ def main():
         for s in ("f32", "f16s", "bf16s"):
             l2 = Lattice(n, n, n, 0.52, storage=s, pattern="aa")
             l2.init_equilibrium(u_tg, rho_tg)
-            t = time_steps(torch, l2, 40, 4) / 40
+            t, rec = leg(torch, l2, 4)
             gbs = n ** 3 * PDF_BYTES[s] / t / 1e9
-            aa["taylor_green_512_" + s] = {"mlups": n ** 3 / t / 1e6, "gbs": gbs, "frac": gbs / peak}
+            aa["taylor_green_512_" + s] = {"mlups": n ** 3 / t / 1e6, "gbs": gbs, "frac": gbs / peak, "timing": rec}
             l2.close()
         for s in ("f32", "f16s"):
             l2 = Lattice(NX, NY, NZ, TAU, flags=flags, force=F, storage=s, pattern="aa")
             l2.init_equilibrium(l2.zeros(3))
-            t = time_steps(torch, l2, ks, args.warmup) / ks
+            t, rec = leg(torch, l2, args.warmup)
             gbs = (n_fluid * PDF_BYTES[s] + n_cells * FLAG_BYTES) / t / 1e9
-            aa["channel_" + s] = {"mflups": n_fluid / t / 1e6, "gbs": gbs, "frac": gbs / peak}
+            aa["channel_" + s] = {"mflups": n_fluid / t / 1e6, "gbs": gbs, "frac": gbs / peak, "timing": rec}
             l2.close()
         extras["aa_pattern"] = aa
         # ---- the 512^3 box as two z-slabs on this GPU: what the halo exchange costs ---------
         from paper_1112_0850_gb300.slabs import SlabSet
         sl = SlabSet(n, n, n, 0.52, 2, storage="f32")
         sl.init_equilibrium(u_tg, rho_tg)
-        t_sl = time_steps(torch, sl, 10, 3) / 10  # an exchange, then a step of each slab
-        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t_sl, rec_sl = leg(torch, sl)  # an exchange, then a step of each slab
         for _ in range(3):
             sl.exchange()
-        torch.cuda.synchronize()
-        ev0.record(sl.stream)
-        for _ in range(20):
-            sl.exchange()
-        ev1.record(sl.stream)
-        torch.cuda.synchronize()
-        t_ex = ev0.elapsed_time(ev1) / 1e3 / 20
+        ts_ex = time_reps(torch, sl.stream, lambda: [sl.exchange() for _ in range(20)])
+        t_ex = spread([t / 20 for t in ts_ex])["median_ms"] / 1e3
         face = 5 * n * n * 4  # five FP32 populations of one 512^2 plane
         sl.overlap = True  # the exchange on a second stream while the interior planes update
-        t_ov = time_steps(torch, sl, 10, 3) / 10
+        t_ov, rec_ov = leg(torch, sl)
         extras["z_slabs"] = {
             "workload": "Taylor-Green 512^3 FP32 as 2 z-slabs of 256 planes plus 2 ghost planes each",
             "mlups": n ** 3 / t_sl / 1e6, "exchange_us": t_ex * 1e6, "face_bytes": face,
             "exchange_gbs": 16 * face / t_ex / 1e9, "exchange_share_of_step": t_ex / t_sl,
-            "mlups_overlapped": n ** 3 / t_ov / 1e6}
+            "mlups_overlapped": n ** 3 / t_ov / 1e6, "timing": rec_sl, "timing_overlapped": rec_ov}
         sl.close()
         del rho_tg, u_tg
         # ---- adjoint / forward step-time ratio (FP32, per-cell force gradient) -------------
-        K = 50
+        K = 100
         tape = lat.new_tape(K)
         gF = lat.zeros(3)
         lat.adjoint_seed(lat.zeros(3).add_(1e-3), None, gF)
         st = lat.stream
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
         lat.step_record(K, tape)
         lat.adjoint_step(K, tape, gF)
-        torch.cuda.synchronize()
-        ev[0].record(st)
-        lat.step_record(K, tape)
-        ev[1].record(st)
-        lat.adjoint_step(K, tape, gF)
-        ev[2].record(st)
-        torch.cuda.synchronize()
-        t_rec = ev[0].elapsed_time(ev[1]) / 1e3 / K
-        t_adj = ev[1].elapsed_time(ev[2]) / 1e3 / K
-        extras["adjoint_forward_ratio"] = (t_rec + t_adj) / per_launch
-        extras["adjoint_forward_ratio_no_recompute"] = t_adj / per_launch
+        ratios, ratios_nr, t_adjs = [], [], []
+        for _ in range(REPS):
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            torch.cuda.synchronize()
+            ev[0].record(st)
+            lat.step_record(K, tape)
+            ev[1].record(st)
+            lat.adjoint_step(K, tape, gF)
+            ev[2].record(st)
+            torch.cuda.synchronize()
+            t_rec = ev[0].elapsed_time(ev[1]) / 1e3 / K
+            t_adj = ev[1].elapsed_time(ev[2]) / 1e3 / K
+            ratios.append((t_rec + t_adj) / head_spread["median_ms"] * 1e3)
+            ratios_nr.append(t_adj / head_spread["median_ms"] * 1e3)
+            t_adjs.append(t_adj)
+        ratios.sort()
+        ratios_nr.sort()
+        t_adj = sorted(t_adjs)[REPS // 2]
+        extras["adjoint_forward_ratio"] = ratios[REPS // 2]
+        extras["adjoint_forward_ratio_no_recompute"] = ratios_nr[REPS // 2]
+        extras["adjoint_forward_ratio_range"] = [ratios[0], ratios[-1]]
         extras["adjoint_step_gbs"] = (n_fluid * (76 + 76 + 16 + 24) + n_cells) / t_adj / 1e9
+        extras["adjoint_timing"] = dict(spread(t_adjs), steps_per_rep=K)
         del tape, gF
         # ---- end to end through the C-ABI with host buffers --------------------------------
         u0_host = torch.zeros((3, NZ, NY, NX), dtype=torch.float32).pin_memory()
@@ -553,7 +621,12 @@ def main():
         # ---- CPU baseline: the oracle on a bounded sample -----------------------------------
         if rank == 0 and world == 1:
             v, cores, desc, _, _ = oracle_baseline(flags, 10.0)
-            cpu = {"value": v, "unit": "MFLUPS", "cores": cores, "kind": "oracle", "sample": desc}
+            copy = host_copy_gbs(cores)
+            cpu = {"value": v, "unit": "MFLUPS", "cores": cores, "kind": "oracle", "sample": desc,
+                   "host_copy_gbs": copy,
+                   "host_copy_how": "torch CPU copy of 1 GiB FP64 over %d threads, read + write bytes, best of 5" % cores,
+                   "host_model_mflups_fp64": copy * 1e3 / 456.0,
+                   "host_model_note": "the paper's CPU model (Sec. 4): 456 B per FP64 update with write-allocate"}
 
     lat_bytes = lat.info.lattice_bytes
     lat.close()
@@ -564,7 +637,8 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if storage == "f64" else "f32",
             "data": "synthetic",
             "config": {"workload": workload, "n_cells": n_cells, "n_fluid": n_fluid,
-                       "storage": storage + " (shifted f - w)",
+                       "storage": storage + (" (moment split: 16-bit momentum + remainders)" if storage.endswith("m")
+                                             else " (shifted f - w)"),
                        "pattern": args.pattern,
                        "l2": "no flush: the %s (%.0f MB each) exceed%s the 129 MB L2" % (
                            "lattice" if args.pattern == "aa" else "two lattices", lat_bytes / 1e6,
@@ -578,7 +652,7 @@ def main():
                          "peak_source": peak_kind + " hbm_gbs (MEASURED_PEAKS.json)",
                          "alg_bytes_per_launch": alg_bytes},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps, "clocks": clocks,
-            "status_word": status,
+            "status_word": status, "timing": dict(head_spread, sub_regions=len(chunks)),
         }
         line.update(extras)
         print(json.dumps(line), flush=True)
