@@ -217,6 +217,77 @@ __global__ void __launch_bounds__(256, AdjBlocks<R>::value)
     }
 }
 
+// The FP32 reverse step with one cell per thread: a warp's 4-byte loads of 32
+// consecutive cells already fill whole 128-byte lines, so FP32 needs no cell
+// pairs, and one cell's 19 adjoint populations, tape and gradient fit in 64
+// registers, so 4 blocks of 256 threads are resident per SM (the paired
+// kernel holds 2 at 128 registers, and its long-scoreboard waits were the
+// top stall). Threads take the cells of a plane's box rows in order, across
+// row ends. A solid cell stores zeros (its slots are never read), so that
+// every 32-byte sector of a lattice row is written whole.
+constexpr int ADJ1_BLOCKS = 4;
+
+template <bool FLAGS, bool FORCE>
+__global__ void __launch_bounds__(256, ADJ1_BLOCKS)
+    k_adj_step1(const Dev d, const float *__restrict__ lam_in, float *__restrict__ lam_out,
+                const float *__restrict__ tape, float *__restrict__ grad_F) {
+    const Geom &g = d.g;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int r = k / g.nx;
+    if (r >= d.P.nyr) return;
+    const int x = k - r * g.nx, y = d.P.y0 + r, z = d.P.z0 + blockIdx.y;
+    const int c = cell_index(g, x, y, z);
+    const long long qs = g.qs;
+    uint32_t m = 0u;
+    if (FLAGS) {
+        m = __ldg(d.mask + c);
+        if (m & SOLID_BIT) {
+#pragma unroll
+            for (int i = 0; i < Q; ++i) lam_out[(long long)i * qs + c] = 0.0f;
+            return;
+        }
+    }
+    const long long N = d.n_cells, cc = canon_index(g, x, y, z);
+    float Gx = 0.0f, Gy = 0.0f, Gz = 0.0f;
+    if (grad_F) {  // loaded with the gather, not after the collision
+        Gx = grad_F[cc];
+        Gy = grad_F[N + cc];
+        Gz = grad_F[2 * N + cc];
+    }
+    float mu[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        // mu_i(x) = lambda_i(x + e_i), or lambda_opp(i)(x) where x + e_i is solid
+        const int src = (wrap1(z + ez(i), g.nz) * g.ny + wrap1(y + ey(i), g.ny)) * g.pitch + wrap1(x + ex(i), g.nx);
+        const bool b = FLAGS && i > 0 && ((m >> i) & 1u);
+        mu[i] = __ldg(lam_in + (b ? (long long)opp(i) * qs + c : (long long)i * qs + src));
+    }
+    const float rho = __ldg(tape + c), ux = __ldg(tape + qs + c), uy = __ldg(tape + 2 * qs + c),
+                uz = __ldg(tape + 3 * qs + c);
+    float Fx = 0.0f, Fy = 0.0f, Fz = 0.0f;
+    if (FORCE) {
+        if (d.Ffield) {
+            const float *F = static_cast<const float *>(d.Ffield);
+            Fx = __ldg(F + c);
+            Fy = __ldg(F + qs + c);
+            Fz = __ldg(F + 2 * qs + c);
+        } else {
+            Fx = float(d.F[0]);
+            Fy = float(d.F[1]);
+            Fz = float(d.F[2]);
+        }
+    }
+    float gx, gy, gz;
+    adj_collide<float, FORCE>(mu, rho, ux, uy, uz, Fx, Fy, Fz, float(d.omega), gx, gy, gz, d.incomp);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) __stcs(lam_out + (long long)i * qs + c, mu[i]);
+    if (grad_F) {
+        grad_F[cc] = Gx + gx;
+        grad_F[N + cc] = Gy + gy;
+        grad_F[2 * N + cc] = Gz + gz;
+    }
+}
+
 // dL/du0 and dL/drho0 through f^0 = f_eq(rho0, u0):
 //   dL/du0 = rho0 sum_i lambda_i w_i [3 e_i + 9 (e_i.u0) e_i - 3 u0]
 //   dL/drho0 = sum_i lambda_i w_i [1 + 3 e_i.u0 + 9/2 (e_i.u0)^2 - 3/2 u0.u0]
@@ -283,9 +354,26 @@ static cudaError_t launch_adj_step(const Dev &d, const void *li, void *lo, const
                        : launch_adj_step2<R, FLAGS, false>(d, li, lo, tape, gF);
 }
 
+// FP32: one cell per thread over the cells of the fluid box's rows.
+template <bool FLAGS>
+static cudaError_t launch_adj_step1(const Dev &d, const void *li, void *lo, const void *tape, void *gF) {
+    const dim3 grid((unsigned)(((long long)d.P.nyr * d.g.nx + 255) / 256), d.P.nzr);
+    const float *a = static_cast<const float *>(li);
+    const float *t = static_cast<const float *>(tape);
+    float *b = static_cast<float *>(lo), *G = static_cast<float *>(gF);
+    if (d.force_on)
+        k_adj_step1<FLAGS, true><<<grid, 256, 0, d.stream>>>(d, a, b, t, G);
+    else
+        k_adj_step1<FLAGS, false><<<grid, 256, 0, d.stream>>>(d, a, b, t, G);
+    return cudaGetLastError();
+}
+
 template <class R>
 cudaError_t AdjOps<R>::step(const Dev &d, const void *lam_in, void *lam_out, const void *tape_k, void *grad_F) {
     if (d.flags && !d.mask) return cudaErrorInvalidValue;  // the reverse gather reads the push masks
+    if (sizeof(R) == 4)
+        return d.flags ? launch_adj_step1<true>(d, lam_in, lam_out, tape_k, grad_F)
+                       : launch_adj_step1<false>(d, lam_in, lam_out, tape_k, grad_F);
     return d.flags ? launch_adj_step<R, true>(d, lam_in, lam_out, tape_k, grad_F)
                    : launch_adj_step<R, false>(d, lam_in, lam_out, tape_k, grad_F);
 }

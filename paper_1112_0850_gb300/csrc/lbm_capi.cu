@@ -1041,6 +1041,7 @@ int64_t lbm_check_launch_indices(int nx, int ny, int nz, lbm_storage fmt, int ro
                     visited2 += has1 ? 2 : 1;
                     const int c = cell_index(g, x0, y, z);
                     if (c % 2 || !in_row(c - x0, x0) || !in_row(c - x0, x0 + 1)) ++bad;  // pair at c, c + 1
+                    if ((nx & 1) && x0 == 0 && !in_row(c, nx)) ++bad;  // split formats' copy of cell 0 after an odd row
                     const int xa = wrap1(x0 - 1, nx), xb = wrap1(x0 + 1, nx), xc = has1 ? wrap1(x0 + 2, nx) : x0;
                     for (int j = 1; j < Q; ++j)  // store-side bounce-back targets
                         if (!cell_ok(push_dst(g, x0, y, z, j)) || (has1 && !cell_ok(push_dst(g, x0 + 1, y, z, j))))
@@ -1064,6 +1065,23 @@ int64_t lbm_check_launch_indices(int nx, int ny, int nz, lbm_storage fmt, int ro
     };
     walk_pairs(Prows, false);
     walk_pairs(flat_launch(Prows), true);  // the two-grid step's launch when rows leave lanes idle
+    // the FP32 reverse step, one cell per thread over the box rows in order
+    {
+        long long visited1 = 0;
+        const long long cells = (long long)Prows.nyr * nx, nblk = (cells + 255) / 256;
+        for (int bz = 0; bz < Prows.nzr; ++bz)
+            for (long long k = 0; k < nblk * 256; ++k) {
+                const long long r = k / nx;
+                if (r >= Prows.nyr) continue;
+                ++visited1;
+                const int x = (int)(k - r * nx), y = Prows.y0 + (int)r, z = Prows.z0 + bz;
+                const int c = cell_index(g, x, y, z);
+                if (!cell_ok(c) || canon_index(g, x, y, z) >= N) ++bad;
+                for (int i = 0; i < Q; ++i)
+                    if (!cell_ok(push_dst(g, x, y, z, i))) ++bad;
+            }
+        if (visited1 != N) ++bad;
+    }
     const RowLaunch &P = Prows;
     if (P.bx_threads * P.by_threads > 256 || P.bx_threads % 32 || P.by_threads < 1) ++bad;
     if (L.bx_threads * L.by_threads != 256 || L.bx_threads % 32) ++bad;

@@ -88,6 +88,14 @@ template <class T> __device__ __forceinline__ uint2 *split_words(const Dev &d, T
     return reinterpret_cast<uint2 *>(P + d.jo);
 }
 
+// In a row of odd length the padding cell after the last cell holds a copy of
+// the momentum word of the row's first cell (x = 0): the lone last cell of the
+// row, whose thread loads the word pair (nx - 1, nx), pulls its e_x = -1
+// values from cell 0 (periodic in x). Every writer of cell 0's word keeps it.
+__device__ __forceinline__ void split_ghost(const Dev &d, uint2 *J, int x, int c, uint2 w) {
+    if ((d.g.nx & 1) && x == 0) J[c + d.g.nx] = w;
+}
+
 // Round to the 16-bit format (nearest even) from float or double.
 template <int S> __device__ __forceinline__ unsigned split_pack(float a, float b) { return SplitJ<S>::pack(a, b); }
 template <int S> __device__ __forceinline__ unsigned split_pack(double a, double b) {
@@ -109,7 +117,7 @@ template <int S> __device__ __forceinline__ unsigned split_pack(double a, double
 // moment-split lattice: J = sum_i v_i e_i rounded to the format, then the
 // remainders g_i = v_i - K_i (e_i . J) rounded.
 template <int S, class V>
-__device__ __forceinline__ void split_store(const Dev &d, typename Stor<S>::T *P, int c, const V v[Q]) {
+__device__ __forceinline__ void split_store(const Dev &d, typename Stor<S>::T *P, int x, int c, const V v[Q]) {
     V jx = V(0), jy = V(0), jz = V(0);
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
@@ -126,6 +134,7 @@ __device__ __forceinline__ void split_store(const Dev &d, typename Stor<S>::T *P
         IOFmt<S>::put(P + (long long)i * d.g.qs + c, (double)g);
     }
     split_words(d, P)[c] = w;
+    split_ghost(d, split_words(d, P), x, c, w);
 }
 
 __device__ __forceinline__ bool is_solid(const uint8_t *flags, int c) { return flags && flags[c]; }
@@ -533,7 +542,7 @@ __device__ __forceinline__ void step_pair(const Dev &d, const Rows &rows, const 
 // values from its own word, and the store writes the pair's momentum word,
 // J = j + F (the momentum of the post-collision values: the Guo collision
 // adds F), rounded, then the remainders against it.
-template <int S, bool FLAGS, int FORCE, bool RECORD, bool RED = false>
+template <int S, bool FLAGS, int FORCE, bool RECORD, bool RED = false, bool ODD = false>
 __device__ __forceinline__ void step_pair_split(const Dev &d, const typename Stor<S>::T *__restrict__ src,
                                                 typename Stor<S>::T *__restrict__ dst, float *__restrict__ tape,
                                                 int x0, int y, int z, double *red = nullptr) {
@@ -555,12 +564,12 @@ __device__ __forceinline__ void step_pair_split(const Dev &d, const typename Sto
     const int xa = wrap1(x0 - 1, g.nx);              // e_x = +1, cell x0
     const int xb = wrap1(x0 + 1, g.nx);              // e_x = -1, cell x0
     const int xc = has1 ? wrap1(x0 + 2, g.nx) : x0;  // e_x = -1, cell x0 + 1 (e_x = +1 pulls from x0)
-    // the cell after the pair: x0 + 2, or, for the lone last cell of an odd
-    // row, its own e_x = -1 source xb (the row's first cell)
-    const int xn = has1 ? xc : xb;
     // Momentum words of the nine source rows (y - e_y, z - e_z), r = 3 (e_y + 1)
-    // + e_z + 1: the pair (x0, x0 + 1) of each, and cells xa and xn of the five
+    // + e_z + 1: the pair (x0, x0 + 1) of each, and cells xa and xc of the five
     // rows that directions with e_x = +-1 pull from (those with e_y e_z = 0).
+    // The lone last cell of an odd row pulls its e_x = -1 values from the
+    // row's first cell: its pair's second word is the copy of that cell's word
+    // kept after the row's last cell (split_ghost), so no lane needs a select.
     const uint2 *Js = split_words(d, src);
     uint4 jq[9];
     uint2 ja[9], jc[9];
@@ -571,7 +580,7 @@ __device__ __forceinline__ void step_pair_split(const Dev &d, const typename Sto
         jq[r] = __ldg(reinterpret_cast<const uint4 *>(Js + rb + x0));
         if (dy == 0 || dz == 0) {
             ja[r] = __ldg(Js + rb + xa);
-            jc[r] = __ldg(Js + rb + xn);
+            jc[r] = __ldg(Js + rb + xc);
         }
     }
     V s[Q];
@@ -597,8 +606,8 @@ __device__ __forceinline__ void step_pair_split(const Dev &d, const typename Sto
         } else if (ex(i) > 0) {
             wa = ja[r];
             wb = make_uint2(jq[r].x, jq[r].y);
-        } else {  // sources xb, xc: x0 + 1 and x0 + 2, or the row's first cell for a lone last cell
-            wa = has1 ? make_uint2(jq[r].z, jq[r].w) : jc[r];
+        } else {  // sources xb, xc: x0 + 1 (or its copy of cell 0 for a lone last cell) and x0 + 2
+            wa = make_uint2(jq[r].z, jq[r].w);
             wb = jc[r];
         }
         const V jx = make_float2(SplitJ<S>::lo(wa.x), SplitJ<S>::lo(wb.x));
@@ -685,7 +694,12 @@ __device__ __forceinline__ void step_pair_split(const Dev &d, const typename Sto
     // cell's own slots), so 32-byte sectors are written complete.
 #pragma unroll
     for (int i = 0; i < Q; ++i) Stor<S>::st2(dst + (long long)i * g.qs + c, s[i].x, s[i].y);
-    *reinterpret_cast<uint4 *>(split_words(d, dst) + c) = make_uint4(w0x, w0y, w1x, w1y);
+    uint2 *Jd = split_words(d, dst);
+    if (!ODD || has1)
+        *reinterpret_cast<uint4 *>(Jd + c) = make_uint4(w0x, w0y, w1x, w1y);
+    else  // the lone last cell of an odd row: the slot after it holds cell 0's copy
+        Jd[c] = make_uint2(w0x, w0y);
+    if (ODD) split_ghost(d, Jd, x0, c, make_uint2(w0x, w0y));
 }
 
 // Launch the step kernel of the link form as a programmatic dependent of the
@@ -694,7 +708,9 @@ __device__ __forceinline__ void step_pair_split(const Dev &d, const typename Sto
 constexpr int STEP_PDL = 1;
 
 // FLAT: the launch of d.PF (pairs in plane order), else of d.P (whole rows).
-template <int S, bool FLAGS, int FORCE, bool RECORD, bool FLAT = false>
+// ODD (moment-split formats only): rows of odd length, whose last cell is
+// alone in its pair (see split_ghost).
+template <int S, bool FLAGS, int FORCE, bool RECORD, bool FLAT = false, bool ODD = false>
 __global__ void __launch_bounds__(256, StepBlocks<S>::value)
     k_step(const Dev d, const typename Stor<S>::T *__restrict__ src, typename Stor<S>::T *__restrict__ dst,
            typename Stor<S>::R *__restrict__ tape) {
@@ -710,7 +726,7 @@ __global__ void __launch_bounds__(256, StepBlocks<S>::value)
                          threadIdx.y, x0, y, z))
         return;
     if constexpr (is_split(S))
-        step_pair_split<S, FLAGS, FORCE, RECORD>(d, src, dst, tape, x0, y, z);
+        step_pair_split<S, FLAGS, FORCE, RECORD, false, ODD>(d, src, dst, tape, x0, y, z);
     else
         step_pair<S, FLAGS, FORCE, RECORD>(d, GlobalRows<S>{src}, src, dst, tape, x0, y, z);
 }
@@ -719,7 +735,7 @@ __global__ void __launch_bounds__(256, StepBlocks<S>::value)
 // (the reduction of lbm_reduce without a pass of its own): every thread, in
 // the lattice or not, reaches the block reduction; partials[4 b + k] of block
 // b = blockIdx.y * gridDim.x + blockIdx.x, summed in a fixed order.
-template <int S, bool FLAGS, int FORCE, bool FLAT>
+template <int S, bool FLAGS, int FORCE, bool FLAT, bool ODD = false>
 __global__ void __launch_bounds__(256, StepBlocks<S>::value)
     k_step_reduce(const Dev d, const typename Stor<S>::T *__restrict__ src, typename Stor<S>::T *__restrict__ dst,
                   double *__restrict__ partials) {
@@ -729,7 +745,7 @@ __global__ void __launch_bounds__(256, StepBlocks<S>::value)
     if (pair_cell<FLAT>(d.g, FLAT ? d.PF : d.P, blockDim.x, blockDim.y, blockIdx.x, blockIdx.y, threadIdx.x,
                         threadIdx.y, x0, y, z)) {
         if constexpr (is_split(S))
-            step_pair_split<S, FLAGS, FORCE, false, true>(d, src, dst, nullptr, x0, y, z, red);
+            step_pair_split<S, FLAGS, FORCE, false, true, ODD>(d, src, dst, nullptr, x0, y, z, red);
         else
             step_pair<S, FLAGS, FORCE, false, GlobalRows<S>, true>(d, GlobalRows<S>{src}, src, dst, nullptr, x0, y,
                                                                   z, red);
@@ -948,7 +964,7 @@ __global__ void __launch_bounds__(256)
             v[i] = feq_shifted<R>(k, r1, u0[ct], u0[N + ct], u0[2 * N + ct], d.incomp);
             if (bounce && d.flags[t] == 2 && d.moving_on) v[i] += wall_term<R>(d, i);
         }
-        split_store<S>(d, P, c, v);
+        split_store<S>(d, P, x, c, v);
         return;
     }
     if (d.layout == LAYOUT_AA_NAT) {  // AA natural layout: f^0_i(x) at the cell itself
@@ -1028,7 +1044,7 @@ __global__ void __launch_bounds__(256)
             if (bounce) off = (long long)opp(i) * N + cc;
             v[i] = IOFmt<D>::get(in + off) + (bounce && d.flags[t] == 2 && d.moving_on ? d.wc[i] : 0.0);
         }
-        split_store<S>(d, P, c, v);
+        split_store<S>(d, P, x, c, v);
         return;
     }
     if (d.layout == LAYOUT_AA_NAT) {  // AA natural layout: s_i(x) at the cell itself
@@ -1178,7 +1194,7 @@ inline dim3 row_block(const Dev &d) { return dim3(d.L.bx_threads, d.L.by_threads
 inline dim3 step_grid(const Dev &d) { return dim3(d.P.nxb * d.P.nyb, d.P.nzr); }
 inline dim3 step_block(const Dev &d) { return dim3(d.P.bx_threads, d.P.by_threads); }
 
-template <int S, bool FLAGS, int FORCE, bool FLAT>
+template <int S, bool FLAGS, int FORCE, bool FLAT, bool ODD = false>
 static cudaError_t launch_step3f(const Dev &d, const void *src, void *dst, void *tape) {
     typedef typename Stor<S>::T T;
     typedef typename Stor<S>::R R;
@@ -1194,19 +1210,19 @@ static cudaError_t launch_step3f(const Dev &d, const void *src, void *dst, void 
         attr[0].val.programmaticStreamSerializationAllowed = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        cudaError_t e = tape ? cudaLaunchKernelEx(&cfg, k_step<S, FLAGS, FORCE, true, FLAT>, d,
+        cudaError_t e = tape ? cudaLaunchKernelEx(&cfg, k_step<S, FLAGS, FORCE, true, FLAT, ODD>, d,
                                                   static_cast<const T *>(src), static_cast<T *>(dst),
                                                   static_cast<R *>(tape))
-                             : cudaLaunchKernelEx(&cfg, k_step<S, FLAGS, FORCE, false, FLAT>, d,
+                             : cudaLaunchKernelEx(&cfg, k_step<S, FLAGS, FORCE, false, FLAT, ODD>, d,
                                                   static_cast<const T *>(src), static_cast<T *>(dst), (R *)nullptr);
         if (e != cudaSuccess) return e;
         return cudaGetLastError();
     }
     if (tape)
-        k_step<S, FLAGS, FORCE, true, FLAT><<<grid, block, 0, d.stream>>>(
+        k_step<S, FLAGS, FORCE, true, FLAT, ODD><<<grid, block, 0, d.stream>>>(
             d, static_cast<const T *>(src), static_cast<T *>(dst), static_cast<R *>(tape));
     else
-        k_step<S, FLAGS, FORCE, false, FLAT><<<grid, block, 0, d.stream>>>(
+        k_step<S, FLAGS, FORCE, false, FLAT, ODD><<<grid, block, 0, d.stream>>>(
             d, static_cast<const T *>(src), static_cast<T *>(dst), nullptr);
     return cudaGetLastError();
 }
@@ -1222,8 +1238,12 @@ template <int S, bool FLAGS> constexpr bool flat_preferred() {
 
 template <int S, bool FLAGS, int FORCE>
 static cudaError_t launch_step3(const Dev &d, const void *src, void *dst, void *tape) {
-    return d.flat_step || flat_preferred<S, FLAGS>() ? launch_step3f<S, FLAGS, FORCE, true>(d, src, dst, tape)
-                                                     : launch_step3f<S, FLAGS, FORCE, false>(d, src, dst, tape);
+    if constexpr (is_split(S))  // (always the flat launch)
+        return (d.g.nx & 1) ? launch_step3f<S, FLAGS, FORCE, true, true>(d, src, dst, tape)
+                            : launch_step3f<S, FLAGS, FORCE, true, false>(d, src, dst, tape);
+    else
+        return d.flat_step || flat_preferred<S, FLAGS>() ? launch_step3f<S, FLAGS, FORCE, true>(d, src, dst, tape)
+                                                         : launch_step3f<S, FLAGS, FORCE, false>(d, src, dst, tape);
 }
 
 // Shared memory of the row-staged step: two buffers of 19 padded rows.
@@ -1312,6 +1332,21 @@ cudaError_t Ops<S>::bounce(const Dev &d, void *dst) {
     return cudaGetLastError();
 }
 
+// The fused step-reduce kernel for one launch mapping (FLAT) and row parity (ODD).
+template <int S, bool FLAT, bool ODD>
+static void launch_step_reduce2(const Dev &d, const dim3 grid, const dim3 block, const typename Stor<S>::T *s,
+                                typename Stor<S>::T *t, double *partials) {
+    if (d.flags) {
+        if (d.Ffield) k_step_reduce<S, true, 2, FLAT, ODD><<<grid, block, 0, d.stream>>>(d, s, t, partials);
+        else if (d.force_on) k_step_reduce<S, true, 1, FLAT, ODD><<<grid, block, 0, d.stream>>>(d, s, t, partials);
+        else k_step_reduce<S, true, 0, FLAT, ODD><<<grid, block, 0, d.stream>>>(d, s, t, partials);
+    } else {
+        if (d.Ffield) k_step_reduce<S, false, 2, FLAT, ODD><<<grid, block, 0, d.stream>>>(d, s, t, partials);
+        else if (d.force_on) k_step_reduce<S, false, 1, FLAT, ODD><<<grid, block, 0, d.stream>>>(d, s, t, partials);
+        else k_step_reduce<S, false, 0, FLAT, ODD><<<grid, block, 0, d.stream>>>(d, s, t, partials);
+    }
+}
+
 template <int S>
 cudaError_t Ops<S>::step_reduce(const Dev &d, const void *src, void *dst, double *partials, double *out) {
     typedef typename Stor<S>::T T;
@@ -1322,26 +1357,15 @@ cudaError_t Ops<S>::step_reduce(const Dev &d, const void *src, void *dst, double
     const bool flat = d.flat_step || (d.flags ? flat_preferred<S, true>() : flat_preferred<S, false>());
     const RowLaunch &P = flat ? d.PF : d.P;
     const dim3 grid(P.nxb * P.nyb, P.nzr), block(P.bx_threads, P.by_threads);
-    if (flat) {
-        if (d.flags) {
-            if (d.Ffield) k_step_reduce<S, true, 2, true><<<grid, block, 0, d.stream>>>(d, s, t, partials);
-            else if (d.force_on) k_step_reduce<S, true, 1, true><<<grid, block, 0, d.stream>>>(d, s, t, partials);
-            else k_step_reduce<S, true, 0, true><<<grid, block, 0, d.stream>>>(d, s, t, partials);
-        } else {
-            if (d.Ffield) k_step_reduce<S, false, 2, true><<<grid, block, 0, d.stream>>>(d, s, t, partials);
-            else if (d.force_on) k_step_reduce<S, false, 1, true><<<grid, block, 0, d.stream>>>(d, s, t, partials);
-            else k_step_reduce<S, false, 0, true><<<grid, block, 0, d.stream>>>(d, s, t, partials);
-        }
+    if constexpr (is_split(S)) {  // (always the flat launch)
+        if (d.g.nx & 1)
+            launch_step_reduce2<S, true, true>(d, grid, block, s, t, partials);
+        else
+            launch_step_reduce2<S, true, false>(d, grid, block, s, t, partials);
+    } else if (flat) {
+        launch_step_reduce2<S, true, false>(d, grid, block, s, t, partials);
     } else {
-        if (d.flags) {
-            if (d.Ffield) k_step_reduce<S, true, 2, false><<<grid, block, 0, d.stream>>>(d, s, t, partials);
-            else if (d.force_on) k_step_reduce<S, true, 1, false><<<grid, block, 0, d.stream>>>(d, s, t, partials);
-            else k_step_reduce<S, true, 0, false><<<grid, block, 0, d.stream>>>(d, s, t, partials);
-        } else {
-            if (d.Ffield) k_step_reduce<S, false, 2, false><<<grid, block, 0, d.stream>>>(d, s, t, partials);
-            else if (d.force_on) k_step_reduce<S, false, 1, false><<<grid, block, 0, d.stream>>>(d, s, t, partials);
-            else k_step_reduce<S, false, 0, false><<<grid, block, 0, d.stream>>>(d, s, t, partials);
-        }
+        launch_step_reduce2<S, false, false>(d, grid, block, s, t, partials);
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
