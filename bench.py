@@ -22,7 +22,9 @@ value); every other leg is timed as 5 repetitions of at least 10 ms each.
 
 With N > 1 (torchrun), every rank runs an independent replica on its own GPU
 (weak scaling; the method needs no exchange between replicas); rank 0 prints
-the aggregate over the max-over-ranks time.
+the aggregate over the max-over-ranks time. With --decompose z the ranks
+instead share one lattice as z-slabs, exchanging halos every step over the
+process group (strong scaling).
 """
 import argparse
 import hashlib
@@ -385,6 +387,62 @@ def sweep():
     print(json.dumps(out), flush=True)
 
 
+def decomposed(args, torch, dist, world, rank):
+    """One lattice split over the ranks as z-slabs (slabs.RankSlab): every step
+    exchanges the five crossing populations of each face with the neighbouring
+    ranks (point-to-point; NCCL between GPUs, a local copy on one rank), then
+    steps the slab. value = the whole lattice's fluid-cell updates per second
+    (strong scaling: the lattice is fixed, each rank holds 1/N of it)."""
+    from paper_1112_0850_gb300.slabs import RankSlab
+    if world == 1:  # a one-rank group for the driver (its exchange is a local copy)
+        import socket
+        sck = socket.socket()
+        sck.bind(("127.0.0.1", 0))
+        port = sck.getsockname()[1]
+        sck.close()
+        dist.init_process_group("gloo", init_method="tcp://127.0.0.1:%d" % port, rank=0, world_size=1)
+    storage = args.storage
+    if args.case == "channel":
+        flags = workload_flags()
+        sl = RankSlab(NX, NY, NZ, TAU, flags=flags, force=(GX, 0.0, 0.0), storage=storage)
+        sl.init_equilibrium(torch.zeros((3, NZ, NY, NX), dtype=sl.lat.real))
+        n_units = int((flags == 0).sum())
+        workload = WORKLOAD
+    else:
+        n = args.n
+        sl = RankSlab(n, n, n, 0.52, storage=storage)
+        rho_tg, u_tg = lbm_inputs.taylor_green(n, 0.02, dtype=np.float32)
+        real = torch.float64 if storage == "f64" else torch.float32
+        sl.init_equilibrium(torch.from_numpy(u_tg).to(real), torch.from_numpy(rho_tg).to(real))
+        del rho_tg, u_tg
+        n_units = n ** 3
+        workload = "D3Q19 BGK Taylor-Green vortex, periodic %d^3, U0=0.02, tau=0.52" % n
+    sl.step(args.warmup)
+    torch.cuda.synchronize()
+    dist.barrier()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        ts = time_reps(torch, sl.stream, lambda: sl.step(max(1, args.steps // REPS)))
+    dist.barrier()
+    steps = REPS * max(1, args.steps // REPS)
+    dt = max_over_ranks(sum(ts), world, "cuda")
+    tot = sl.totals()
+    status = sl.lat.status_word()
+    slab_planes = sl.z1 - sl.z0
+    sl.close()
+    if rank == 0:
+        line = {"metric": METRIC, "value": n_units * steps / dt / 1e6, "unit": "MFLUPS" if args.case == "channel"
+                else "MLUPS", "n_gpus": world, "steps": steps, "warmup": args.warmup,
+                "ms_per_step": dt / steps * 1e3, "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
+                "dtype": "f64" if storage == "f64" else "f32", "data": "synthetic",
+                "config": {"workload": workload, "storage": storage, "decomposition": "z-slabs, one per rank",
+                           "planes_per_rank": slab_planes,
+                           "parallelism": "z-slabs over %d ranks, point-to-point halo exchange per step" % world},
+                "timing": spread([t / max(1, args.steps // REPS) for t in ts]), "clocks": clk.summary(),
+                "mass": float(tot[0]), "status_word": status, "gpu_launches": None}
+        print(json.dumps(line), flush=True)
+    dist.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -404,6 +462,9 @@ def main():
                     help="run K recorded steps, the seed and K reverse steps on the channel (for profilers) and exit")
     ap.add_argument("--record-traffic", nargs="+", metavar="KEY=REPORT",
                     help="write profiles/step_kernel_traffic.json from ncu reports and exit")
+    ap.add_argument("--decompose", choices=["z"], default=None,
+                    help="split one lattice over the ranks as z-slabs with a halo exchange per step "
+                         "(strong scaling), instead of independent replicas")
     args = ap.parse_args()
     if args.record_traffic:
         return record_traffic(args.record_traffic)
@@ -433,6 +494,9 @@ def main():
     def barrier():
         if world > 1:
             dist.barrier()
+
+    if args.decompose:
+        return decomposed(args, torch, dist, world, rank)
 
     flags = workload_flags()
     F = (GX, 0.0, 0.0)

@@ -21,6 +21,11 @@ populations between a slab's boundary planes and packed buffers.
   momentum totals of a split lattice, each slab summing its interior planes
   (lbm_reduce_planes, or inside the step with lbm_step_planes) and the slabs'
   sums added on the host, or over ranks by an all-reduce.
+- `exchange_halos`, `run_ranks`, `RankSlab`: one slab per rank of a
+  torch.distributed group (NCCL between GPUs; gloo on CPU ranks in the tests):
+  each step packs the slab's two faces, exchanges them with the neighbouring
+  ranks (`exchange_ranks`) and unpacks them into the ghosts before the slab's
+  step.
 """
 import datetime
 
@@ -284,12 +289,22 @@ def exchange_ranks(send_down, send_up, recv_below, recv_above, timeout=datetime.
         recv_above.copy_(send_down)
         return EXCHANGE_OK, ""
     lo, hi = (r - 1) % n, (r + 1) % n
-    # with two ranks lo == hi: the tag tells the two messages apart
-    works = [("receive from rank %d (below)" % lo, dist.irecv(recv_below, src=lo, group=group, tag=1)),
-             ("receive from rank %d (above)" % hi, dist.irecv(recv_above, src=hi, group=group, tag=2)),
-             ("send to rank %d (above)" % hi, dist.isend(send_up, dst=hi, group=group, tag=1)),
-             ("send to rank %d (below)" % lo, dist.isend(send_down, dst=lo, group=group, tag=2))]
-    for what, w in works:
+    # One batch of the four point-to-point operations, posted in the same order
+    # on every rank: NCCL then runs them as one group (individual sends and
+    # receives, each rank posting its receives first, would wait on each
+    # other), gloo as four operations. With two ranks lo == hi: the order (and,
+    # for gloo, the tag) tells the two messages between them apart.
+    names = ["receive from rank %d (below)" % lo, "receive from rank %d (above)" % hi,
+             "send to rank %d (above)" % hi, "send to rank %d (below)" % lo]
+    ops = [dist.P2POp(dist.irecv, recv_below, lo, group, 1), dist.P2POp(dist.irecv, recv_above, hi, group, 2),
+           dist.P2POp(dist.isend, send_up, hi, group, 1), dist.P2POp(dist.isend, send_down, lo, group, 2)]
+    try:
+        reqs = dist.batch_isend_irecv(ops)
+    except RuntimeError as e:
+        return EXCHANGE_FAILED, "posting the exchange: %s" % str(e).splitlines()[0][:200]
+    if len(reqs) != len(names):  # coalesced into one request
+        names = ["exchange with ranks %d and %d" % (lo, hi)] * len(reqs)
+    for what, w in zip(names, reqs):
         try:
             w.wait(timeout=timeout)
         except RuntimeError as e:
@@ -314,3 +329,106 @@ def reduce_ranks(totals, timeout=datetime.timedelta(seconds=10), group=None):
     except RuntimeError as e:
         return EXCHANGE_FAILED, "all-reduce of totals: %s" % str(e).splitlines()[0][:200]
     return EXCHANGE_OK, ""
+
+
+def exchange_halos(slab, bufs, timeout=datetime.timedelta(seconds=10), group=None):
+    """One step's halo exchange of this rank's slab with the ranks below and
+    above. `slab` is any object with halo_pack(side, buf) and
+    halo_unpack(side, buf) (a `Lattice` slab on the GPU, moving the five
+    populations that cross each face; a test slab on the CPU, moving whole
+    planes); `bufs` = (send_down, send_up, recv_below, recv_above), tensors of
+    one packed halo each, on the device the group's backend moves. Side 0 of
+    the slab is its bottom face (plane 1 out, ghost plane 0 in), side 1 its
+    top face (plane nz - 2 out, ghost plane nz - 1 in). Returns the status of
+    `exchange_ranks`; on EXCHANGE_FAILED the ghosts are left as they were."""
+    send_down, send_up, recv_below, recv_above = bufs
+    slab.halo_pack(0, send_down)
+    slab.halo_pack(1, send_up)
+    st, why = exchange_ranks(send_down, send_up, recv_below, recv_above, timeout, group)
+    if st != EXCHANGE_OK:
+        return st, why
+    slab.halo_unpack(0, recv_below)
+    slab.halo_unpack(1, recv_above)
+    return EXCHANGE_OK, ""
+
+
+def run_ranks(slab, bufs, steps, timeout=datetime.timedelta(seconds=10), group=None):
+    """`steps` steps of a lattice decomposed over the ranks of `group`, one
+    z-slab per rank in rank order (periodic in z): before each step of the
+    slab, the exchange of `exchange_halos`. Stops at the first exchange that
+    fails and returns its status (no step is taken after it), else
+    (EXCHANGE_OK, "")."""
+    for _ in range(int(steps)):
+        st, why = exchange_halos(slab, bufs, timeout, group)
+        if st != EXCHANGE_OK:
+            return st, why
+        slab.step(1)
+    return EXCHANGE_OK, ""
+
+
+class RankSlab:
+    """This rank's z-slab of an nx x ny x nz lattice decomposed over the ranks
+    of a torch.distributed group: the planes `split_planes(nz, ranks)[rank]`
+    between two ghost planes, as one `Lattice` on the current device, created
+    with the flags of those planes. Each step exchanges the halos with the
+    neighbouring ranks (point-to-point sends and receives into this rank's
+    own buffers, every wait bounded) and then steps the slab; on a single rank
+    the exchange is the periodic copy of the slab's own faces, and the slab's
+    interior evolves bit for bit as the unsplit lattice. With NCCL the halo
+    buffers are device tensors and the library's stream must be torch's
+    current stream (the `Lattice` default). Keyword arguments go to `Lattice`
+    (storage, model, ...; pull pattern, shifted or FP32/FP64 storage)."""
+
+    def __init__(self, nx, ny, nz, tau, flags=None, force=None, group=None,
+                 timeout=datetime.timedelta(seconds=10), **kw):
+        import torch.distributed as dist
+        from .lattice import Lattice
+        self.group = group
+        self.timeout = timeout
+        self.rank, self.ranks = dist.get_rank(group), dist.get_world_size(group)
+        self.z0, self.z1 = split_planes(nz, self.ranks)[self.rank]
+        self.shape = (nz, ny, nx)
+        fl = None if flags is None else with_ghosts(np.asarray(flags, dtype=np.uint8), self.z0, self.z1)
+        self.lat = Lattice(nx, ny, self.z1 - self.z0 + 2, tau, flags=fl, force=force, **kw)
+        self.stream = self.lat.stream
+        self.bufs = tuple(self.lat.new_halo() for _ in range(4))
+
+    def init_equilibrium(self, u0, rho0=None):
+        """u0 [3][nz][ny][nx] (and rho0 [nz][ny][nx]) of the whole lattice."""
+        self.lat.init_equilibrium(with_ghosts(u0, self.z0, self.z1),
+                                  None if rho0 is None else with_ghosts(rho0, self.z0, self.z1))
+
+    def set_force_field(self, F):
+        self.lat.set_force_field(with_ghosts(F, self.z0, self.z1))
+
+    def step(self, n=1):
+        """n exchange-then-step rounds; raises RuntimeError naming the wait if
+        an exchange fails (a neighbour that stopped, a wait that ran out)."""
+        st, why = run_ranks(self.lat, self.bufs, n, self.timeout, self.group)
+        if st != EXCHANGE_OK:
+            raise RuntimeError("z-slab exchange failed: " + why)
+
+    def interior_state(self, fmt=None):
+        """This rank's interior planes of the state, [19][z1 - z0][ny][nx],
+        read after an exchange (the readers gather from the ghosts)."""
+        st, why = exchange_halos(self.lat, self.bufs, self.timeout, self.group)
+        if st != EXCHANGE_OK:
+            raise RuntimeError("z-slab exchange failed: " + why)
+        return self.lat.get_state(fmt)[:, 1:-1]
+
+    def totals(self):
+        """{sum rho, sum rho u} over the fluid cells of the whole lattice: this
+        rank's interior planes (after an exchange) in FP64, all-reduced over
+        the ranks with a bounded wait."""
+        st, why = exchange_halos(self.lat, self.bufs, self.timeout, self.group)
+        if st != EXCHANGE_OK:
+            raise RuntimeError("z-slab exchange failed: " + why)
+        t = torch.tensor(self.lat.reduce(1, self.lat.shape[0] - 1), dtype=torch.float64,
+                         device=self.bufs[0].device)
+        st, why = reduce_ranks(t, self.timeout, self.group)
+        if st != EXCHANGE_OK:
+            raise RuntimeError("totals all-reduce failed: " + why)
+        return t.cpu().numpy()
+
+    def close(self):
+        self.lat.close()

@@ -185,6 +185,93 @@ def test_rank_that_skips_the_totals_all_reduce_fails_it_in_bounded_time():
     assert r0[3] < 10.0  # the 1.5 s bound, not the 60 s process-group timeout
 
 
+class _OracleSlab:
+    """A rank's slab for slabs.run_ranks on the CPU: the FP64 oracle on the
+    slab's planes with their ghosts. The oracle's state is pre-collision and a
+    step pushes, so a face is a whole plane (all 19 populations): plane 1 goes
+    down, plane nz - 2 up, into the neighbours' ghost planes."""
+
+    def __init__(self, rank, world):
+        import oracle
+        from paper_1112_0850_gb300 import slabs as sl
+        self.oracle = oracle
+        flags, u0, rho0, self.F = _problem()
+        z0, z1 = sl.split_planes(NZ, world)[rank]
+        self.flags = sl.with_ghosts(flags, z0, z1)
+        self.f = oracle.init_equilibrium(sl.with_ghosts(u0, z0, z1), rho0=sl.with_ghosts(rho0, z0, z1),
+                                         flags=self.flags)
+
+    def new_halo(self):
+        import torch
+        return torch.zeros(self.f[:, 0].shape, dtype=torch.float64)
+
+    def halo_pack(self, side, buf):
+        import torch
+        buf.copy_(torch.from_numpy(np.ascontiguousarray(self.f[:, 1 if side == 0 else -2])))
+
+    def halo_unpack(self, side, buf):
+        self.f[:, 0 if side == 0 else -1] = buf.numpy()
+
+    def step(self, n):
+        self.f = self.oracle.run(self.f, TAU, n, flags=self.flags, F=self.F, threads=1)
+
+
+def _driver_worker(rank, world, port, q, stop_after):
+    """slabs.run_ranks, the library's rank driver, with an oracle slab per
+    rank; with stop_after >= 0 rank 1 leaves after that many steps."""
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    from paper_1112_0850_gb300 import slabs as sl
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=60))
+    slab = _OracleSlab(rank, world)
+    bufs = tuple(slab.new_halo() for _ in range(4))
+    steps = stop_after if (rank == 1 and stop_after >= 0) else T
+    t0 = time.time()
+    status, msg = sl.run_ranks(slab, bufs, steps, timeout=datetime.timedelta(seconds=1.5))
+    if rank == 1 and stop_after >= 0:
+        time.sleep(4.0)  # stopped: sends nothing more, then leaves
+    q.put((rank, status, msg, time.time() - t0, slab.f[:, 1:-1]))
+    q.close()
+    q.join_thread()
+    os._exit(0)
+
+
+def _run_driver(world, stop_after=-1):
+    import torch.multiprocessing as mp
+    import oracle
+    oracle.default()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_driver_worker, args=(r, world, port, q, stop_after)) for r in range(world)]
+    for p in procs:
+        p.start()
+    res = sorted((q.get(timeout=180) for _ in procs), key=lambda r: r[0])
+    for p in procs:
+        p.join(timeout=60)
+    return res
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_rank_driver_over_gloo_equals_unsplit(world):
+    """The decomposed driver (exchange_halos + step per round, as RankSlab runs
+    it on GPUs) on gloo ranks: the joined interiors equal the unsplit oracle
+    run bit for bit."""
+    import oracle
+    flags, u0, rho0, F = _problem()
+    ref = oracle.run(oracle.init_equilibrium(u0, rho0=rho0, flags=flags), TAU, T, flags=flags, F=F, threads=1)
+    res = _run_driver(world)
+    assert all(r[1] == slabs.EXCHANGE_OK for r in res), [r[2] for r in res]
+    assert np.array_equal(np.concatenate([r[4] for r in res], axis=1), ref)
+
+
+def test_rank_driver_stops_when_a_neighbour_leaves():
+    res = _run_driver(2, stop_after=2)
+    assert res[0][1] == slabs.EXCHANGE_FAILED and "rank 1" in res[0][2], res[0][2]
+    assert res[0][3] < 10.0  # the 1.5 s bound per wait, not the 60 s process-group timeout
+
+
 def test_reduce_ranks_wants_float64():
     import torch
     with pytest.raises(TypeError):

@@ -403,3 +403,43 @@ def test_slab_step_reduce_equals_unsplit(storage, k):
     assert torch.equal(whole.get_state(), slabs.get_state())
     whole.close()
     slabs.close()
+
+
+@pytest.mark.parametrize("storage", STORAGES)
+def test_rank_slab_on_one_rank_equals_unsplit(storage):
+    """The rank driver (RankSlab: one z-slab per rank of a torch.distributed
+    group, exchange then step) on a single rank, whose exchange is the
+    periodic copy of its own faces: the slab's interior equals the unsplit
+    lattice bit for bit, and its all-reduced totals equal lbm_reduce's to the
+    order of the FP64 sums."""
+    import datetime
+    import socket
+    import torch.distributed as dist
+    from paper_1112_0850_gb300.lattice import Lattice
+    from paper_1112_0850_gb300.slabs import RankSlab
+    ensure_built()
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    dist.init_process_group("gloo", init_method="tcp://127.0.0.1:%d" % port, rank=0, world_size=1,
+                            timeout=datetime.timedelta(seconds=60))
+    try:
+        nx, ny, nz = 21, 10, 14
+        u0, rho0, flags = _fields(nx, ny, nz, 5, "channel")
+        real = REAL[storage]
+        F = (2e-5, -1e-5, 3e-5)
+        u0t, rho0t = torch.as_tensor(u0, dtype=real).cuda(), torch.as_tensor(rho0, dtype=real).cuda()
+        whole = Lattice(nx, ny, nz, 0.56, flags=flags, force=F, storage=storage)
+        rank = RankSlab(nx, ny, nz, 0.56, flags=flags, force=F, storage=storage)
+        assert (rank.z0, rank.z1) == (0, nz)
+        for lat in (whole, rank):
+            lat.init_equilibrium(u0t, rho0t)
+            lat.step(9)
+        assert torch.equal(whole.get_state(), rank.interior_state())
+        want, got = whole.reduce(), rank.totals()
+        assert abs(got[0] - want[0]) <= 1e-12 * want[0] and np.abs(got[1:] - want[1:]).max() <= 1e-12 * want[0]
+        whole.close()
+        rank.close()
+    finally:
+        dist.destroy_process_group()
