@@ -853,7 +853,14 @@ __global__ void __launch_bounds__(512)
         const bool ok = mbar_wait_bounded(bar + b, (k >> 1) & 1);
         if (__syncthreads_or(!ok)) {
             // copies that never completed: report, give the other buffer's
-            // copies a bounded chance to land, and leave
+            // copies a bounded chance to land, and leave. If that second
+            // wait runs out too, the block exits with bulk copies still
+            // addressed to its shared memory; there is no way to cancel them,
+            // and an SM that later reuses that shared memory for another
+            // block could see it overwritten. This path has never been
+            // observed (no test forces it, nor may one: forcing it means a
+            // copy that never completes); the status word tells the caller to
+            // discard the run. The kernel is opt-in (lbm_options.stage_rows).
             if (t == 0) {
                 atomicOr(d.status, LBM_STATUS_TIMEOUT);
                 mbar_wait_bounded(bar + (b ^ 1), ((k + 1) >> 1) & 1);
