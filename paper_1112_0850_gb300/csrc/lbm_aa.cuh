@@ -46,16 +46,16 @@ __device__ __forceinline__ void pair_force(const Dev &d, int c, typename Pair2<R
                                            typename Pair2<R>::V &Fz, Guo2<R> &G) {
     Fx = Fy = Fz = vsplat(R(0));
     if (FORCE == 1) {
-        Fx = vsplat(R(d.F[0]));
-        Fy = vsplat(R(d.F[1]));
-        Fz = vsplat(R(d.F[2]));
+        Fx = vsplat(DevR<R>::F(d, 0));
+        Fy = vsplat(DevR<R>::F(d, 1));
+        Fz = vsplat(DevR<R>::F(d, 2));
         G = uniform_guo<R, TFORM>(d);
     } else if (FORCE == 2) {
         const R *F = static_cast<const R *>(d.Ffield);
         ld2_real(F + c, Fx.x, Fx.y);
         ld2_real(F + d.g.qs + c, Fy.x, Fy.y);
         ld2_real(F + 2 * d.g.qs + c, Fz.x, Fz.y);
-        G = guo2<R>(TFORM ? R(d.cs) : R(1) - R(0.5) * R(d.omega), Fx, Fy, Fz);
+        G = guo2<R>(TFORM ? DevR<R>::cs(d) : R(1) - R(0.5) * DevR<R>::omega(d), Fx, Fy, Fz);
     }
 }
 
@@ -102,7 +102,7 @@ __device__ __forceinline__ void aa_even_pair(const Dev &d, typename Stor<S>::T *
     const Mom2<R> m = moments2<R, FORCE != 0>(s, Fx, Fy, Fz, d.incomp);
     if (RED) pair_add_totals<R>(m, live0, live1, d.incomp, red);
     pair_check_record<R, RECORD>(d, c, live0, live1, m, tape);
-    collide2<R, FORCE != 0, relax_about_t(S)>(s, m, R(d.omega), R(d.cs), Fx, Fy, Fz, G, d.incomp);
+    collide2<R, FORCE != 0, relax_about_t(S)>(s, m, DevR<R>::omega(d), DevR<R>::cs(d), Fx, Fy, Fz, G, d.incomp);
     // a solid lane writes its NaN back (its slots stay marked)
 #pragma unroll
     for (int i = 0; i < Q; ++i)
@@ -201,7 +201,7 @@ __device__ __forceinline__ void aa_odd_pair(const Dev &d, typename Stor<S>::T *_
     const Mom2<R> m = moments2<R, FORCE != 0>(s, Fx, Fy, Fz, d.incomp);
     if (RED) pair_add_totals<R>(m, live0, live1, d.incomp, red);
     pair_check_record<R, RECORD>(d, c, live0, live1, m, tape);
-    collide2<R, FORCE != 0, relax_about_t(S)>(s, m, R(d.omega), R(d.cs), Fx, Fy, Fz, G, d.incomp);
+    collide2<R, FORCE != 0, relax_about_t(S)>(s, m, DevR<R>::omega(d), DevR<R>::cs(d), Fx, Fy, Fz, G, d.incomp);
     // P_i(x) to slot i of x + e_i, or to slot opp(i) of x if x + e_i is solid
 #pragma unroll
     for (int i = 0; i < Q; ++i) {

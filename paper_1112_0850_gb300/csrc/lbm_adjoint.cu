@@ -191,12 +191,12 @@ __global__ void __launch_bounds__(256, AdjBlocks<R>::value)
             ld2_real(F + qs + c, F0y, F1y);
             ld2_real(F + 2 * qs + c, F0z, F1z);
         } else {
-            F0x = F1x = R(d.F[0]);
-            F0y = F1y = R(d.F[1]);
-            F0z = F1z = R(d.F[2]);
+            F0x = F1x = DevR<R>::F(d, 0);
+            F0y = F1y = DevR<R>::F(d, 1);
+            F0z = F1z = DevR<R>::F(d, 2);
         }
     }
-    const R om = R(d.omega);
+    const R om = DevR<R>::omega(d);
     R g0x, g0y, g0z, g1x, g1y, g1z;
     adj_collide<R, FORCE>(mu0, rho0, ux0, uy0, uz0, F0x, F0y, F0z, om, g0x, g0y, g0z, d.incomp);
     adj_collide<R, FORCE>(mu1, rho1, ux1, uy1, uz1, F1x, F1y, F1z, om, g1x, g1y, g1z, d.incomp);
@@ -272,13 +272,13 @@ __global__ void __launch_bounds__(256, ADJ1_BLOCKS)
             Fy = __ldg(F + qs + c);
             Fz = __ldg(F + 2 * qs + c);
         } else {
-            Fx = float(d.F[0]);
-            Fy = float(d.F[1]);
-            Fz = float(d.F[2]);
+            Fx = DevR<float>::F(d, 0);
+            Fy = DevR<float>::F(d, 1);
+            Fz = DevR<float>::F(d, 2);
         }
     }
     float gx, gy, gz;
-    adj_collide<float, FORCE>(mu, rho, ux, uy, uz, Fx, Fy, Fz, float(d.omega), gx, gy, gz, d.incomp);
+    adj_collide<float, FORCE>(mu, rho, ux, uy, uz, Fx, Fy, Fz, DevR<float>::omega(d), gx, gy, gz, d.incomp);
 #pragma unroll
     for (int i = 0; i < Q; ++i) __stcs(lam_out + (long long)i * qs + c, mu[i]);
     if (grad_F) {

@@ -119,6 +119,9 @@ Dev make_dev(const lbm_ctx *ctx) {
     d.force_on = ctx->Ffield_d != nullptr || ctx->F[0] != 0.0 || ctx->F[1] != 0.0 || ctx->F[2] != 0.0;
     d.omega = 1.0 / ctx->tau;
     d.cs = ctx->tau - 0.5;
+    d.omega_f = (float)d.omega;
+    d.cs_f = (float)d.cs;
+    for (int a = 0; a < 3; ++a) d.F_f[a] = (float)d.F[a];
     const double cF = 1.0 - 0.5 * d.omega;
     for (int p = 0; p < NPAIR; ++p) {
         const int i = pair_first(p);

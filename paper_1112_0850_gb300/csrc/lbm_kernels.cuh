@@ -151,9 +151,9 @@ template <class R> __device__ __forceinline__ void force_at(const Dev &d, int c,
         Fy = F[d.g.qs + c];
         Fz = F[2 * d.g.qs + c];
     } else {
-        Fx = R(d.F[0]);
-        Fy = R(d.F[1]);
-        Fz = R(d.F[2]);
+        Fx = DevR<R>::F(d, 0);
+        Fy = DevR<R>::F(d, 1);
+        Fz = DevR<R>::F(d, 2);
     }
 }
 
@@ -450,16 +450,16 @@ __device__ __forceinline__ void step_pair(const Dev &d, const Rows &rows, const 
     V Fx = vsplat(R(0)), Fy = vsplat(R(0)), Fz = vsplat(R(0));
     Guo2<R> G;
     if (FORCE == 1) {
-        Fx = vsplat(R(d.F[0]));
-        Fy = vsplat(R(d.F[1]));
-        Fz = vsplat(R(d.F[2]));
+        Fx = vsplat(DevR<R>::F(d, 0));
+        Fy = vsplat(DevR<R>::F(d, 1));
+        Fz = vsplat(DevR<R>::F(d, 2));
         G = uniform_guo<R, relax_about_t(S)>(d);
     } else if (FORCE == 2) {
         const R *F = static_cast<const R *>(d.Ffield);
         ld2_real(F + c, Fx.x, Fx.y);
         ld2_real(F + g.qs + c, Fy.x, Fy.y);
         ld2_real(F + 2 * g.qs + c, Fz.x, Fz.y);
-        G = guo2<R>(relax_about_t(S) ? R(d.cs) : R(1) - R(0.5) * R(d.omega), Fx, Fy, Fz);
+        G = guo2<R>(relax_about_t(S) ? DevR<R>::cs(d) : R(1) - R(0.5) * DevR<R>::omega(d), Fx, Fy, Fz);
     }
     Mom2<R> m = moments2<R, FORCE != 0>(s, Fx, Fy, Fz, d.incomp);
     if (FLAGS && NANS && ((live0 && m.rho.x != m.rho.x) || (live1 && m.rho.y != m.rho.y))) {
@@ -493,7 +493,7 @@ __device__ __forceinline__ void step_pair(const Dev &d, const Rows &rows, const 
         st2_real(tape + 2 * qs + c, m.uy.x, m.uy.y);
         st2_real(tape + 3 * qs + c, m.uz.x, m.uz.y);
     }
-    collide2<R, FORCE != 0, relax_about_t(S)>(s, m, R(d.omega), R(d.cs), Fx, Fy, Fz, G, d.incomp);
+    collide2<R, FORCE != 0, relax_about_t(S)>(s, m, DevR<R>::omega(d), DevR<R>::cs(d), Fx, Fy, Fz, G, d.incomp);
     // The pair is stored whole, a solid cell included, so 32-byte sectors are
     // written complete: a solid cell's values are never read (load side), it
     // stores the NaN that marks it (NaN marks), or its slots are link targets
@@ -645,16 +645,16 @@ __device__ __forceinline__ void step_pair_split(const Dev &d, const typename Sto
     V Fx = vsplat(R(0)), Fy = vsplat(R(0)), Fz = vsplat(R(0));
     Guo2<R> G;
     if (FORCE == 1) {
-        Fx = vsplat(R(d.F[0]));
-        Fy = vsplat(R(d.F[1]));
-        Fz = vsplat(R(d.F[2]));
+        Fx = vsplat(DevR<R>::F(d, 0));
+        Fy = vsplat(DevR<R>::F(d, 1));
+        Fz = vsplat(DevR<R>::F(d, 2));
         G = uniform_guo<R, false>(d);
     } else if (FORCE == 2) {
         const R *F = static_cast<const R *>(d.Ffield);
         ld2_real(F + c, Fx.x, Fx.y);
         ld2_real(F + g.qs + c, Fy.x, Fy.y);
         ld2_real(F + 2 * g.qs + c, Fz.x, Fz.y);
-        G = guo2<R>(R(1) - R(0.5) * R(d.omega), Fx, Fy, Fz);
+        G = guo2<R>(R(1) - R(0.5) * DevR<R>::omega(d), Fx, Fy, Fz);
     }
     const Mom2<R> m = moments2<R, FORCE != 0>(s, Fx, Fy, Fz, d.incomp);
     const bool bad0 = live0 && !(m.rho.x > R(0) && m.rho.x < R(1e30));
@@ -668,7 +668,7 @@ __device__ __forceinline__ void step_pair_split(const Dev &d, const typename Sto
         st2_real(tape + 2 * qs + c, m.uy.x, m.uy.y);
         st2_real(tape + 3 * qs + c, m.uz.x, m.uz.y);
     }
-    collide2<R, FORCE != 0, false>(s, m, R(d.omega), R(d.cs), Fx, Fy, Fz, G, d.incomp);
+    collide2<R, FORCE != 0, false>(s, m, DevR<R>::omega(d), DevR<R>::cs(d), Fx, Fy, Fz, G, d.incomp);
     // the pair's momentum word, then the remainders against the rounded J
     V Jx = m.jx, Jy = m.jy, Jz = m.jz;
     if (FORCE) {

@@ -40,6 +40,8 @@ struct Dev {
     bool force_on;         // Ffield != nullptr or F != 0
     double omega;          // 1 / tau
     double cs;             // tau - 1/2: the Guo factor 1 - omega/2 over omega
+    float omega_f, cs_f;   // the same, and F, rounded to float on the host: a conversion from
+    float F_f[3];          // double in every thread costs the narrow FP64 pipe (28% busy in the FP32 step)
     unsigned *status;      // device status word
     cudaStream_t stream;
     long long n_cells;     // nx * ny * nz
@@ -48,6 +50,19 @@ struct Dev {
     bool row_staging;      // use the TMA row-staged step kernel where it applies
     int num_sms;           // multiprocessors of the device (grid of persistent kernels)
     long long jo;          // moment-split formats: element offset of the momentum words in a lattice
+};
+
+// omega, tau - 1/2 and the uniform force in the arithmetic type R.
+template <class R> struct DevR;
+template <> struct DevR<float> {
+    static __device__ __forceinline__ float omega(const Dev &d) { return d.omega_f; }
+    static __device__ __forceinline__ float cs(const Dev &d) { return d.cs_f; }
+    static __device__ __forceinline__ float F(const Dev &d, int a) { return d.F_f[a]; }
+};
+template <> struct DevR<double> {
+    static __device__ __forceinline__ double omega(const Dev &d) { return d.omega; }
+    static __device__ __forceinline__ double cs(const Dev &d) { return d.cs; }
+    static __device__ __forceinline__ double F(const Dev &d, int a) { return d.F[a]; }
 };
 
 // Bounce-back form per storage format (see k_step), the measured fastest on
