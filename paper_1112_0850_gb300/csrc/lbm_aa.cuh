@@ -13,16 +13,20 @@
 // opp(i) of x; no neighbour is touched. Odd step: cell x gathers from the
 // swapped layout, collides, and writes P_i(x) to slot i of x + e_i (where the
 // next even step reads f_i(x + e_i)); if x + e_i is solid, the bounced value
-// goes to slot opp(i) of x instead. In both steps the slots a cell writes are
-// exactly the slots it read, each read before it is written by the same
-// thread, so the in-place update has no races (and the read-only load path is
-// safe: nothing is written before it is read within a launch).
+// goes to slot opp(i) of x instead. In both steps the slots a fluid cell
+// writes are exactly the slots it read, each read before it is written by the
+// same thread, so the in-place update has no races (and the read-only load
+// path is safe: no fluid cell reads a slot after it is written within a
+// launch).
 //
 // Halfway bounce-back needs only the odd step: where x - e_j is solid (bit
 // opp(j) of the push mask, i.e. x + e_opp(j) is solid too) population j is
 // read from slot j of x itself, and population opp(j) is written back there.
-// Solid cells are never read; the even step stores their lanes with the rest
-// of the pair (whole 32-byte sectors), the odd step leaves them alone.
+// Solid cells' values are never used; the even step stores their lanes with
+// the rest of the pair (whole 32-byte sectors). The odd step's two forms
+// (aa_odd_pair) either leave solid cells alone or let a solid lane load
+// values it discards (slots a neighbour may be rewriting) and let fluid
+// cells store into solid slots that only they read.
 #pragma once
 
 #include "lbm_kernels.cuh"
@@ -134,18 +138,32 @@ template <int S, bool FLAGS> struct AaOddBlocks {
 };
 
 // Odd step (swapped -> natural): gather from the neighbours, scatter to them.
-// Bounce-back reads and writes are both selected by the push mask (bit j: x +
-// e_j is solid): population i comes from slot i of x itself when bit opp(i)
-// is set, and goes to slot opp(i) of x itself when bit i is set. Every
-// address is a select, so the whole step is one branch-free sequence (a
-// NaN-driven fix-up with separate store paths measured twice as slow here:
-// its code size and divergence made it instruction-bound).
+// Halfway bounce-back (push mask bit j: x + e_j is solid) takes one of two
+// forms, chosen per storage format by measurement on the walled channel:
+//  - selected addresses (FP64, 16-bit storage): population i comes from slot
+//    i of x itself when bit opp(i) is set, and goes to slot opp(i) of x itself
+//    when bit i is set; every address is a select, so the whole step is one
+//    branch-free sequence, which waits for the mask before its first load (a
+//    NaN-driven fix-up with separate store paths measured twice as slow: its
+//    code size and divergence made it instruction-bound). FP16 35.0 GFLUPS
+//    against 32.1 for the other form.
+//  - mask-free gather (FP32), as in the two-grid FP32 step: every population
+//    is loaded from its neighbour's slot without waiting for the mask, and
+//    pairs with a bounce bit then reload the bounced ones from the cell's own
+//    slots; every population of a live cell is stored to its neighbour's
+//    slot, a solid neighbour's included (slot i of a solid x + e_i is written
+//    by x alone and read only by x, for a value it replaces), and the bounced
+//    ones to the cell's own slots after that. Solid lanes load but never
+//    store. 32.8 GFLUPS against 31.1.
+template <int S> __host__ __device__ constexpr bool aa_free_gather() { return S == LBM_F32; }
+
 template <int S, bool FLAGS, int FORCE, bool RECORD, bool FLAT, bool RED>
 __device__ __forceinline__ void aa_odd_pair(const Dev &d, typename Stor<S>::T *__restrict__ A,
                                             typename Stor<S>::R *__restrict__ tape, double *red) {
     typedef typename Stor<S>::T T;
     typedef typename Stor<S>::R R;
     typedef typename Pair2<R>::V V;
+    constexpr bool FREE = aa_free_gather<S>();
     int x0, y, z;
     if (!pair_cell<FLAT>(d.g, FLAT ? d.PF : d.P, blockDim.x, blockDim.y, blockIdx.x, blockIdx.y, threadIdx.x,
                          threadIdx.y, x0, y, z))
@@ -161,7 +179,7 @@ __device__ __forceinline__ void aa_odd_pair(const Dev &d, typename Stor<S>::T *_
         m1 |= mm.y;
     }
     const bool live0 = !(m0 & SOLID_BIT), live1 = !(m1 & SOLID_BIT);
-    if (!live0 && !live1) return;  // (the gather waits for the mask anyway)
+    if (!FREE && !live0 && !live1) return;  // (the selected gather waits for the mask anyway)
     // neighbour columns: x0 - 1, x0 + 1, x0 + 2 (the last only for a full pair)
     const int xa = wrap1(x0 - 1, g.nx);
     const int xb = wrap1(x0 + 1, g.nx);
@@ -173,7 +191,8 @@ __device__ __forceinline__ void aa_odd_pair(const Dev &d, typename Stor<S>::T *_
         const int row = (wrap1(z - ez(i), g.nz) * g.ny + wrap1(y - ey(i), g.ny)) * g.pitch;
         const T *Pn = A + (long long)opp(i) * qs + row;
         const T *Po = A + (long long)i * qs + c;
-        const bool b0 = FLAGS && i > 0 && ((m0 >> opp(i)) & 1u), b1 = FLAGS && i > 0 && ((m1 >> opp(i)) & 1u);
+        const bool b0 = FLAGS && !FREE && i > 0 && ((m0 >> opp(i)) & 1u);
+        const bool b1 = FLAGS && !FREE && i > 0 && ((m1 >> opp(i)) & 1u);
         if (ex(i) == 0) {
             if (b0 == b1) {
                 Stor<S>::ld2(b0 ? Po : Pn + x0, s[i].x, s[i].y);
@@ -184,6 +203,16 @@ __device__ __forceinline__ void aa_odd_pair(const Dev &d, typename Stor<S>::T *_
         } else {
             s[i].x = Stor<S>::ld(b0 ? Po : Pn + (ex(i) > 0 ? xa : xb));
             s[i].y = Stor<S>::ld(b1 ? Po + 1 : Pn + (ex(i) > 0 ? x0 : xc));
+        }
+    }
+    const bool bounce = FLAGS && FREE && ((m0 | m1) & 0x7fffeu);
+    if (bounce) {
+        // the mask-free gather: reload the bounced ones from the own slots
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+            const T *Po = A + (long long)i * qs + c;
+            if ((m0 >> opp(i)) & 1u) s[i].x = Stor<S>::ld(Po);
+            if ((m1 >> opp(i)) & 1u) s[i].y = Stor<S>::ld(Po + 1);
         }
     }
     const bool mv = FLAGS && d.moving_on && ((m0 | m1) & MOVING_BIT);
@@ -208,12 +237,22 @@ __device__ __forceinline__ void aa_odd_pair(const Dev &d, typename Stor<S>::T *_
         const int row = (wrap1(z + ez(i), g.nz) * g.ny + wrap1(y + ey(i), g.ny)) * g.pitch;
         T *Pn = A + (long long)i * qs + row;
         T *Po = A + (long long)opp(i) * qs + c;
-        const bool b0 = FLAGS && i > 0 && ((m0 >> i) & 1u), b1 = FLAGS && i > 0 && ((m1 >> i) & 1u);
+        const bool b0 = FLAGS && !FREE && i > 0 && ((m0 >> i) & 1u);
+        const bool b1 = FLAGS && !FREE && i > 0 && ((m1 >> i) & 1u);
         if (ex(i) == 0 && b0 == b1 && live0 && live1) {
             Stor<S>::st2(b0 ? Po : Pn + x0, s[i].x, s[i].y);
         } else {
             if (live0) Stor<S>::st(b0 ? Po : Pn + (ex(i) > 0 ? xb : (ex(i) < 0 ? xa : x0)), s[i].x);
             if (live1) Stor<S>::st(b1 ? Po + 1 : Pn + (ex(i) > 0 ? xc : (ex(i) < 0 ? x0 : x0 + 1)), s[i].y);
+        }
+    }
+    if (bounce) {
+        // the mask-free gather's bounced values, to the own slots
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+            T *Po = A + (long long)opp(i) * qs + c;
+            if (live0 && ((m0 >> i) & 1u)) Stor<S>::st(Po, s[i].x);
+            if (live1 && ((m1 >> i) & 1u)) Stor<S>::st(Po + 1, s[i].y);
         }
     }
     if (mv) {
