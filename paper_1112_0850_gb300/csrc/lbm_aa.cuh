@@ -130,9 +130,10 @@ __global__ void __launch_bounds__(256, StepBlocks<S>::value)
 }
 
 // Resident 256-thread blocks per SM the odd step is compiled for. With flags
-// its selected addresses need more registers: 2 blocks (128 registers) ran
-// the walled channel at 30.4 vs 22.8 GFLUPS (FP32, 3 blocks) and 33.2 vs 26.7
-// (FP16, 3 blocks).
+// both of its forms (aa_odd_pair) need more registers: 2 blocks (128
+// registers) ran the walled channel at 33.2 vs 26.7 GFLUPS in FP16 with
+// selected addresses, and at 32.8 vs 32.1 in FP32 with the mask-free gather
+// (3 blocks spill about 110 bytes there).
 template <int S, bool FLAGS> struct AaOddBlocks {
     static constexpr int value = S == LBM_F64 ? 1 : (FLAGS ? 2 : StepBlocks<S>::value);
 };
