@@ -209,6 +209,15 @@ lbm_status lbm_init_equilibrium(lbm_ctx *ctx, const void *rho, const void *u);
  * the context's stream is being captured. */
 lbm_status lbm_step(lbm_ctx *ctx, int n);
 
+/* lbm_step(ctx, n) between two CUDA events recorded on the context's stream;
+ * waits for the second and writes the device time between them to *ms
+ * (milliseconds). Synchronizes, and like lbm_synchronize returns
+ * LBM_ERR_DIVERGED if the status word's divergence bit is set. The time
+ * includes any idle gap while the host enqueues, so a call that captures a
+ * step graph (the first with n >= 32 after create or a force change) reads
+ * longer than the ones after it. ms must not be NULL (LBM_ERR_ARG). */
+lbm_status lbm_step_timed(lbm_ctx *ctx, int n, float *ms);
+
 /* Macroscopic fields of the current state (Sec. 2 step 1): rho = sum f_i,
  * u = (sum f_i e_i + F/2) / rho. rho nullable: real [nz][ny][nx];
  * u: real [3][nz][ny][nx]. Solid cells read 0. */

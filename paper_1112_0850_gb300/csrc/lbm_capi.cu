@@ -635,6 +635,30 @@ lbm_status lbm_step(lbm_ctx *ctx, int n) {
     return LBM_OK;
 }
 
+lbm_status lbm_step_timed(lbm_ctx *ctx, int n, float *ms) {
+    if (check_ctx(ctx)) return LBM_ERR_ARG;
+    if (!ms) return fail(ctx, LBM_ERR_ARG, "ms is required");
+    if (n < 0) return fail(ctx, LBM_ERR_ARG, "n must be >= 0");
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    cudaError_t e = cudaEventCreate(&ev[0]);
+    if (e == cudaSuccess) e = cudaEventCreate(&ev[1]);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[0], ctx->stream);
+    lbm_status s = LBM_OK;
+    if (e == cudaSuccess) {
+        s = lbm_step(ctx, n);
+        if (s == LBM_OK) {
+            e = cudaEventRecord(ev[1], ctx->stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(ev[1]);
+            if (e == cudaSuccess) e = cudaEventElapsedTime(ms, ev[0], ev[1]);
+        }
+    }
+    for (cudaEvent_t v : ev)
+        if (v) cudaEventDestroy(v);
+    if (s != LBM_OK) return s;
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "timed steps");
+    return lbm_synchronize(ctx);
+}
+
 lbm_status lbm_set_stream(lbm_ctx *ctx, void *cuda_stream) {
     if (check_ctx(ctx)) return LBM_ERR_ARG;
     ctx->stream = static_cast<cudaStream_t>(cuda_stream);

@@ -138,6 +138,13 @@ class Lattice:
     def step(self, n=1):
         self._call("lbm_step", int(n))
 
+    def step_timed(self, n=1):
+        """n steps between two CUDA events on the context's stream; returns
+        their device time in milliseconds (synchronizes)."""
+        ms = ctypes.c_float(0.0)
+        self._call("lbm_step_timed", int(n), ctypes.byref(ms))
+        return ms.value
+
     def macros(self, rho=None, u=None, with_rho=True):
         if u is None:
             u = self.zeros(3)

@@ -352,3 +352,35 @@ def test_graph_replay_matches_single_launches(storage):
     assert torch.equal(a.get_state(), b.get_state())
     a.close()
     b.close()
+
+
+def test_step_timed_is_step_with_a_device_time():
+    """lbm_step_timed(n) leaves the state lbm_step(n) leaves and returns a
+    positive device time that grows with n; a missing output pointer and a
+    negative count are refused."""
+    import ctypes
+    from paper_1112_0850_gb300 import capi
+    from paper_1112_0850_gb300.lattice import Lattice
+    ensure_built()
+    u0, rho0, tau, steps, flags, F, Ff = _case("channel_64x20x18")
+    nz, ny, nx = u0.shape[1:]
+    lats = []
+    for _ in range(2):
+        lat = Lattice(nx, ny, nz, tau, flags=flags, force=F, storage="f32")
+        lat.init_equilibrium(torch.tensor(u0, dtype=torch.float32).cuda(),
+                             torch.tensor(rho0, dtype=torch.float32).cuda())
+        lats.append(lat)
+    a, b = lats
+    t_first = a.step_timed(64)  # captures the step graph
+    t_short = a.step_timed(32)
+    t_long = a.step_timed(320)
+    b.step(64 + 32 + 320)
+    assert torch.equal(a.get_state(), b.get_state())
+    assert t_first > 0 and t_short > 0 and t_long > 2 * t_short, (t_first, t_short, t_long)
+    assert a.step_timed(0) >= 0
+    L = capi.lib()
+    assert L.lbm_step_timed(a.handle, 4, None) == 1  # LBM_ERR_ARG
+    ms = ctypes.c_float(0)
+    assert L.lbm_step_timed(a.handle, -1, ctypes.byref(ms)) == 1
+    a.close()
+    b.close()
