@@ -13,11 +13,11 @@
 // opp(i) of x; no neighbour is touched. Odd step: cell x gathers from the
 // swapped layout, collides, and writes P_i(x) to slot i of x + e_i (where the
 // next even step reads f_i(x + e_i)); if x + e_i is solid, the bounced value
-// goes to slot opp(i) of x instead. In both steps the slots a fluid cell
-// writes are exactly the slots it read, each read before it is written by the
-// same thread, so the in-place update has no races (and the read-only load
-// path is safe: no fluid cell reads a slot after it is written within a
-// launch).
+// goes to slot opp(i) of x instead. In both steps a fluid cell writes the
+// slots it read, each read before it is written by the same thread, and (the
+// odd step's mask-free scatter) solid slots that no one reads, so the
+// in-place update has no races (and the read-only load path is safe: no
+// fluid cell reads a slot after it is written within a launch).
 //
 // Halfway bounce-back needs only the odd step: where x - e_j is solid (bit
 // opp(j) of the push mask, i.e. x + e_opp(j) is solid too) population j is
@@ -139,24 +139,25 @@ template <int S, bool FLAGS> struct AaOddBlocks {
 };
 
 // Odd step (swapped -> natural): gather from the neighbours, scatter to them.
-// Halfway bounce-back (push mask bit j: x + e_j is solid) takes one of two
-// forms, chosen per storage format by measurement on the walled channel:
-//  - selected addresses (FP64, 16-bit storage): population i comes from slot
-//    i of x itself when bit opp(i) is set, and goes to slot opp(i) of x itself
-//    when bit i is set; every address is a select, so the whole step is one
-//    branch-free sequence, which waits for the mask before its first load (a
-//    NaN-driven fix-up with separate store paths measured twice as slow: its
-//    code size and divergence made it instruction-bound). FP16 35.0 GFLUPS
-//    against 32.1 for the other form.
-//  - mask-free gather (FP32), as in the two-grid FP32 step: every population
-//    is loaded from its neighbour's slot without waiting for the mask, and
-//    pairs with a bounce bit then reload the bounced ones from the cell's own
-//    slots; every population of a live cell is stored to its neighbour's
-//    slot, a solid neighbour's included (slot i of a solid x + e_i is written
-//    by x alone and read only by x, for a value it replaces), and the bounced
-//    ones to the cell's own slots after that. Solid lanes load but never
-//    store. 32.8 GFLUPS against 31.1.
-template <int S> __host__ __device__ constexpr bool aa_free_gather() { return S == LBM_F32; }
+// Halfway bounce-back (push mask bit j: x + e_j is solid):
+//  - loads: population i comes from slot i of x itself when bit opp(i) is set,
+//    from slot opp(i) of x - e_i otherwise; every load address is a select,
+//    so the gather is one branch-free sequence that waits for the mask.
+//  - stores, in one of two forms per storage format: selected (FP64), P_i(x)
+//    to slot opp(i) of x itself when bit i is set, else to slot i of x + e_i;
+//    or the mask-free scatter (FP32, 16-bit storage): every population of a
+//    live cell is stored to its neighbour's slot, a solid neighbour's
+//    included (slot i of a solid x + e_i is written by x alone and read by no
+//    one: x itself reads its own slot there), and the bounced ones are then
+//    stored to the cell's own slots.
+// Walled channel, GFLUPS, FP32 / FP16: selected stores 31.1 / 35.0, the
+// mask-free scatter 33.1 / 38.0. Also measured: a mask-free gather (every
+// population loaded from its neighbour without waiting for the mask, the
+// bounced ones reloaded from the own slots after) with the mask-free scatter
+// 32.8 / 32.1, with selected stores 30.9 / 33.2; a NaN-driven fix-up with
+// separate store paths twice as slow (its code size and divergence made it
+// instruction-bound).
+template <int S> __host__ __device__ constexpr bool aa_free_scatter() { return S != LBM_F64; }
 
 template <int S, bool FLAGS, int FORCE, bool RECORD, bool FLAT, bool RED>
 __device__ __forceinline__ void aa_odd_pair(const Dev &d, typename Stor<S>::T *__restrict__ A,
@@ -164,7 +165,7 @@ __device__ __forceinline__ void aa_odd_pair(const Dev &d, typename Stor<S>::T *_
     typedef typename Stor<S>::T T;
     typedef typename Stor<S>::R R;
     typedef typename Pair2<R>::V V;
-    constexpr bool FREE = aa_free_gather<S>();
+    constexpr bool FREE_ST = aa_free_scatter<S>();
     int x0, y, z;
     if (!pair_cell<FLAT>(d.g, FLAT ? d.PF : d.P, blockDim.x, blockDim.y, blockIdx.x, blockIdx.y, threadIdx.x,
                          threadIdx.y, x0, y, z))
@@ -180,7 +181,7 @@ __device__ __forceinline__ void aa_odd_pair(const Dev &d, typename Stor<S>::T *_
         m1 |= mm.y;
     }
     const bool live0 = !(m0 & SOLID_BIT), live1 = !(m1 & SOLID_BIT);
-    if (!FREE && !live0 && !live1) return;  // (the selected gather waits for the mask anyway)
+    if (!live0 && !live1) return;  // (the selected gather waits for the mask anyway)
     // neighbour columns: x0 - 1, x0 + 1, x0 + 2 (the last only for a full pair)
     const int xa = wrap1(x0 - 1, g.nx);
     const int xb = wrap1(x0 + 1, g.nx);
@@ -192,8 +193,8 @@ __device__ __forceinline__ void aa_odd_pair(const Dev &d, typename Stor<S>::T *_
         const int row = (wrap1(z - ez(i), g.nz) * g.ny + wrap1(y - ey(i), g.ny)) * g.pitch;
         const T *Pn = A + (long long)opp(i) * qs + row;
         const T *Po = A + (long long)i * qs + c;
-        const bool b0 = FLAGS && !FREE && i > 0 && ((m0 >> opp(i)) & 1u);
-        const bool b1 = FLAGS && !FREE && i > 0 && ((m1 >> opp(i)) & 1u);
+        const bool b0 = FLAGS && i > 0 && ((m0 >> opp(i)) & 1u);
+        const bool b1 = FLAGS && i > 0 && ((m1 >> opp(i)) & 1u);
         if (ex(i) == 0) {
             if (b0 == b1) {
                 Stor<S>::ld2(b0 ? Po : Pn + x0, s[i].x, s[i].y);
@@ -206,16 +207,7 @@ __device__ __forceinline__ void aa_odd_pair(const Dev &d, typename Stor<S>::T *_
             s[i].y = Stor<S>::ld(b1 ? Po + 1 : Pn + (ex(i) > 0 ? x0 : xc));
         }
     }
-    const bool bounce = FLAGS && FREE && ((m0 | m1) & 0x7fffeu);
-    if (bounce) {
-        // the mask-free gather: reload the bounced ones from the own slots
-#pragma unroll
-        for (int i = 1; i < Q; ++i) {
-            const T *Po = A + (long long)i * qs + c;
-            if ((m0 >> opp(i)) & 1u) s[i].x = Stor<S>::ld(Po);
-            if ((m1 >> opp(i)) & 1u) s[i].y = Stor<S>::ld(Po + 1);
-        }
-    }
+    const bool bounce_st = FLAGS && FREE_ST && ((m0 | m1) & 0x7fffeu);
     const bool mv = FLAGS && d.moving_on && ((m0 | m1) & MOVING_BIT);
     if (mv) {
         // bounced off a moving wall: plus 6 w_i (e_i . u_w)
@@ -238,8 +230,8 @@ __device__ __forceinline__ void aa_odd_pair(const Dev &d, typename Stor<S>::T *_
         const int row = (wrap1(z + ez(i), g.nz) * g.ny + wrap1(y + ey(i), g.ny)) * g.pitch;
         T *Pn = A + (long long)i * qs + row;
         T *Po = A + (long long)opp(i) * qs + c;
-        const bool b0 = FLAGS && !FREE && i > 0 && ((m0 >> i) & 1u);
-        const bool b1 = FLAGS && !FREE && i > 0 && ((m1 >> i) & 1u);
+        const bool b0 = FLAGS && !FREE_ST && i > 0 && ((m0 >> i) & 1u);
+        const bool b1 = FLAGS && !FREE_ST && i > 0 && ((m1 >> i) & 1u);
         if (ex(i) == 0 && b0 == b1 && live0 && live1) {
             Stor<S>::st2(b0 ? Po : Pn + x0, s[i].x, s[i].y);
         } else {
@@ -247,8 +239,8 @@ __device__ __forceinline__ void aa_odd_pair(const Dev &d, typename Stor<S>::T *_
             if (live1) Stor<S>::st(b1 ? Po + 1 : Pn + (ex(i) > 0 ? xc : (ex(i) < 0 ? x0 : x0 + 1)), s[i].y);
         }
     }
-    if (bounce) {
-        // the mask-free gather's bounced values, to the own slots
+    if (bounce_st) {
+        // the mask-free scatter's bounced values, to the own slots
 #pragma unroll
         for (int i = 1; i < Q; ++i) {
             T *Po = A + (long long)opp(i) * qs + c;

@@ -206,8 +206,8 @@ __device__ __forceinline__ void gather(const Dev &d, const typename Stor<S>::T *
 }
 
 // NaN marks solid slots in the NaN-mark form and in the AA pattern. (In the
-// AA pattern they are hygiene only: the FP32 odd step stores into solid slots
-// that its own cells reload past, and no reader takes a solid slot's value.)
+// AA pattern they are hygiene only: the odd step's mask-free scatter stores
+// into solid slots, and no reader takes a solid slot's value.)
 template <int S> __device__ __forceinline__ bool nan_marked(const Dev &d) {
     return bounce_mode(S) == BB_NANS || d.layout != LAYOUT_PULL;
 }
