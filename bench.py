@@ -539,12 +539,14 @@ def main():
     # The K timed steps run as REPS back-to-back sub-regions with a CUDA event
     # between them: `value` is K steps over the whole region, and the
     # sub-regions give the median and spread of the step time.
-    lat.step(args.warmup)
-    torch.cuda.synchronize()
-    barrier()
+    # The clock sampler starts first: its start leaves the GPU idle for 0.3 s,
+    # which the warm-up then follows straight before the timed region.
     chunks = [args.steps // REPS + (1 if k < args.steps % REPS else 0) for k in range(REPS)]
     chunks = [c for c in chunks if c > 0]
     with ClockSampler(torch.cuda.current_device()) as clk:
+        lat.step(args.warmup)
+        torch.cuda.synchronize()
+        barrier()
         it = iter(chunks)
         ts = time_reps(torch, lat.stream, lambda: lat.step(next(it)), reps=len(chunks))
     barrier()
