@@ -543,6 +543,8 @@ def main():
     # which the warm-up then follows straight before the timed region.
     chunks = [args.steps // REPS + (1 if k < args.steps % REPS else 0) for k in range(REPS)]
     chunks = [c for c in chunks if c > 0]
+    for c in set(chunks):  # capture the sub-regions' step graphs (host work; no step runs)
+        lat.prepare_steps(c)
     with ClockSampler(torch.cuda.current_device()) as clk:
         lat.step(args.warmup)
         torch.cuda.synchronize()

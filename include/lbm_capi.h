@@ -203,19 +203,27 @@ lbm_status lbm_init_equilibrium(lbm_ctx *ctx, const void *rho, const void *u);
  * bounce-back; Sec. 6 pull-style update over two grids, or the in-place AA
  * update when the context was created with LBM_PATTERN_AA; both give the same
  * f^n sequence, and every other call sees the same state). Asynchronous. Whole
- * blocks of 32 steps replay a CUDA graph captured on first use (one launch per
- * block; rebuilt after the force changes), so small lattices are not bound by
- * launch overhead; the first call that uses a graph should not be made while
- * the context's stream is being captured. */
+ * blocks of 32 steps, and a remaining 2 to 31, replay CUDA graphs of that many
+ * steps (one launch each), captured on first use or by lbm_step_prepare and
+ * dropped when the force or wall velocity changes; a single step is launched
+ * on its own. A call that captures a graph should not be made while the
+ * context's stream is being captured. */
 lbm_status lbm_step(lbm_ctx *ctx, int n);
+
+/* Capture the graphs that lbm_step(ctx, n) replays, from either starting
+ * lattice, without running a step (host work only; nothing is enqueued), so
+ * that a later lbm_step(n) does not capture them while the GPU waits. n >= 0;
+ * a graph that cannot be captured leaves lbm_step launching step by step. */
+lbm_status lbm_step_prepare(lbm_ctx *ctx, int n);
 
 /* lbm_step(ctx, n) between two CUDA events recorded on the context's stream;
  * waits for the second and writes the device time between them to *ms
  * (milliseconds). Synchronizes, and like lbm_synchronize returns
  * LBM_ERR_DIVERGED if the status word's divergence bit is set. The time
  * includes any idle gap while the host enqueues, so a call that captures a
- * step graph (the first with n >= 32 after create or a force change) reads
- * longer than the ones after it. ms must not be NULL (LBM_ERR_ARG). */
+ * step graph (the first with a given n after create or a force change, unless
+ * lbm_step_prepare(n) came first) reads longer than the ones after it. ms must
+ * not be NULL (LBM_ERR_ARG). */
 lbm_status lbm_step_timed(lbm_ctx *ctx, int n, float *ms);
 
 /* Macroscopic fields of the current state (Sec. 2 step 1): rho = sum f_i,

@@ -57,6 +57,7 @@ PROTOTYPES = {
     "lbm_set_force_field": (_st, [_vp, _vp]),
     "lbm_init_equilibrium": (_st, [_vp, _vp, _vp]),
     "lbm_step": (_st, [_vp, _i]),
+    "lbm_step_prepare": (_st, [_vp, _i]),
     "lbm_step_timed": (_st, [_vp, _i, ctypes.POINTER(ctypes.c_float)]),
     "lbm_macros": (_st, [_vp, _vp, _vp]),
     "lbm_reduce": (_st, [_vp, _vp]),

@@ -10,6 +10,11 @@
 
 using namespace lbm;
 
+// Steps per captured block graph (even, so a replay ends on the lattice it
+// began on); a call's remaining 2 .. GRAPH_STEPS - 1 steps replay a graph of
+// their own count.
+constexpr int GRAPH_STEPS = 32;
+
 struct lbm_ctx {
     Geom g;
     RowLaunch L;
@@ -46,9 +51,10 @@ struct lbm_ctx {
     size_t staging_bytes;
     int64_t n_fluid;
     int64_t steps_done;
-    // CUDA graphs of GRAPH_STEPS consecutive steps, one per starting lattice
-    // (lat[0] or lat[1] as source); rebuilt when the step parameters change
-    cudaGraphExec_t graph[2];
+    // CUDA graphs of n consecutive steps (graph[from][n], 2 <= n <= GRAPH_STEPS),
+    // one per starting lattice (lat[0] or lat[1] as source), captured on first
+    // use or by lbm_step_prepare; dropped when the step parameters change
+    cudaGraphExec_t graph[2][GRAPH_STEPS + 1];
     bool graph_failed;
     std::string err;
 };
@@ -256,14 +262,12 @@ lbm_status check_ctx(const lbm_ctx *ctx) {
     return LBM_OK;
 }
 
-// Steps per captured graph (even, so a replay ends on the lattice it began on).
-constexpr int GRAPH_STEPS = 32;
-
 void drop_graphs(lbm_ctx *ctx) {
-    for (int k = 0; k < 2; ++k) {
-        if (ctx->graph[k]) cudaGraphExecDestroy(ctx->graph[k]);
-        ctx->graph[k] = nullptr;
-    }
+    for (int k = 0; k < 2; ++k)
+        for (int n = 0; n <= GRAPH_STEPS; ++n) {
+            if (ctx->graph[k][n]) cudaGraphExecDestroy(ctx->graph[k][n]);
+            ctx->graph[k][n] = nullptr;
+        }
 }
 
 void free_ctx(lbm_ctx *ctx) {
@@ -353,7 +357,8 @@ lbm_status lbm_create(lbm_ctx **out, int nx, int ny, int nz, double tau, const u
     ctx->staging = nullptr;
     ctx->staging_bytes = 0;
     ctx->steps_done = 0;
-    ctx->graph[0] = ctx->graph[1] = nullptr;
+    for (int k = 0; k < 2; ++k)
+        for (int n = 0; n <= GRAPH_STEPS; ++n) ctx->graph[k][n] = nullptr;
     ctx->graph_failed = false;
     cudaError_t e = cudaGetDevice(&ctx->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device);
@@ -582,10 +587,10 @@ lbm_status lbm_init_equilibrium(lbm_ctx *ctx, const void *rho, const void *u) {
     return LBM_OK;
 }
 
-// Capture GRAPH_STEPS steps starting from lattice `from` into ctx->graph[from]
-// (on a private stream; the graph is then launched on the context's stream).
+// Capture n steps starting from lattice `from` into ctx->graph[from][n] (on a
+// private stream; the graph is then launched on the context's stream).
 // Returns false, leaving no graph, if capture or instantiation fails.
-static bool build_graph(lbm_ctx *ctx, int from) {
+static bool build_graph(lbm_ctx *ctx, int from, int n) {
     cudaStream_t cs = nullptr;
     if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
         cudaGetLastError();
@@ -595,35 +600,44 @@ static bool build_graph(lbm_ctx *ctx, int from) {
     d.stream = cs;
     cudaGraph_t graph = nullptr;
     bool ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
-    for (int k = 0; ok && k < GRAPH_STEPS; ++k) {
+    for (int k = 0; ok && k < n; ++k) {
         const int c = from ^ (k & 1);
         ok = step_from(ctx, d, c, nullptr) == cudaSuccess;
     }
     const bool ended = cudaStreamEndCapture(cs, &graph) == cudaSuccess;
-    ok = ok && ended && graph && cudaGraphInstantiate(&ctx->graph[from], graph, 0) == cudaSuccess;
+    ok = ok && ended && graph && cudaGraphInstantiate(&ctx->graph[from][n], graph, 0) == cudaSuccess;
     if (graph) cudaGraphDestroy(graph);
     cudaStreamDestroy(cs);
     if (!ok) {
         cudaGetLastError();
-        ctx->graph[from] = nullptr;
+        ctx->graph[from][n] = nullptr;
     }
     return ok;
+}
+
+// The graph of n steps from lattice `from`, captured if missing; null if
+// graphs failed on this context (the caller then launches step by step).
+static cudaGraphExec_t graph_for(lbm_ctx *ctx, int from, int n) {
+    if (ctx->graph_failed) return nullptr;
+    if (!ctx->graph[from][n] && !build_graph(ctx, from, n)) ctx->graph_failed = true;
+    return ctx->graph[from][n];
 }
 
 lbm_status lbm_step(lbm_ctx *ctx, int n) {
     if (check_ctx(ctx)) return LBM_ERR_ARG;
     if (n < 0) return fail(ctx, LBM_ERR_ARG, "n must be >= 0");
-    // whole blocks of GRAPH_STEPS steps replay a captured graph (one launch
-    // instead of GRAPH_STEPS); the remainder is launched step by step
-    while (n >= GRAPH_STEPS && !ctx->graph_failed) {
-        if (!ctx->graph[ctx->cur] && !build_graph(ctx, ctx->cur)) {
-            ctx->graph_failed = true;
-            break;
-        }
-        cudaError_t e = cudaGraphLaunch(ctx->graph[ctx->cur], ctx->stream);
+    // whole blocks of GRAPH_STEPS steps, then a remainder of 2 or more, replay
+    // captured graphs (one launch each); a single step, or every step where
+    // graphs failed, is launched on its own
+    while (n >= 2) {
+        const int m = n >= GRAPH_STEPS ? GRAPH_STEPS : n;
+        cudaGraphExec_t ge = graph_for(ctx, ctx->cur, m);
+        if (!ge) break;
+        cudaError_t e = cudaGraphLaunch(ge, ctx->stream);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "stream-collide graph launch");
-        n -= GRAPH_STEPS;
-        ctx->steps_done += GRAPH_STEPS;
+        n -= m;
+        ctx->cur ^= m & 1;
+        ctx->steps_done += m;
     }
     Dev d = make_dev(ctx);
     for (int k = 0; k < n; ++k) {
@@ -631,6 +645,17 @@ lbm_status lbm_step(lbm_ctx *ctx, int n) {
         if (e != cudaSuccess) return cuda_fail(ctx, e, "stream-collide launch");
         ctx->cur ^= 1;
         ctx->steps_done++;
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_step_prepare(lbm_ctx *ctx, int n) {
+    if (check_ctx(ctx)) return LBM_ERR_ARG;
+    if (n < 0) return fail(ctx, LBM_ERR_ARG, "n must be >= 0");
+    const int r = n % GRAPH_STEPS;
+    for (int from = 0; from < 2; ++from) {
+        if (n >= GRAPH_STEPS) graph_for(ctx, from, GRAPH_STEPS);
+        if (r >= 2) graph_for(ctx, from, r);
     }
     return LBM_OK;
 }

@@ -138,6 +138,10 @@ class Lattice:
     def step(self, n=1):
         self._call("lbm_step", int(n))
 
+    def prepare_steps(self, n):
+        """Capture the step graphs that step(n) replays, running nothing."""
+        self._call("lbm_step_prepare", int(n))
+
     def step_timed(self, n=1):
         """n steps between two CUDA events on the context's stream; returns
         their device time in milliseconds (synchronizes)."""

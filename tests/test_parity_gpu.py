@@ -384,3 +384,35 @@ def test_step_timed_is_step_with_a_device_time():
     assert L.lbm_step_timed(a.handle, -1, ctypes.byref(ms)) == 1
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("storage,pattern", [("f32", "pull"), ("f16s", "pull"), ("bf16m", "pull"), ("f32", "aa"),
+                                             ("f16s", "aa")])
+def test_step_counts_replay_graphs_bit_for_bit(storage, pattern):
+    """lbm_step(n) replays a graph of 32-step blocks and one of the remaining
+    2..31 steps, each from either lattice, captured on first use or ahead by
+    lbm_step_prepare; every count gives the bits of the same steps launched
+    one by one."""
+    from paper_1112_0850_gb300.lattice import Lattice
+    ensure_built()
+    u0, rho0, tau, steps, flags, F, Ff = _case("flags_33x7x5")
+    nz, ny, nx = u0.shape[1:]
+    real = REAL[storage]
+    lats = []
+    for _ in range(2):
+        lat = Lattice(nx, ny, nz, tau, flags=flags, force=F, storage=storage, pattern=pattern)
+        lat.init_equilibrium(torch.tensor(u0, dtype=real).cuda(), torch.tensor(rho0, dtype=real).cuda())
+        lats.append(lat)
+    a, b = lats
+    a.prepare_steps(5)
+    a.prepare_steps(37)
+    a.prepare_steps(0)
+    counts = [2, 3, 5, 31, 33, 64, 7, 4, 37, 1]
+    for n in counts:
+        a.step(n)
+    for _ in range(sum(counts)):
+        b.step(1)
+    assert torch.equal(a.get_state(), b.get_state())
+    assert a.info.steps_done == b.info.steps_done == sum(counts)
+    a.close()
+    b.close()
