@@ -697,6 +697,9 @@ def main():
                    "host_model_note": "the paper's CPU model (Sec. 4): 456 B per FP64 update with write-allocate"}
 
     lat_bytes = lat.info.lattice_bytes
+    # kernels per step in the timed region: the step kernel, plus the link
+    # kernel of 16-bit shifted storage on a lattice with solid cells
+    kernels_per_step = 2 if (args.pattern == "pull" and storage in ("f16s", "bf16s") and n_fluid < n_cells) else 1
     lat.close()
     if rank == 0:
         line = {
@@ -719,7 +722,7 @@ def main():
                                                  ",flags,uniform force" if args.case == "channel" else ""),
                          "peak_source": peak_kind + " hbm_gbs (MEASURED_PEAKS.json)",
                          "alg_bytes_per_launch": alg_bytes},
-            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps, "clocks": clocks,
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps * kernels_per_step, "clocks": clocks,
             "status_word": status, "timing": dict(head_spread, sub_regions=len(chunks)),
         }
         line.update(extras)
