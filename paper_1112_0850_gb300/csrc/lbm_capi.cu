@@ -386,33 +386,42 @@ lbm_status lbm_create(lbm_ctx **out, int nx, int ny, int nz, double tau, const u
     std::vector<uint8_t> hflags;
     int64_t n_fluid = N;
     if (flags) {
-        std::vector<uint8_t> canon((size_t)N);
+        std::vector<uint8_t> canon;
+        const uint8_t *hf = flags;
         if (is_device_ptr(flags)) {
+            canon.resize((size_t)N);
             e = cudaMemcpy(canon.data(), flags, (size_t)N, cudaMemcpyDeviceToHost);
             if (e != cudaSuccess) {
                 delete ctx;
                 return LBM_ERR_CUDA;
             }
-        } else {
-            memcpy(canon.data(), flags, (size_t)N);
+            hf = canon.data();
         }
         hflags.assign((size_t)qs, 1);
         n_fluid = 0;
         long long ylo = ny, yhi = -1, zlo = nz, zhi = -1;  // box of the fluid cells
         for (long long z = 0; z < nz; ++z)
-            for (long long y = 0; y < ny; ++y)
+            for (long long y = 0; y < ny; ++y) {
+                // one row, branch-free: 0 fluid, 2 moving wall, any other value solid (1)
+                const uint8_t *src = hf + (size_t)(nx * (y + ny * z));
+                uint8_t *dst = hflags.data() + (size_t)((z * ny + y) * pitch);
+                long long fluid = 0;
+                unsigned moving = 0;
                 for (long long x = 0; x < nx; ++x) {
-                    const uint8_t v = canon[(size_t)(x + nx * (y + ny * z))];
-                    const uint8_t f = v == 0 ? 0 : (v == 2 ? 2 : 1);  // fluid, moving wall, solid
-                    hflags[(size_t)((z * ny + y) * pitch + x)] = f;
-                    if (f == 2) ctx->has_moving = true;
-                    if (f) continue;
-                    ++n_fluid;
-                    if (y < ylo) ylo = y;
-                    if (y > yhi) yhi = y;
-                    if (z < zlo) zlo = z;
-                    if (z > zhi) zhi = z;
+                    const uint8_t v = src[x];
+                    const uint8_t f = (uint8_t)(v == 0 ? 0 : (v == 2 ? 2 : 1));
+                    dst[x] = f;
+                    fluid += f == 0;
+                    moving |= f == 2;
                 }
+                if (moving) ctx->has_moving = true;
+                if (!fluid) continue;
+                n_fluid += fluid;
+                if (y < ylo) ylo = y;
+                if (y > yhi) yhi = y;
+                if (z < zlo) zlo = z;
+                if (z > zhi) zhi = z;
+            }
         if (n_fluid > 0) {  // the step kernels update rows of this box only
             ctx->box[0] = (int)ylo;
             ctx->box[1] = (int)(yhi - ylo + 1);
