@@ -87,8 +87,9 @@ __device__ __forceinline__ void aa_even_pair(const Dev &d, typename Stor<S>::T *
     typedef typename Stor<S>::R R;
     typedef typename Pair2<R>::V V;
     int x0, y, z;
-    if (!pair_cell<FLAT>(d.g, FLAT ? d.PF : d.P, blockDim.x, blockDim.y, blockIdx.x, blockIdx.y, threadIdx.x,
-                         threadIdx.y, x0, y, z))
+    const int bz = d.zrev ? (int)gridDim.y - 1 - (int)blockIdx.y : (int)blockIdx.y;  // (see k_step)
+    if (!pair_cell<FLAT>(d.g, FLAT ? d.PF : d.P, blockDim.x, blockDim.y, blockIdx.x, bz, threadIdx.x, threadIdx.y,
+                         x0, y, z))
         return;
     const long long qs = d.g.qs;
     const int c = cell_index(d.g, x0, y, z);
@@ -167,8 +168,9 @@ __device__ __forceinline__ void aa_odd_pair(const Dev &d, typename Stor<S>::T *_
     typedef typename Pair2<R>::V V;
     constexpr bool FREE_ST = aa_free_scatter<S>();
     int x0, y, z;
-    if (!pair_cell<FLAT>(d.g, FLAT ? d.PF : d.P, blockDim.x, blockDim.y, blockIdx.x, blockIdx.y, threadIdx.x,
-                         threadIdx.y, x0, y, z))
+    const int bz = d.zrev ? (int)gridDim.y - 1 - (int)blockIdx.y : (int)blockIdx.y;  // (see k_step)
+    if (!pair_cell<FLAT>(d.g, FLAT ? d.PF : d.P, blockDim.x, blockDim.y, blockIdx.x, bz, threadIdx.x, threadIdx.y,
+                         x0, y, z))
         return;
     const Geom &g = d.g;
     const long long qs = g.qs;

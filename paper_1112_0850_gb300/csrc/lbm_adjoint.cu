@@ -235,7 +235,8 @@ __global__ void __launch_bounds__(256, ADJ1_BLOCKS)
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     const int r = k / g.nx;
     if (r >= d.P.nyr) return;
-    const int x = k - r * g.nx, y = d.P.y0 + r, z = d.P.z0 + blockIdx.y;
+    const int bz = d.zrev ? (int)gridDim.y - 1 - (int)blockIdx.y : (int)blockIdx.y;  // (see k_step)
+    const int x = k - r * g.nx, y = d.P.y0 + r, z = d.P.z0 + bz;
     const int c = cell_index(g, x, y, z);
     const long long qs = g.qs;
     uint32_t m = 0u;

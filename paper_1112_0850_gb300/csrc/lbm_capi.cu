@@ -156,6 +156,7 @@ Dev make_dev(const lbm_ctx *ctx) {
     d.row_staging = ctx->stage_rows;
     d.num_sms = ctx->num_sms;
     d.jo = split_j_offset(ctx->g.qs);
+    d.zrev = 0;
     return d;
 }
 
@@ -251,9 +252,14 @@ void *state_lat(const lbm_ctx *ctx) { return ctx->pattern == LBM_PATTERN_AA ? ct
 
 // One step from parity / lattice c (pull: lat[c] -> lat[c ^ 1]; AA: the even
 // step for c = 0, the odd one for c = 1).
+// Steps alternate the order of their planes (ascending from lattice 0 or for
+// an even AA step, descending otherwise): each step starts on the planes the
+// step before it wrote last, which are still in L2.
 cudaError_t step_from(const lbm_ctx *ctx, const Dev &d, int c, void *tape) {
-    if (ctx->pattern == LBM_PATTERN_AA) return LBM_AA_DISPATCH(ctx, step(d, ctx->lat[0], c, tape));
-    return LBM_DISPATCH(ctx, step(d, ctx->lat[c], ctx->lat[c ^ 1], tape));
+    Dev dc = d;
+    dc.zrev = c;
+    if (ctx->pattern == LBM_PATTERN_AA) return LBM_AA_DISPATCH(ctx, step(dc, ctx->lat[0], c, tape));
+    return LBM_DISPATCH(ctx, step(dc, ctx->lat[c], ctx->lat[c ^ 1], tape));
 }
 
 lbm_status check_ctx(const lbm_ctx *ctx) {
@@ -976,6 +982,7 @@ lbm_status lbm_adjoint_step(lbm_ctx *ctx, int n, const void *tape, void *grad_F)
     Dev d = make_dev(ctx);
     for (int k = n - 1; k >= 0; --k) {
         const void *tk = static_cast<const char *>(tape) + per * (size_t)k;
+        d.zrev = ctx->lcur;  // alternating plane order, as in the forward steps
         cudaError_t e = ctx->storage == LBM_F64
                             ? AdjOps<double>::step(d, ctx->lam[ctx->lcur], ctx->lam[ctx->lcur ^ 1], tk, grad_F)
                             : AdjOps<float>::step(d, ctx->lam[ctx->lcur], ctx->lam[ctx->lcur ^ 1], tk, grad_F);

@@ -732,9 +732,12 @@ __global__ void __launch_bounds__(256, StepBlocks<S>::value)
     // once every block of this grid is running; it still waits for this grid
     // to complete before it reads what this grid writes
     if (STEP_PDL) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    // blocks are dispatched in index order: with d.zrev the planes run from
+    // the last to the first
+    const int bz = d.zrev ? (int)gridDim.y - 1 - (int)blockIdx.y : (int)blockIdx.y;
     int x0, y, z;
-    if (!pair_cell<FLAT>(d.g, FLAT ? d.PF : d.P, blockDim.x, blockDim.y, blockIdx.x, blockIdx.y, threadIdx.x,
-                         threadIdx.y, x0, y, z))
+    if (!pair_cell<FLAT>(d.g, FLAT ? d.PF : d.P, blockDim.x, blockDim.y, blockIdx.x, bz, threadIdx.x, threadIdx.y,
+                         x0, y, z))
         return;
     if constexpr (is_split(S))
         step_pair_split<S, FLAGS, FORCE, RECORD, false, ODD>(d, src, dst, tape, x0, y, z);

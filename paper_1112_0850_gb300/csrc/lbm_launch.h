@@ -50,6 +50,7 @@ struct Dev {
     bool row_staging;      // use the TMA row-staged step kernel where it applies
     int num_sms;           // multiprocessors of the device (grid of persistent kernels)
     long long jo;          // moment-split formats: element offset of the momentum words in a lattice
+    int zrev;              // step kernels: take the planes in descending order (alternates by step)
 };
 
 // omega, tau - 1/2 and the uniform force in the arithmetic type R.
