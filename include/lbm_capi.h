@@ -171,7 +171,9 @@ lbm_status lbm_options_default(lbm_options *opt);
  *   opt   nullable (= defaults).
  * Sizes: 1 <= nx, ny; 1 <= nz <= 65535; padded cells nz * ny * pitch < 2^31.
  * Returns LBM_ERR_OOM if the lattices (two; one with LBM_PATTERN_AA) do not
- * fit in free device memory. The state is the rest state after creation. */
+ * fit in free device memory, and LBM_ERR_UNSUPPORTED for 16-bit shifted
+ * storage when one direction has more than 65535 * 1024 bounce-back links
+ * (the link kernel's grid). The state is the rest state after creation. */
 lbm_status lbm_create(lbm_ctx **out, int nx, int ny, int nz, double tau, const uint8_t *flags,
                       const double force[3], const lbm_options *opt);
 

@@ -492,6 +492,10 @@ lbm_status lbm_create(lbm_ctx **out, int nx, int ny, int nz, double tau, const u
             if (cnt > ctx->link_max) ctx->link_max = cnt;
             hlinks.insert(hlinks.end(), per[j].begin(), per[j].end());
         }
+        if ((long long)ctx->link_max > BOUNCE_MAX_LINKS) {  // more spans than k_bounce's grid holds
+            free_ctx(ctx);
+            return LBM_ERR_UNSUPPORTED;
+        }
         if (ok && !hlinks.empty())
             ok = cudaMalloc((void **)&ctx->links_d, hlinks.size() * sizeof(uint32_t)) == cudaSuccess &&
                  cudaMemcpyAsync(ctx->links_d, hlinks.data(), hlinks.size() * sizeof(uint32_t),

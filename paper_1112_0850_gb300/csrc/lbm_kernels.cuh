@@ -897,20 +897,33 @@ __global__ void __launch_bounds__(512)
 // direction j with x + e_j solid and at rest, slot opp(j) of the solid cell
 // receives the post-collision population j of x, copied bit for bit (links
 // into moving walls are written by the step kernel). Links are grouped by
-// direction (blockIdx.y + 1) and ordered by cell within a direction.
+// direction (blockIdx.x + 1) and ordered by cell within a direction. Every
+// direction's links are cut into gridDim.y equal spans, block (j, b) taking
+// span b of direction j: blocks are dispatched span by span across the 18
+// directions, so the kernel sweeps the planes once, against the order of the
+// step before it, and ends on the planes the next step starts with (FP16
+// channel 45.9 GFLUPS; sweeping in the step's own order 44.2, and one sweep
+// per direction 45.6).
 // Each thread copies LINKS_PER_THREAD links (256 apart, so index loads stay
 // coalesced); all index loads are issued before the value loads, and all value
 // loads before the stores, so the two dependent round trips are shared.
 constexpr int LINKS_PER_THREAD = 4;
+static_assert(256 * LINKS_PER_THREAD == BOUNCE_LINKS_PER_BLOCK, "k_bounce block size");
+constexpr int BOUNCE_SWEEP_OPPOSITE = 1;
 // Launch k_bounce as a programmatic dependent of the step kernel.
 constexpr int BOUNCE_PDL = 1;
 
 template <int S>
 __global__ void __launch_bounds__(256) k_bounce(const Dev d, typename Stor<S>::T *__restrict__ P) {
     typedef typename Stor<S>::T T;
-    const int j = blockIdx.y + 1;
-    const int base = d.link_off[j], n = d.link_off[j + 1] - base;
-    const int k0 = blockIdx.x * (blockDim.x * LINKS_PER_THREAD) + threadIdx.x;
+    const int j = blockIdx.x + 1;
+    const int base = d.link_off[j];
+    const int nb = (int)gridDim.y;
+    const int b = (d.zrev ^ BOUNCE_SWEEP_OPPOSITE) ? nb - 1 - (int)blockIdx.y : (int)blockIdx.y;
+    const int nj = d.link_off[j + 1] - base;
+    const int span = (nj + nb - 1) / nb;  // <= blockDim.x * LINKS_PER_THREAD: nb spans the largest direction
+    const int k0 = b * span + threadIdx.x;
+    const int n = min(nj, (b + 1) * span);  // end of this block's span
     const uint2 *L = reinterpret_cast<const uint2 *>(d.links) + base;
     const T *from = P + (long long)j * d.g.qs;
     T *to = P + (long long)opp(j) * d.g.qs;
@@ -1330,7 +1343,7 @@ cudaError_t Ops<S>::step(const Dev &d, const void *src, void *dst, void *tape) {
     // load their links) while the step kernel drains; they wait for its grid
     // before reading the values (griddepcontrol.wait in k_bounce)
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((d.link_max + per_block - 1) / per_block, Q - 1);
+    cfg.gridDim = dim3(Q - 1, (d.link_max + per_block - 1) / per_block);
     cfg.blockDim = dim3(256);
     cfg.dynamicSmemBytes = 0;
     cfg.stream = d.stream;
@@ -1348,7 +1361,7 @@ template <int S>
 cudaError_t Ops<S>::bounce(const Dev &d, void *dst) {
     if (!d.flags || !LinkBounce<S>::value || d.link_max == 0) return cudaSuccess;
     const int per_block = 256 * LINKS_PER_THREAD;
-    k_bounce<S><<<dim3((d.link_max + per_block - 1) / per_block, Q - 1), 256, 0, d.stream>>>(
+    k_bounce<S><<<dim3(Q - 1, (d.link_max + per_block - 1) / per_block), 256, 0, d.stream>>>(
         d, static_cast<typename Stor<S>::T *>(dst));
     return cudaGetLastError();
 }
@@ -1392,7 +1405,7 @@ cudaError_t Ops<S>::step_reduce(const Dev &d, const void *src, void *dst, double
     if (e != cudaSuccess) return e;
     if (d.flags && LinkBounce<S>::value && d.link_max > 0) {
         const int per_block = 256 * LINKS_PER_THREAD;
-        k_bounce<S><<<dim3((d.link_max + per_block - 1) / per_block, Q - 1), 256, 0, d.stream>>>(d, t);
+        k_bounce<S><<<dim3(Q - 1, (d.link_max + per_block - 1) / per_block), 256, 0, d.stream>>>(d, t);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     k_reduce_final<<<1, RED_THREADS, 0, d.stream>>>(partials, (int)(grid.x * grid.y), out);

@@ -87,6 +87,11 @@ __host__ __device__ constexpr bool bounce_in_solid(int s) { return bounce_mode(s
 // rounding) keep the cheaper omega-scaled form.
 __host__ __device__ constexpr bool relax_about_t(int s) { return s == LBM_F32; }
 
+// Links each k_bounce block copies at most (256 threads x 4), and the most
+// blocks per direction its grid has (gridDim.y): the link form's limit.
+constexpr int BOUNCE_LINKS_PER_BLOCK = 1024;
+constexpr long long BOUNCE_MAX_LINKS = 65535LL * BOUNCE_LINKS_PER_BLOCK;
+
 constexpr int RED_BLOCKS = 152 * 8;  // fixed grid of the reduction: deterministic order
 constexpr int RED_THREADS = 256;
 
