@@ -58,6 +58,10 @@ template <> struct Stor<LBM_F64> {
     static __device__ __forceinline__ void st2(T *p, R a, R b) {
         __stcs(reinterpret_cast<double2 *>(p), make_double2(a, b));
     }
+    // a write-back store: the line stays in L2 for a later reader
+    static __device__ __forceinline__ void st2_wb(T *p, R a, R b) {
+        *reinterpret_cast<double2 *>(p) = make_double2(a, b);
+    }
     // plain loads (shared memory)
     static __device__ __forceinline__ R ls(const T *p) { return *p; }
     static __device__ __forceinline__ void ls2(const T *p, R &a, R &b) {
@@ -81,6 +85,9 @@ template <> struct Stor<LBM_F32> {
     static __device__ __forceinline__ void st2(T *p, R a, R b) {
         __stcs(reinterpret_cast<float2 *>(p), make_float2(a, b));
     }
+    static __device__ __forceinline__ void st2_wb(T *p, R a, R b) {
+        *reinterpret_cast<float2 *>(p) = make_float2(a, b);
+    }
     static __device__ __forceinline__ R ls(const T *p) { return *p; }
     static __device__ __forceinline__ void ls2(const T *p, R &a, R &b) {
         const float2 v = *reinterpret_cast<const float2 *>(p);
@@ -92,6 +99,8 @@ template <> struct Stor<LBM_F32> {
 template <> struct Stor<LBM_F16S> {
     typedef __half T;
     typedef float R;
+    // (16-bit pairs are stored write-back already)
+    static __device__ __forceinline__ void st2_wb(T *p, R a, R b) { st2(p, a, b); }
     static __device__ __forceinline__ R ld(const T *p) {
         return __half2float(__ushort_as_half(__ldg(reinterpret_cast<const unsigned short *>(p))));
     }
@@ -129,6 +138,8 @@ template <> struct Stor<LBM_F16S> {
 template <> struct Stor<LBM_BF16S> {
     typedef __nv_bfloat16 T;
     typedef float R;
+    // (16-bit pairs are stored write-back already)
+    static __device__ __forceinline__ void st2_wb(T *p, R a, R b) { st2(p, a, b); }
     static __device__ __forceinline__ R ld(const T *p) {
         return __bfloat162float(
             __ushort_as_bfloat16(__ldg(reinterpret_cast<const unsigned short *>(p))));
