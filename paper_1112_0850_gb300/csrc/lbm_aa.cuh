@@ -87,7 +87,10 @@ __device__ __forceinline__ void aa_even_pair(const Dev &d, typename Stor<S>::T *
     typedef typename Stor<S>::R R;
     typedef typename Pair2<R>::V V;
     int x0, y, z;
-    const int bz = d.zrev ? (int)gridDim.y - 1 - (int)blockIdx.y : (int)blockIdx.y;  // (see k_step)
+    // alternating plane order (see k_step) on walled lattices only: without
+    // flags the 16-bit forms spill 16 more bytes at 64 registers for it (the
+    // 512^3 box lost 2.4%, and a lattice that size keeps no plane in L2)
+    const int bz = FLAGS && d.zrev ? (int)gridDim.y - 1 - (int)blockIdx.y : (int)blockIdx.y;
     if (!pair_cell<FLAT>(d.g, FLAT ? d.PF : d.P, blockDim.x, blockDim.y, blockIdx.x, bz, threadIdx.x, threadIdx.y,
                          x0, y, z))
         return;
@@ -168,7 +171,10 @@ __device__ __forceinline__ void aa_odd_pair(const Dev &d, typename Stor<S>::T *_
     typedef typename Pair2<R>::V V;
     constexpr bool FREE_ST = aa_free_scatter<S>();
     int x0, y, z;
-    const int bz = d.zrev ? (int)gridDim.y - 1 - (int)blockIdx.y : (int)blockIdx.y;  // (see k_step)
+    // alternating plane order (see k_step) on walled lattices only: without
+    // flags the 16-bit forms spill 16 more bytes at 64 registers for it (the
+    // 512^3 box lost 2.4%, and a lattice that size keeps no plane in L2)
+    const int bz = FLAGS && d.zrev ? (int)gridDim.y - 1 - (int)blockIdx.y : (int)blockIdx.y;
     if (!pair_cell<FLAT>(d.g, FLAT ? d.PF : d.P, blockDim.x, blockDim.y, blockIdx.x, bz, threadIdx.x, threadIdx.y,
                          x0, y, z))
         return;
