@@ -736,8 +736,11 @@ __global__ void __launch_bounds__(256, StepBlocks<S>::value)
     // to complete before it reads what this grid writes
     if (STEP_PDL) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     // blocks are dispatched in index order: with d.zrev the planes run from
-    // the last to the first
-    const int bz = d.zrev ? (int)gridDim.y - 1 - (int)blockIdx.y : (int)blockIdx.y;
+    // the last to the first. (The BF16 split step keeps ascending order: with
+    // the reversal its code schedules worse, 35.5 against 36.8 GFLUPS on the
+    // walled channel at the same spills, while the FP16 split one gains 1.3%.)
+    constexpr bool REV = S != LBM_BF16M;
+    const int bz = REV && d.zrev ? (int)gridDim.y - 1 - (int)blockIdx.y : (int)blockIdx.y;
     int x0, y, z;
     if (!pair_cell<FLAT>(d.g, FLAT ? d.PF : d.P, blockDim.x, blockDim.y, blockIdx.x, bz, threadIdx.x, threadIdx.y,
                          x0, y, z))
