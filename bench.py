@@ -394,7 +394,7 @@ def decomposed(args, torch, dist, world, rank):
     steps the slab. value = the whole lattice's fluid-cell updates per second
     (strong scaling: the lattice is fixed, each rank holds 1/N of it)."""
     from paper_1112_0850_gb300.slabs import RankSlab
-    if world == 1:  # a one-rank group for the driver (its exchange is a local copy)
+    if world == 1:  # a one-rank process group for RankSlab (its exchange is then a local copy)
         import socket
         sck = socket.socket()
         sck.bind(("127.0.0.1", 0))

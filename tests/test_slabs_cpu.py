@@ -255,7 +255,7 @@ def _run_driver(world, stop_after=-1):
 
 @pytest.mark.parametrize("world", [2, 3])
 def test_rank_driver_over_gloo_equals_unsplit(world):
-    """The decomposed driver (exchange_halos + step per round, as RankSlab runs
+    """The decomposed driver (exchange_halos, then a step, every step, as RankSlab runs
     it on GPUs) on gloo ranks: the joined interiors equal the unsplit oracle
     run bit for bit."""
     import oracle
