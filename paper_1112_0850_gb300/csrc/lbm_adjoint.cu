@@ -225,9 +225,12 @@ __global__ void __launch_bounds__(256, AdjBlocks<R>::value)
 // top stall). Threads take the cells of a plane's box rows in order, across
 // row ends. A solid cell stores zeros (its slots are never read), so that
 // every 32-byte sector of a lattice row is written whole.
+// I: the index type of the lattice, tape and gradient offsets; int where
+// every offset fits (19 qs and 3 nx ny nz below 2^31), so that each address is
+// one 32-bit index and one wide multiply-add.
 constexpr int ADJ1_BLOCKS = 4;
 
-template <bool FLAGS, bool FORCE>
+template <bool FLAGS, bool FORCE, class I>
 __global__ void __launch_bounds__(256, ADJ1_BLOCKS)
     k_adj_step1(const Dev d, const float *__restrict__ lam_in, float *__restrict__ lam_out,
                 const float *__restrict__ tape, float *__restrict__ grad_F) {
@@ -238,17 +241,17 @@ __global__ void __launch_bounds__(256, ADJ1_BLOCKS)
     const int bz = d.zrev ? (int)gridDim.y - 1 - (int)blockIdx.y : (int)blockIdx.y;  // (see k_step)
     const int x = k - r * g.nx, y = d.P.y0 + r, z = d.P.z0 + bz;
     const int c = cell_index(g, x, y, z);
-    const long long qs = g.qs;
+    const I qs = (I)g.qs;
     uint32_t m = 0u;
     if (FLAGS) {
         m = __ldg(d.mask + c);
         if (m & SOLID_BIT) {
 #pragma unroll
-            for (int i = 0; i < Q; ++i) lam_out[(long long)i * qs + c] = 0.0f;
+            for (int i = 0; i < Q; ++i) lam_out[(I)i * qs + c] = 0.0f;
             return;
         }
     }
-    const long long N = d.n_cells, cc = canon_index(g, x, y, z);
+    const I N = (I)d.n_cells, cc = (I)canon_index(g, x, y, z);
     float Gx = 0.0f, Gy = 0.0f, Gz = 0.0f;
     if (grad_F) {  // loaded with the gather, not after the collision
         Gx = grad_F[cc];
@@ -261,7 +264,7 @@ __global__ void __launch_bounds__(256, ADJ1_BLOCKS)
         // mu_i(x) = lambda_i(x + e_i), or lambda_opp(i)(x) where x + e_i is solid
         const int src = (wrap1(z + ez(i), g.nz) * g.ny + wrap1(y + ey(i), g.ny)) * g.pitch + wrap1(x + ex(i), g.nx);
         const bool b = FLAGS && i > 0 && ((m >> i) & 1u);
-        mu[i] = __ldg(lam_in + (b ? (long long)opp(i) * qs + c : (long long)i * qs + src));
+        mu[i] = __ldg(lam_in + (b ? (I)opp(i) * qs + c : (I)i * qs + src));
     }
     const float rho = __ldg(tape + c), ux = __ldg(tape + qs + c), uy = __ldg(tape + 2 * qs + c),
                 uz = __ldg(tape + 3 * qs + c);
@@ -281,7 +284,7 @@ __global__ void __launch_bounds__(256, ADJ1_BLOCKS)
     float gx, gy, gz;
     adj_collide<float, FORCE>(mu, rho, ux, uy, uz, Fx, Fy, Fz, DevR<float>::omega(d), gx, gy, gz, d.incomp);
 #pragma unroll
-    for (int i = 0; i < Q; ++i) __stcs(lam_out + (long long)i * qs + c, mu[i]);
+    for (int i = 0; i < Q; ++i) __stcs(lam_out + (I)i * qs + c, mu[i]);
     if (grad_F) {
         grad_F[cc] = Gx + gx;
         grad_F[N + cc] = Gy + gy;
@@ -362,10 +365,18 @@ static cudaError_t launch_adj_step1(const Dev &d, const void *li, void *lo, cons
     const float *a = static_cast<const float *>(li);
     const float *t = static_cast<const float *>(tape);
     float *b = static_cast<float *>(lo), *G = static_cast<float *>(gF);
-    if (d.force_on)
-        k_adj_step1<FLAGS, true><<<grid, 256, 0, d.stream>>>(d, a, b, t, G);
-    else
-        k_adj_step1<FLAGS, false><<<grid, 256, 0, d.stream>>>(d, a, b, t, G);
+    const bool small = (long long)Q * d.g.qs < (1LL << 31) && 3 * d.n_cells < (1LL << 31);
+    if (small) {
+        if (d.force_on)
+            k_adj_step1<FLAGS, true, int><<<grid, 256, 0, d.stream>>>(d, a, b, t, G);
+        else
+            k_adj_step1<FLAGS, false, int><<<grid, 256, 0, d.stream>>>(d, a, b, t, G);
+    } else {
+        if (d.force_on)
+            k_adj_step1<FLAGS, true, long long><<<grid, 256, 0, d.stream>>>(d, a, b, t, G);
+        else
+            k_adj_step1<FLAGS, false, long long><<<grid, 256, 0, d.stream>>>(d, a, b, t, G);
+    }
     return cudaGetLastError();
 }
 
