@@ -302,12 +302,22 @@ template <> __device__ __forceinline__ Guo2<double> uniform_guo<double, false>(c
 // Where the gather finds the row of population i that cell row (y, z) pulls
 // from, (y - e_iy, z - e_iz): in the source lattice in global memory, or in
 // a shared-memory copy of those 19 rows (see k_step_tma).
-template <int S> struct GlobalRows {
+// Offset k qs + c of lattice P: in 64 bits, or (I = unsigned, where every
+// offset of the lattice fits) as one 32-bit index, which costs fewer
+// instructions per address.
+template <class I, class T> __device__ __forceinline__ T *lat_at(T *P, int k, long long qs, int c) {
+    if constexpr (sizeof(I) == 4)
+        return P + ((unsigned)k * (unsigned)qs + (unsigned)c);
+    else
+        return P + (long long)k * qs + c;
+}
+
+template <int S, class I = long long> struct GlobalRows {
     typedef typename Stor<S>::T T;
     typedef typename Stor<S>::R R;
     const T *src;
     __device__ __forceinline__ const T *row(const Geom &g, int i, int y, int z) const {
-        return src + (long long)i * g.qs + (wrap1(z - ez(i), g.nz) * g.ny + wrap1(y - ey(i), g.ny)) * g.pitch;
+        return lat_at<I>(src, i, g.qs, (wrap1(z - ez(i), g.nz) * g.ny + wrap1(y - ey(i), g.ny)) * g.pitch);
     }
     static __device__ __forceinline__ R ld(const T *p) { return Stor<S>::ld(p); }
     static __device__ __forceinline__ void ld2(const T *p, R &a, R &b) { Stor<S>::ld2(p, a, b); }
@@ -372,7 +382,7 @@ __device__ __forceinline__ void block_partials(const double red[4], double *__re
 // collide, store to dst. RED: also add the pair's mass and momentum j + F/2
 // (of the pre-collision state, in FP64) to red[4]; the pair then never
 // returns early, so that its block can reduce.
-template <int S, bool FLAGS, int FORCE, bool RECORD, class Rows, bool RED = false>
+template <int S, bool FLAGS, int FORCE, bool RECORD, class Rows, bool RED = false, class I = long long>
 __device__ __forceinline__ void step_pair(const Dev &d, const Rows &rows, const typename Stor<S>::T *__restrict__ src,
                                           typename Stor<S>::T *__restrict__ dst, typename Stor<S>::R *__restrict__ tape,
                                           int x0, int y, int z, double *red = nullptr) {
@@ -411,7 +421,7 @@ __device__ __forceinline__ void step_pair(const Dev &d, const Rows &rows, const 
     for (int i = 0; i < Q; ++i) {
         const T *Pi = rows.row(g, i, y, z);
         if (FLAGS && !LINKS && !MFIX && i > 0) {
-            const T *Po = src + (long long)opp(i) * g.qs + c;  // own cell, opposite population
+            const T *Po = lat_at<I>(src, opp(i), g.qs, c);  // own cell, opposite population
             const bool b0 = (m0 >> opp(i)) & 1u, b1 = (m1 >> opp(i)) & 1u;
             if (ex(i) == 0) {
                 if (b0 == b1) {
@@ -436,7 +446,7 @@ __device__ __forceinline__ void step_pair(const Dev &d, const Rows &rows, const 
         // cell's own opposite slots, loaded over the gathered (unread) ones
 #pragma unroll
         for (int i = 1; i < Q; ++i) {
-            const T *Po = src + (long long)opp(i) * g.qs + c;
+            const T *Po = lat_at<I>(src, opp(i), g.qs, c);
             if ((m0 >> opp(i)) & 1u) s[i].x = Stor<S>::ld(Po);
             if ((m1 >> opp(i)) & 1u) s[i].y = Stor<S>::ld(Po + 1);
         }
@@ -472,7 +482,7 @@ __device__ __forceinline__ void step_pair(const Dev &d, const Rows &rows, const 
         // moments again.
 #pragma unroll
         for (int i = 1; i < Q; ++i) {
-            const T *Po = src + (long long)opp(i) * g.qs + c;
+            const T *Po = lat_at<I>(src, opp(i), g.qs, c);
             if (live0 && s[i].x != s[i].x) {
                 s[i].x = Stor<S>::ld(Po);
                 if (d.moving_on && d.flags[pull_src(g, x0, y, z, i)] == 2) s[i].x += wall_term<R>(d, i);
@@ -506,19 +516,19 @@ __device__ __forceinline__ void step_pair(const Dev &d, const Rows &rows, const 
         const R nan = quiet_nan<R>();
 #pragma unroll
         for (int i = 0; i < Q; ++i)
-            Stor<S>::st2(dst + (long long)i * g.qs + c, live0 ? s[i].x : nan, live1 ? s[i].y : nan);
+            Stor<S>::st2(lat_at<I>(dst, i, g.qs, c), live0 ? s[i].x : nan, live1 ? s[i].y : nan);
     } else if (FLAGS && LinkBounce<S>::value && d.has_moving && !(live0 && live1)) {
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            if (live0) Stor<S>::st(dst + (long long)i * g.qs + c, s[i].x);
-            if (live1) Stor<S>::st(dst + (long long)i * g.qs + c + 1, s[i].y);
+            if (live0) Stor<S>::st(lat_at<I>(dst, i, g.qs, c), s[i].x);
+            if (live1) Stor<S>::st(lat_at<I>(dst, i, g.qs, c + 1), s[i].y);
         }
     } else {
         // write-back stores: the planes a step writes last stay in L2 for the
         // next step, which starts on them (FP32 channel 39.3 against 39.8
         // GFLUPS with streaming stores; the AA and reverse steps keep theirs)
 #pragma unroll
-        for (int i = 0; i < Q; ++i) Stor<S>::st2_wb(dst + (long long)i * g.qs + c, s[i].x, s[i].y);
+        for (int i = 0; i < Q; ++i) Stor<S>::st2_wb(lat_at<I>(dst, i, g.qs, c), s[i].x, s[i].y);
     }
     if (FLAGS && LinkBounce<S>::value && d.has_moving) {
         // Links into a moving wall (not in the link list): slot opp(j) of the
@@ -530,11 +540,11 @@ __device__ __forceinline__ void step_pair(const Dev &d, const Rows &rows, const 
             for (int j = 1; j < Q; ++j) {
                 if (live0 && ((mm.x >> j) & 1u)) {
                     const int t = push_dst(g, x0, y, z, j);
-                    if (d.flags[t] == 2) Stor<S>::st(dst + (long long)opp(j) * g.qs + t, s[j].x - wall_term<R>(d, j));
+                    if (d.flags[t] == 2) Stor<S>::st(lat_at<I>(dst, opp(j), g.qs, t), s[j].x - wall_term<R>(d, j));
                 }
                 if (live1 && ((mm.y >> j) & 1u)) {
                     const int t = push_dst(g, x0 + 1, y, z, j);
-                    if (d.flags[t] == 2) Stor<S>::st(dst + (long long)opp(j) * g.qs + t, s[j].y - wall_term<R>(d, j));
+                    if (d.flags[t] == 2) Stor<S>::st(lat_at<I>(dst, opp(j), g.qs, t), s[j].y - wall_term<R>(d, j));
                 }
             }
         }
@@ -722,8 +732,8 @@ constexpr int STEP_PDL = 1;
 
 // FLAT: the launch of d.PF (pairs in plane order), else of d.P (whole rows).
 // ODD (moment-split formats only): rows of odd length, whose last cell is
-// alone in its pair (see split_ghost).
-template <int S, bool FLAGS, int FORCE, bool RECORD, bool FLAT = false, bool ODD = false>
+// alone in its pair (see split_ghost). U32: 32-bit lattice offsets (lat_at).
+template <int S, bool FLAGS, int FORCE, bool RECORD, bool FLAT = false, bool ODD = false, bool U32 = false>
 __global__ void __launch_bounds__(256, StepBlocks<S>::value)
     k_step(const Dev d, const typename Stor<S>::T *__restrict__ src, typename Stor<S>::T *__restrict__ dst,
            typename Stor<S>::R *__restrict__ tape) {
@@ -747,6 +757,9 @@ __global__ void __launch_bounds__(256, StepBlocks<S>::value)
         return;
     if constexpr (is_split(S))
         step_pair_split<S, FLAGS, FORCE, RECORD, false, ODD>(d, src, dst, tape, x0, y, z);
+    else if constexpr (U32)
+        step_pair<S, FLAGS, FORCE, RECORD, GlobalRows<S, unsigned>, false, unsigned>(
+            d, GlobalRows<S, unsigned>{src}, src, dst, tape, x0, y, z);
     else
         step_pair<S, FLAGS, FORCE, RECORD>(d, GlobalRows<S>{src}, src, dst, tape, x0, y, z);
 }
@@ -1234,10 +1247,20 @@ inline dim3 row_block(const Dev &d) { return dim3(d.L.bx_threads, d.L.by_threads
 inline dim3 step_grid(const Dev &d) { return dim3(d.P.nxb * d.P.nyb, d.P.nzr); }
 inline dim3 step_block(const Dev &d) { return dim3(d.P.bx_threads, d.P.by_threads); }
 
-template <int S, bool FLAGS, int FORCE, bool FLAT, bool ODD = false>
+// 32-bit lattice offsets: measured on the FP32 step with flags (walled
+// channel +0.9%); the 16-bit and flag-free steps gained nothing (512^3 box
+// FP16 -1.9%), so they keep 64-bit offsets.
+template <int S, bool FLAGS> inline bool step_u32(const Dev &d) {
+    return S == LBM_F32 && FLAGS && (long long)Q * d.g.qs < (1LL << 32);
+}
+
+template <int S, bool FLAGS, int FORCE, bool FLAT, bool ODD = false, bool U32 = false>
 static cudaError_t launch_step3f(const Dev &d, const void *src, void *dst, void *tape) {
     typedef typename Stor<S>::T T;
     typedef typename Stor<S>::R R;
+    if constexpr (!U32 && S == LBM_F32 && FLAGS) {
+        if (step_u32<S, FLAGS>(d)) return launch_step3f<S, FLAGS, FORCE, FLAT, ODD, true>(d, src, dst, tape);
+    }
     const RowLaunch &P = FLAT ? d.PF : d.P;
     const dim3 grid(P.nxb * P.nyb, P.nzr), block(P.bx_threads, P.by_threads);
     if (STEP_PDL) {
@@ -1250,19 +1273,19 @@ static cudaError_t launch_step3f(const Dev &d, const void *src, void *dst, void 
         attr[0].val.programmaticStreamSerializationAllowed = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        cudaError_t e = tape ? cudaLaunchKernelEx(&cfg, k_step<S, FLAGS, FORCE, true, FLAT, ODD>, d,
+        cudaError_t e = tape ? cudaLaunchKernelEx(&cfg, k_step<S, FLAGS, FORCE, true, FLAT, ODD, U32>, d,
                                                   static_cast<const T *>(src), static_cast<T *>(dst),
                                                   static_cast<R *>(tape))
-                             : cudaLaunchKernelEx(&cfg, k_step<S, FLAGS, FORCE, false, FLAT, ODD>, d,
+                             : cudaLaunchKernelEx(&cfg, k_step<S, FLAGS, FORCE, false, FLAT, ODD, U32>, d,
                                                   static_cast<const T *>(src), static_cast<T *>(dst), (R *)nullptr);
         if (e != cudaSuccess) return e;
         return cudaGetLastError();
     }
     if (tape)
-        k_step<S, FLAGS, FORCE, true, FLAT, ODD><<<grid, block, 0, d.stream>>>(
+        k_step<S, FLAGS, FORCE, true, FLAT, ODD, U32><<<grid, block, 0, d.stream>>>(
             d, static_cast<const T *>(src), static_cast<T *>(dst), static_cast<R *>(tape));
     else
-        k_step<S, FLAGS, FORCE, false, FLAT, ODD><<<grid, block, 0, d.stream>>>(
+        k_step<S, FLAGS, FORCE, false, FLAT, ODD, U32><<<grid, block, 0, d.stream>>>(
             d, static_cast<const T *>(src), static_cast<T *>(dst), nullptr);
     return cudaGetLastError();
 }
