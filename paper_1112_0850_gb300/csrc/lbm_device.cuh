@@ -323,14 +323,15 @@ inline RowLaunch pair_launch(const Geom &g, int y0 = 0, int nyr = -1, int z0 = 0
 // pairs are not a multiple of 32 (n = 200: 28 of 128 threads). The flat launch
 // gives consecutive threads consecutive pairs of a plane's rows, across row
 // ends (with rows padded only to pairs, consecutive rows are adjacent in
-// memory, so such warps still load contiguous runs): blocks of 256 x 1.
+// memory, so such warps still load contiguous runs): blocks of threads x 1
+// (256 unless a kernel is compiled for another block size).
 inline bool rows_leave_lanes_idle(const RowLaunch &P) { return P.nxb * P.bx_threads != P.W; }
-inline RowLaunch flat_launch(const RowLaunch &rows) {
+inline RowLaunch flat_launch(const RowLaunch &rows, int threads = 256) {
     RowLaunch L = rows;
     L.nxb = 1;
-    L.bx_threads = 256;
+    L.bx_threads = threads;
     L.by_threads = 1;
-    L.nyb = (int)(((long long)L.nyr * L.W + 255) / 256);
+    L.nyb = (int)(((long long)L.nyr * L.W + threads - 1) / threads);
     return L;
 }
 

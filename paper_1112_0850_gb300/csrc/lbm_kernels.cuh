@@ -730,11 +730,20 @@ __device__ __forceinline__ void step_pair_split(const Dev &d, const typename Sto
 // +0.5% when launched one by one (short runs), +0.2% in replayed graphs.
 constexpr int STEP_PDL = 1;
 
+// Block shape of the step kernel: the flat FP32 step with 32-bit offsets runs
+// 7 blocks of 128 threads per SM (72 registers, no spills: 28 warps) instead
+// of 3 of 256 (80 registers: 24 warps), +1.1% on the walled channel; 4 blocks
+// of 256 (64 registers) spilled 48 bytes and lost 4%.
+template <int S, bool FLAT, bool U32> constexpr int step_threads() { return U32 && FLAT ? 128 : 256; }
+template <int S, bool FLAT, bool U32> constexpr int step_min_blocks() {
+    return U32 && FLAT ? 7 : StepBlocks<S>::value;
+}
+
 // FLAT: the launch of d.PF (pairs in plane order), else of d.P (whole rows).
 // ODD (moment-split formats only): rows of odd length, whose last cell is
 // alone in its pair (see split_ghost). U32: 32-bit lattice offsets (lat_at).
 template <int S, bool FLAGS, int FORCE, bool RECORD, bool FLAT = false, bool ODD = false, bool U32 = false>
-__global__ void __launch_bounds__(256, StepBlocks<S>::value)
+__global__ void __launch_bounds__(step_threads<S, FLAT, U32>(), step_min_blocks<S, FLAT, U32>())
     k_step(const Dev d, const typename Stor<S>::T *__restrict__ src, typename Stor<S>::T *__restrict__ dst,
            typename Stor<S>::R *__restrict__ tape) {
     // launched as a programmatic dependent: wait for the kernel before it (the
@@ -1259,7 +1268,14 @@ static cudaError_t launch_step3f(const Dev &d, const void *src, void *dst, void 
     typedef typename Stor<S>::T T;
     typedef typename Stor<S>::R R;
     if constexpr (!U32 && S == LBM_F32 && FLAGS) {
-        if (step_u32<S, FLAGS>(d)) return launch_step3f<S, FLAGS, FORCE, FLAT, ODD, true>(d, src, dst, tape);
+        if (step_u32<S, FLAGS>(d)) {
+            if constexpr (FLAT && step_threads<S, true, true>() != 256) {
+                Dev d2 = d;  // the same pairs in blocks of the kernel's size
+                d2.PF = flat_launch(d.P, step_threads<S, true, true>());
+                return launch_step3f<S, FLAGS, FORCE, FLAT, ODD, true>(d2, src, dst, tape);
+            }
+            return launch_step3f<S, FLAGS, FORCE, FLAT, ODD, true>(d, src, dst, tape);
+        }
     }
     const RowLaunch &P = FLAT ? d.PF : d.P;
     const dim3 grid(P.nxb * P.nyb, P.nzr), block(P.bx_threads, P.by_threads);
