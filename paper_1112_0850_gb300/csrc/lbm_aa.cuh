@@ -111,10 +111,23 @@ __device__ __forceinline__ void aa_even_pair(const Dev &d, typename Stor<S>::T *
     if (RED) pair_add_totals<R>(m, live0, live1, d.incomp, red);
     pair_check_record<R, RECORD>(d, c, live0, live1, m, tape);
     collide2<R, FORCE != 0, relax_about_t(S)>(s, m, DevR<R>::omega(d), DevR<R>::cs(d), Fx, Fy, Fz, G, d.incomp);
-    // a solid lane writes its NaN back (its slots stay marked)
+    // a solid lane writes its NaN back (its slots stay marked). FP32: a
+    // 32-byte sector whose 8 cells are all solid skips its stores instead (as
+    // in the two-grid step: no reader takes a solid slot's value), found by
+    // one ballot over the sector's four pairs on lanes 4k .. 4k + 3
+    bool skip = false;
+    if constexpr (FLAGS && S == LBM_F32) {
+        if ((d.g.pitch & 7) == 0 && (((d.g.nx + 1) / 2) & 3) == 0) {
+            const unsigned sb = __ballot_sync(__activemask(), !live0 && !live1);
+            skip = ((sb >> ((threadIdx.x & 31) & ~3u)) & 0xFu) == 0xFu;
+        }
+    }
+    if (!skip) {
 #pragma unroll
-    for (int i = 0; i < Q; ++i)
-        Stor<S>::st2(A + (long long)opp(i) * qs + c, !FLAGS || live0 ? s[i].x : nan, !FLAGS || live1 ? s[i].y : nan);
+        for (int i = 0; i < Q; ++i)
+            Stor<S>::st2(A + (long long)opp(i) * qs + c, !FLAGS || live0 ? s[i].x : nan,
+                         !FLAGS || live1 ? s[i].y : nan);
+    }
 }
 
 template <int S, bool FLAGS, int FORCE, bool RECORD, bool FLAT>
