@@ -220,7 +220,8 @@ template <int S> __device__ __forceinline__ bool nan_marked(const Dev &d) {
 // aligned pair per load and every population is stored as one aligned pair;
 // populations with e_x = +-1 come from sources shifted by one cell and are
 // loaded per cell. Every pair is stored whole, a solid cell included, so
-// 32-byte sectors are written complete. Halfway bounce-back takes one of
+// 32-byte sectors are written complete (FP32 leaves out the sectors whose
+// cells are all solid, which no one reads). Halfway bounce-back takes one of
 // these forms, chosen per storage format by measurement (Bounce<S>):
 //
 //  - load side (FP64): a 32-bit push mask per cell (bit j: x + e_j is solid)
@@ -511,7 +512,8 @@ __device__ __forceinline__ void step_pair(const Dev &d, const Rows &rows, const 
     }
     collide2<R, FORCE != 0, relax_about_t(S)>(s, m, DevR<R>::omega(d), DevR<R>::cs(d), Fx, Fy, Fz, G, d.incomp);
     // The pair is stored whole, a solid cell included, so 32-byte sectors are
-    // written complete: a solid cell's values are never read (load side), it
+    // written complete: a solid cell's values are never read (load side and
+    // mask-guided reload, where all-solid sectors are left out below), it
     // stores the NaN that marks it (NaN marks), or its slots are link targets
     // that k_bounce rewrites (links). When moving-wall links are written into
     // solid slots by other threads of this launch, a pair with a solid cell
